@@ -1,0 +1,796 @@
+/*
+ * pnp_oracle.c -- plain, slow, FP64 CPU oracle for the PNP-cDFT hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may include, link
+ * or call this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * with the CUDA path.
+ *
+ * What it computes, in the paper's order (Meng, Zheng, Lin, Sushko,
+ * "Numerical solution of 3D PNP equations coupled with cDFT", arXiv:1407.0674):
+ *
+ *   weighted densities  n_a(r) = sum_i int rho_i(r') w_i^a(r'-r) dr'      Sec 2.3.1
+ *   Rosenfeld FMT derivatives dPhi/dn_a                                   Sec 2.3.1
+ *   back-convolution  mu_hs,i(r) = sum_a int dPhi/dn_a(r') w_i^a(r-r') dr' Sec 2.3.1
+ *   square-well mean field  mu_sh(r) = 1/2 int rho_s(r') Phi(|r-r'|) dr'  Sec 2.3.2
+ *   delta-shell integrals by the (theta, phi) change of variables         Sec 3.5
+ *   7-point harmonic-mean finite differences                              Sec 3.1
+ *   relaxed Gummel iteration on the Slotboom form                         Sec 2.1, 3.2
+ *
+ * Every integral is evaluated as a DIRECT real-space sum over quadrature nodes
+ * (no FFT).  The value at an off-grid node is trilinear in the 8 surrounding
+ * grid values; grid values outside the domain are 0 on non-periodic axes
+ * (zero extension, Sec 3.5) and wrap on periodic axes.
+ *
+ * Quadrature (Sec 3.5 leaves the rule open; this is the fixed reading):
+ *   angular: theta_a = (a+1/2) 2 pi / n_theta (trapezoid), mu_b = cos(phi_b) at
+ *            the n_mu Gauss-Legendre nodes on [-1,1]; weight (2 pi/n_theta) w_b
+ *            (the R^2 sin(phi) dphi dtheta measure after mu = cos phi).
+ *   shell of radius R: nodes R u, weights R^2 * angular weight.
+ *   ball / thick shell [a,b]: radial Gauss-Legendre (n_r nodes) on [a,b] with
+ *            the r^2 factor, times the angular rule.
+ *   defaults: n_mu = max(8, ceil(2 pi R)), n_theta = 2 n_mu rounded up to a
+ *            multiple of 4, n_r = max(4, ceil(2 (b - a))); for a thick shell
+ *            the angular counts use its outer radius.
+ * All lengths are in units of the grid spacing h; potentials in kT/e;
+ * chemical potentials in kT.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Gauss-Legendre rule on [-1,1]: Newton iteration on P_n, evaluated by the
+ * three-term recurrence (n+1)P_{n+1} = (2n+1) x P_n - n P_{n-1}.            */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            /* P_n'(z) = n (z P_n - P_{n-1}) / (z^2 - 1) */
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) {
+                /* one more evaluation of the derivative at the final z */
+                p0 = 1.0; p1 = z;
+                for (int k = 2; k <= n; ++k) {
+                    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                break;
+            }
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Node sets (Sec 3.5).  kind 0: shell of radius r_out; kind 1: ball [0,r_out];
+ * kind 2: thick shell [r_in, r_out].  Returns the node count.  With null
+ * output pointers it only counts.                                        */
+static int default_nmu(double r) { int n = (int)ceil(2.0 * M_PI * r); return n < 8 ? 8 : n; }
+static int default_ntheta(int nmu) { int n = 2 * nmu; return (n + 3) / 4 * 4; }
+static int default_nr(double len) { int n = (int)ceil(2.0 * len); return n < 4 ? 4 : n; }
+
+int oracle_nodeset(int kind, double r_in, double r_out, int nmu, int ntheta, int nr,
+                   double *px, double *py, double *pz, double *w,
+                   double *ux, double *uy, double *uz)
+{
+    if (nmu <= 0) nmu = default_nmu(r_out);
+    if (ntheta <= 0) ntheta = default_ntheta(nmu);
+    double a = (kind == 1) ? 0.0 : r_in;
+    if (kind == 0) nr = 1;
+    else if (nr <= 0) nr = default_nr(r_out - a);
+    int count = nmu * ntheta * nr;
+    if (!px) return count;
+
+    double *gx = malloc(sizeof(double) * nmu), *gw = malloc(sizeof(double) * nmu);
+    double *rx = malloc(sizeof(double) * nr), *rw = malloc(sizeof(double) * nr);
+    gauss_legendre(nmu, gx, gw);
+    if (kind == 0) {
+        rx[0] = r_out;
+        rw[0] = r_out * r_out;           /* R^2 of the surface measure */
+    } else {
+        gauss_legendre(nr, rx, rw);
+        for (int k = 0; k < nr; ++k) {   /* map [-1,1] -> [a, r_out], weight r^2 dr */
+            double r = 0.5 * (r_out - a) * rx[k] + 0.5 * (r_out + a);
+            rw[k] = 0.5 * (r_out - a) * rw[k] * r * r;
+            rx[k] = r;
+        }
+    }
+    int idx = 0;
+    for (int k = 0; k < nr; ++k)
+        for (int b = 0; b < nmu; ++b) {
+            double mu = gx[b], sphi = sqrt(1.0 - mu * mu);
+            for (int t = 0; t < ntheta; ++t) {
+                double th = (t + 0.5) * 2.0 * M_PI / ntheta;
+                double u0 = cos(th) * sphi, u1 = sin(th) * sphi, u2 = mu;
+                px[idx] = rx[k] * u0;
+                py[idx] = rx[k] * u1;
+                pz[idx] = rx[k] * u2;
+                w[idx] = rw[k] * (2.0 * M_PI / ntheta) * gw[b];
+                if (ux) { ux[idx] = u0; uy[idx] = u1; uz[idx] = u2; }
+                ++idx;
+            }
+        }
+    free(gx); free(gw); free(rx); free(rw);
+    return count;
+}
+
+/* ------------------------------------------------------------------ */
+/* Grid with per-axis periodicity; fields are C order [z][y][x].         */
+typedef struct {
+    int n[3];          /* nx, ny, nz */
+    int periodic[3];
+} grid_t;
+
+static inline double grid_value(const grid_t *g, const double *f, long ix, long iy, long iz)
+{
+    long idx[3] = {ix, iy, iz};
+    for (int d = 0; d < 3; ++d) {
+        long n = g->n[d];
+        if (g->periodic[d]) {
+            idx[d] %= n;
+            if (idx[d] < 0) idx[d] += n;
+        } else if (idx[d] < 0 || idx[d] >= n) {
+            return 0.0;                   /* zero extension outside Omega */
+        }
+    }
+    return f[(idx[2] * g->n[1] + idx[1]) * g->n[0] + idx[0]];
+}
+
+/* trilinear interpolation at the point (X, Y, Z) in grid-index units */
+static double interp(const grid_t *g, const double *f, double X, double Y, double Z)
+{
+    double fx = floor(X), fy = floor(Y), fz = floor(Z);
+    long i0 = (long)fx, j0 = (long)fy, k0 = (long)fz;
+    double tx = X - fx, ty = Y - fy, tz = Z - fz;
+    double v = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+        double wgt = (a ? tx : 1.0 - tx) * (b ? ty : 1.0 - ty) * (e ? tz : 1.0 - tz);
+        if (wgt != 0.0) v += wgt * grid_value(g, f, i0 + a, j0 + b, k0 + e);
+    }
+    return v;
+}
+
+/* Test hook: instead of a grid field, evaluate rho_i(r) = amp_i cos(k.r + ph)
+ * exactly at each node ("analytic" mode for the plane-wave pins).        */
+typedef struct {
+    int enabled;
+    double k[3], phase;
+    const double *amp;   /* per species */
+} wave_t;
+
+static double field_at(const grid_t *g, const double *f, const wave_t *wv, int sp,
+                       double X, double Y, double Z)
+{
+    if (wv && wv->enabled)
+        return wv->amp[sp] * cos(wv->k[0] * X + wv->k[1] * Y + wv->k[2] * Z + wv->phase);
+    return interp(g, f, X, Y, Z);
+}
+
+/* ------------------------------------------------------------------ */
+/* Problem description (oracle-private).                                 */
+typedef struct {
+    int nx, ny, nz;
+    int bc[3];                 /* 0 periodic, 1 Dirichlet, 2 no-flux */
+    int s;                     /* number of mobile species */
+    const double *R;           /* hard-sphere radius per species (h) */
+    const int *q;              /* valence */
+    const double *rho_b;       /* bulk density (h^-3) */
+    const double *D;           /* diffusion coefficient */
+    const double *depth;       /* square-well depth eps_i (kT) */
+    double well_inner, well_outer;   /* square-well shell radii (h) */
+    int nsites;
+    const double *sites;       /* 3*nsites, grid-index coordinates */
+    double site_alpha;         /* Gaussian exponent (h^-2) */
+    const double *rho_f;       /* fixed charge per cell (e h^-3) or NULL */
+    double lB;                 /* Bjerrum length (h) */
+    double phi_lo, phi_hi;     /* Dirichlet potentials on the z faces (kT/e) */
+    double lambda_phi, lambda_rho, tol;
+    int max_iter;
+    int nmu, ntheta, nr;       /* FMT quadrature counts (0 = default rule) */
+    int w_nmu, w_ntheta, w_nr; /* square-well quadrature counts */
+    int sw_half;               /* 1: the 1/2 of Sec 2.3.2 kept; 0: dropped */
+    double lin_tol;            /* PCG relative residual target */
+    int lin_max_iter;
+    int rho_mix;               /* 0: linear relaxation (Sec 3.2), 1: geometric */
+} oracle_problem;
+
+static grid_t cdft_grid(const oracle_problem *p)
+{
+    grid_t g;
+    g.n[0] = p->nx; g.n[1] = p->ny; g.n[2] = p->nz;
+    for (int d = 0; d < 3; ++d) g.periodic[d] = (p->bc[d] == 0);
+    return g;
+}
+
+typedef struct {
+    int n;
+    double *px, *py, *pz, *w, *ux, *uy, *uz;
+} nodes_t;
+
+static nodes_t make_nodes(int kind, double r_in, double r_out, int nmu, int ntheta, int nr)
+{
+    nodes_t t;
+    t.n = oracle_nodeset(kind, r_in, r_out, nmu, ntheta, nr, 0, 0, 0, 0, 0, 0, 0);
+    t.px = malloc(sizeof(double) * t.n * 7);
+    t.py = t.px + t.n; t.pz = t.py + t.n; t.w = t.pz + t.n;
+    t.ux = t.w + t.n; t.uy = t.ux + t.n; t.uz = t.uy + t.n;
+    oracle_nodeset(kind, r_in, r_out, nmu, ntheta, nr, t.px, t.py, t.pz, t.w, t.ux, t.uy, t.uz);
+    return t;
+}
+static void free_nodes(nodes_t *t) { free(t->px); }
+
+/* ------------------------------------------------------------------ */
+/* Weighted densities, Sec 2.3.1:
+ *   n_a(r) = sum_i int_Omega rho_i(r') w_i^a(r' - r) dr'
+ * with w3 the ball indicator, w2 = delta(|r|-R), vec w2 = (r/|r|) delta,
+ * w0 = w2/(4 pi R^2), w1 = w2/(4 pi R), vec w1 = vec w2/(4 pi R).
+ * Output layout: n[a*N + p], a = n0,n1,n2,n3,n1x,n1y,n1z,n2x,n2y,n2z.   */
+void oracle_weighted_densities(const oracle_problem *p, const double *rho, double *n,
+                               const double *wave_k, double wave_phase, const double *wave_amp)
+{
+    grid_t g = cdft_grid(p);
+    long N = (long)p->nx * p->ny * p->nz;
+    wave_t wv = {0};
+    if (wave_k) {
+        wv.enabled = 1;
+        wv.k[0] = wave_k[0]; wv.k[1] = wave_k[1]; wv.k[2] = wave_k[2];
+        wv.phase = wave_phase;
+        wv.amp = wave_amp;
+    }
+    memset(n, 0, sizeof(double) * 10 * N);
+    for (int i = 0; i < p->s; ++i) {
+        double R = p->R[i];
+        nodes_t sh = make_nodes(0, 0.0, R, p->nmu, p->ntheta, p->nr);
+        nodes_t ba = make_nodes(1, 0.0, R, p->nmu, p->ntheta, p->nr);
+        const double *rho_i = rho ? rho + i * N : 0;
+        double c0 = 1.0 / (4.0 * M_PI * R * R), c1 = 1.0 / (4.0 * M_PI * R);
+#pragma omp parallel for schedule(static)
+        for (long pt = 0; pt < N; ++pt) {
+            double X = (double)(pt % p->nx);
+            double Y = (double)((pt / p->nx) % p->ny);
+            double Z = (double)(pt / ((long)p->nx * p->ny));
+            double n2 = 0, v2x = 0, v2y = 0, v2z = 0, n3 = 0;
+            for (int q = 0; q < sh.n; ++q) {
+                double v = field_at(&g, rho_i, &wv, i, X + sh.px[q], Y + sh.py[q], Z + sh.pz[q]);
+                n2 += sh.w[q] * v;
+                v2x += sh.w[q] * sh.ux[q] * v;
+                v2y += sh.w[q] * sh.uy[q] * v;
+                v2z += sh.w[q] * sh.uz[q] * v;
+            }
+            for (int q = 0; q < ba.n; ++q)
+                n3 += ba.w[q] * field_at(&g, rho_i, &wv, i, X + ba.px[q], Y + ba.py[q], Z + ba.pz[q]);
+            n[0 * N + pt] += c0 * n2;
+            n[1 * N + pt] += c1 * n2;
+            n[2 * N + pt] += n2;
+            n[3 * N + pt] += n3;
+            n[4 * N + pt] += c1 * v2x;
+            n[5 * N + pt] += c1 * v2y;
+            n[6 * N + pt] += c1 * v2z;
+            n[7 * N + pt] += v2x;
+            n[8 * N + pt] += v2y;
+            n[9 * N + pt] += v2z;
+        }
+        free_nodes(&sh);
+        free_nodes(&ba);
+    }
+}
+
+/* Rosenfeld FMT free-energy density Phi (Sec 2.3.1) at one point.        */
+static double phi_rosenfeld(const double *a)
+{
+    double n0 = a[0], n1 = a[1], n2 = a[2], n3 = a[3];
+    double v1v2 = a[4] * a[7] + a[5] * a[8] + a[6] * a[9];
+    double v2v2 = a[7] * a[7] + a[8] * a[8] + a[9] * a[9];
+    double o = 1.0 - n3;
+    return -n0 * log(o) + n1 * n2 / o + n2 * n2 * n2 / (24.0 * M_PI * o * o)
+           - v1v2 / o - n2 * v2v2 / (8.0 * M_PI * o * o);
+}
+
+/* The ten partial derivatives printed in Sec 2.3.1.  Returns the number of
+ * points where n3 >= 1 or a value is not finite (packing error).         */
+long oracle_dphi(long N, const double *n, double *psi)
+{
+    long bad = 0;
+    for (long pt = 0; pt < N; ++pt) {
+        double n0 = n[0 * N + pt], n1 = n[1 * N + pt], n2 = n[2 * N + pt], n3 = n[3 * N + pt];
+        double v1[3] = {n[4 * N + pt], n[5 * N + pt], n[6 * N + pt]};
+        double v2[3] = {n[7 * N + pt], n[8 * N + pt], n[9 * N + pt]};
+        int flagged = !(n3 < 1.0);
+        double o = 1.0 - n3;
+        double v1v2 = v1[0] * v2[0] + v1[1] * v2[1] + v1[2] * v2[2];
+        double v2v2 = v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2];
+        psi[0 * N + pt] = -log(1.0 - n3);
+        psi[1 * N + pt] = n2 / (1.0 - n3);
+        psi[2 * N + pt] = n1 / (1.0 - n3) + (n2 * n2 - v2v2) / (8.0 * M_PI * o * o);
+        psi[3 * N + pt] = n0 / (1.0 - n3) + (n1 * n2 - v1v2) / (o * o)
+                          + (n2 * n2 * n2 - 3.0 * n2 * v2v2) / (12.0 * M_PI * o * o * o);
+        for (int c = 0; c < 3; ++c) {
+            psi[(4 + c) * N + pt] = v2[c] / (n3 - 1.0);
+            psi[(7 + c) * N + pt] = v1[c] / (n3 - 1.0) - n2 * v2[c] / (4.0 * M_PI * o * o);
+        }
+        for (int a = 0; a < 10; ++a)
+            if (!isfinite(psi[a * N + pt])) flagged = 1;
+        bad += flagged;
+    }
+    return bad;
+}
+
+/* Free energy h^3 sum_Omega Phi(n) (h = 1); used by the adjoint checks.   */
+double oracle_fhs(long N, const double *n)
+{
+    double F = 0.0;
+    double a[10];
+    for (long pt = 0; pt < N; ++pt) {
+        for (int k = 0; k < 10; ++k) a[k] = n[k * N + pt];
+        F += phi_rosenfeld(a);
+    }
+    return F;
+}
+
+/* Back-convolution, Sec 2.3.1:
+ *   mu_hs,i(r) = sum_a int_Omega dPhi/dn_a(r') w_i^a(r - r') dr'
+ * psi is zero off Omega (zero extension).  Output mu[i*N + p].           */
+void oracle_mu_hs(const oracle_problem *p, const double *psi, double *mu)
+{
+    grid_t g = cdft_grid(p);
+    long N = (long)p->nx * p->ny * p->nz;
+    for (int i = 0; i < p->s; ++i) {
+        double R = p->R[i];
+        nodes_t sh = make_nodes(0, 0.0, R, p->nmu, p->ntheta, p->nr);
+        nodes_t ba = make_nodes(1, 0.0, R, p->nmu, p->ntheta, p->nr);
+        double c0 = 1.0 / (4.0 * M_PI * R * R), c1 = 1.0 / (4.0 * M_PI * R);
+#pragma omp parallel for schedule(static)
+        for (long pt = 0; pt < N; ++pt) {
+            double X = (double)(pt % p->nx);
+            double Y = (double)((pt / p->nx) % p->ny);
+            double Z = (double)(pt / ((long)p->nx * p->ny));
+            double acc = 0.0;
+            for (int q = 0; q < sh.n; ++q) {
+                double x = X - sh.px[q], y = Y - sh.py[q], z = Z - sh.pz[q];
+                double s0 = interp(&g, psi + 0 * N, x, y, z);
+                double s1 = interp(&g, psi + 1 * N, x, y, z);
+                double s2 = interp(&g, psi + 2 * N, x, y, z);
+                double v1x = interp(&g, psi + 4 * N, x, y, z);
+                double v1y = interp(&g, psi + 5 * N, x, y, z);
+                double v1z = interp(&g, psi + 6 * N, x, y, z);
+                double v2x = interp(&g, psi + 7 * N, x, y, z);
+                double v2y = interp(&g, psi + 8 * N, x, y, z);
+                double v2z = interp(&g, psi + 9 * N, x, y, z);
+                double scal = c0 * s0 + c1 * s1 + s2;
+                double vec = sh.ux[q] * (c1 * v1x + v2x) + sh.uy[q] * (c1 * v1y + v2y)
+                             + sh.uz[q] * (c1 * v1z + v2z);
+                acc += sh.w[q] * (scal + vec);
+            }
+            for (int q = 0; q < ba.n; ++q)
+                acc += ba.w[q] * interp(&g, psi + 3 * N, X - ba.px[q], Y - ba.py[q], Z - ba.pz[q]);
+            mu[i * N + pt] = acc;
+        }
+        free_nodes(&sh);
+        free_nodes(&ba);
+    }
+}
+
+/* Stationary-site density, Sec 2.3.2: normalised Gaussians at the sites,
+ * evaluated exactly at grid nodes.  On periodic axes the sites repeat with the
+ * box, so every image whose Gaussian does not underflow (alpha d^2 < 800) is
+ * summed.                                                                  */
+void oracle_site_density(const oracle_problem *p, double *rho_s)
+{
+    long N = (long)p->nx * p->ny * p->nz;
+    int n[3] = {p->nx, p->ny, p->nz};
+    double a = p->site_alpha;
+    double norm = pow(a / M_PI, 1.5);
+    double reach = sqrt(800.0 / a);
+    int m[3];
+    for (int d = 0; d < 3; ++d) m[d] = (p->bc[d] == 0) ? (int)ceil(reach / n[d]) + 1 : 0;
+#pragma omp parallel for schedule(static)
+    for (long pt = 0; pt < N; ++pt) {
+        double r[3] = {(double)(pt % p->nx), (double)((pt / p->nx) % p->ny),
+                       (double)(pt / ((long)p->nx * p->ny))};
+        double acc = 0.0;
+        for (int k = 0; k < p->nsites; ++k)
+            for (int iz = -m[2]; iz <= m[2]; ++iz)
+                for (int iy = -m[1]; iy <= m[1]; ++iy)
+                    for (int ix = -m[0]; ix <= m[0]; ++ix) {
+                        double dx = r[0] - p->sites[3 * k + 0] - (double)ix * n[0];
+                        double dy = r[1] - p->sites[3 * k + 1] - (double)iy * n[1];
+                        double dz = r[2] - p->sites[3 * k + 2] - (double)iz * n[2];
+                        acc += exp(-a * (dx * dx + dy * dy + dz * dz));
+                    }
+        rho_s[pt] = norm * acc;
+    }
+}
+
+/* Square-well chemical potential, Sec 2.3.2:
+ *   mu_sh,i(r) = 1/2 int rho_s(r') Phi_is(|r - r'|) dr',
+ * Phi_is = -eps_i on the shell well_inner <= |r-r'| <= well_outer and 0
+ * beyond; the hard core is FMT's.  Output mu_sh[i*N + p].                */
+void oracle_mu_sh(const oracle_problem *p, const double *rho_s, double *mu_sh)
+{
+    grid_t g = cdft_grid(p);
+    long N = (long)p->nx * p->ny * p->nz;
+    double half = p->sw_half ? 0.5 : 1.0;
+    nodes_t ws = make_nodes(2, p->well_inner, p->well_outer, p->w_nmu, p->w_ntheta, p->w_nr);
+    for (int i = 0; i < p->s; ++i) {
+        double eps = p->depth ? p->depth[i] : 0.0;
+        if (eps == 0.0 || p->nsites == 0) {
+            memset(mu_sh + i * N, 0, sizeof(double) * N);
+            continue;
+        }
+#pragma omp parallel for schedule(static)
+        for (long pt = 0; pt < N; ++pt) {
+            double X = (double)(pt % p->nx);
+            double Y = (double)((pt / p->nx) % p->ny);
+            double Z = (double)(pt / ((long)p->nx * p->ny));
+            double acc = 0.0;
+            for (int q = 0; q < ws.n; ++q)
+                acc += ws.w[q] * interp(&g, rho_s, X + ws.px[q], Y + ws.py[q], Z + ws.pz[q]);
+            mu_sh[i * N + pt] = half * (-eps) * acc;
+        }
+    }
+    free_nodes(&ws);
+}
+
+/* mu_ex,i = mu_hs,i + mu_sh,i (Sec 2.3).  Returns the packing-error count. */
+long oracle_excess_mu(const oracle_problem *p, const double *rho, double *mu)
+{
+    long N = (long)p->nx * p->ny * p->nz;
+    double *n = malloc(sizeof(double) * 10 * N);
+    double *psi = malloc(sizeof(double) * 10 * N);
+    double *rs = malloc(sizeof(double) * N);
+    double *msh = malloc(sizeof(double) * p->s * N);
+    oracle_weighted_densities(p, rho, n, 0, 0.0, 0);
+    long bad = oracle_dphi(N, n, psi);
+    oracle_mu_hs(p, psi, mu);
+    oracle_site_density(p, rs);
+    oracle_mu_sh(p, rs, msh);
+    for (long k = 0; k < p->s * N; ++k) mu[k] += msh[k];
+    free(n); free(psi); free(rs); free(msh);
+    return bad;
+}
+
+/* Bulk mu_ex of the uniform reservoir: dPhi/dn_a at the bulk weighted
+ * densities times the weight integrals (1, R, 4 pi R^2, 4 pi R^3 / 3).    */
+void oracle_bulk_mu(int s, const double *R, const double *rho_b, double *mu_b)
+{
+    double a[10] = {0}, psi[10];
+    for (int i = 0; i < s; ++i) {
+        a[0] += rho_b[i];
+        a[1] += rho_b[i] * R[i];
+        a[2] += rho_b[i] * 4.0 * M_PI * R[i] * R[i];
+        a[3] += rho_b[i] * 4.0 * M_PI * R[i] * R[i] * R[i] / 3.0;
+    }
+    oracle_dphi(1, a, psi);
+    for (int i = 0; i < s; ++i)
+        mu_b[i] = psi[0] + R[i] * psi[1] + 4.0 * M_PI * R[i] * R[i] * psi[2]
+                  + 4.0 * M_PI * R[i] * R[i] * R[i] / 3.0 * psi[3];
+}
+
+/* ------------------------------------------------------------------ */
+/* 7-point finite-difference operators (Sec 3.1).  Unknowns sit on planes
+ * k = 0..nz-1; the Dirichlet planes k = -1 and k = nz carry the boundary
+ * values.  x and y are periodic (bc 0) or no-flux (bc 2).
+ * The operator is  (A u)_p = sum_faces c_f (u_p - u_nbr)  with the Dirichlet
+ * neighbour values moved to the right-hand side.  Face coefficients:
+ *   cx[p] = face between p and its +x neighbour (0 across a no-flux wall),
+ *   cy[p], cz[p] likewise; cz_lo[p] for plane 0 and the lower Dirichlet
+ *   plane, cz[p] for the top plane is the face to the upper Dirichlet plane. */
+typedef struct {
+    int nx, ny, nz, bcx, bcy;
+    double *cx, *cy, *cz, *czlo;
+} fdop_t;
+
+static long nbr(const fdop_t *A, long p, int axis, int dir, int *ok)
+{
+    int i = (int)(p % A->nx), j = (int)((p / A->nx) % A->ny), k = (int)(p / ((long)A->nx * A->ny));
+    int n = axis == 0 ? A->nx : (axis == 1 ? A->ny : A->nz);
+    int c = axis == 0 ? i : (axis == 1 ? j : k);
+    int bc = axis == 0 ? A->bcx : (axis == 1 ? A->bcy : 1);
+    c += dir;
+    *ok = 1;
+    if (c < 0 || c >= n) {
+        if (bc == 0) c = (c + n) % n;
+        else { *ok = 0; return -1; }
+    }
+    if (axis == 0) i = c; else if (axis == 1) j = c; else k = c;
+    return ((long)k * A->ny + j) * A->nx + i;
+}
+
+/* coefficient of the face between p and its neighbour in (axis, dir) */
+static double face(const fdop_t *A, long p, int axis, int dir)
+{
+    int ok;
+    if (axis == 2) {
+        int k = (int)(p / ((long)A->nx * A->ny));
+        if (dir < 0) return k == 0 ? A->czlo[p] : A->cz[nbr(A, p, 2, -1, &ok)];
+        return A->cz[p];
+    }
+    double *c = axis == 0 ? A->cx : A->cy;
+    if (dir > 0) return c[p];
+    long q = nbr(A, p, axis, -1, &ok);
+    return ok ? c[q] : 0.0;
+}
+
+static void fd_apply(const fdop_t *A, const double *u, double *out)
+{
+    long N = (long)A->nx * A->ny * A->nz;
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < N; ++p) {
+        double acc = 0.0;
+        for (int axis = 0; axis < 3; ++axis)
+            for (int dir = -1; dir <= 1; dir += 2) {
+                double c = face(A, p, axis, dir);
+                if (c == 0.0) continue;
+                int ok;
+                long q = nbr(A, p, axis, dir, &ok);
+                acc += c * (u[p] - (ok ? u[q] : 0.0));
+            }
+        out[p] = acc;
+    }
+}
+
+static void fd_diag(const fdop_t *A, double *dg)
+{
+    long N = (long)A->nx * A->ny * A->nz;
+    for (long p = 0; p < N; ++p) {
+        double acc = 0.0;
+        for (int axis = 0; axis < 3; ++axis)
+            for (int dir = -1; dir <= 1; dir += 2) acc += face(A, p, axis, dir);
+        dg[p] = acc;
+    }
+}
+
+static double dot(long N, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long k = 0; k < N; ++k) s += a[k] * b[k];
+    return s;
+}
+
+/* Jacobi-preconditioned conjugate gradients; x holds the initial guess on
+ * entry.  Stops at ||r||_2 <= tol ||b||_2.  Returns the iteration count.  */
+static int pcg(const fdop_t *A, const double *b, double *x, double tol, int maxit, double *relres)
+{
+    long N = (long)A->nx * A->ny * A->nz;
+    double *r = malloc(sizeof(double) * N), *z = malloc(sizeof(double) * N);
+    double *pd = malloc(sizeof(double) * N), *Ap = malloc(sizeof(double) * N);
+    double *dg = malloc(sizeof(double) * N);
+    fd_diag(A, dg);
+    fd_apply(A, x, Ap);
+    for (long k = 0; k < N; ++k) r[k] = b[k] - Ap[k];
+    double bn = sqrt(dot(N, b, b));
+    if (bn == 0.0) bn = 1.0;
+    for (long k = 0; k < N; ++k) { z[k] = r[k] / dg[k]; pd[k] = z[k]; }
+    double rz = dot(N, r, z);
+    int it = 0;
+    double rn = sqrt(dot(N, r, r));
+    while (rn > tol * bn && it < maxit) {
+        fd_apply(A, pd, Ap);
+        double alpha = rz / dot(N, pd, Ap);
+        for (long k = 0; k < N; ++k) { x[k] += alpha * pd[k]; r[k] -= alpha * Ap[k]; }
+        for (long k = 0; k < N; ++k) z[k] = r[k] / dg[k];
+        double rz2 = dot(N, r, z);
+        double beta = rz2 / rz;
+        rz = rz2;
+        for (long k = 0; k < N; ++k) pd[k] = z[k] + beta * pd[k];
+        rn = sqrt(dot(N, r, r));
+        ++it;
+    }
+    if (relres) *relres = rn / bn;
+    free(r); free(z); free(pd); free(Ap); free(dg);
+    return it;
+}
+
+static fdop_t fd_alloc(const oracle_problem *p)
+{
+    fdop_t A;
+    long N = (long)p->nx * p->ny * p->nz;
+    A.nx = p->nx; A.ny = p->ny; A.nz = p->nz; A.bcx = p->bc[0]; A.bcy = p->bc[1];
+    A.cx = calloc(4 * N, sizeof(double));
+    A.cy = A.cx + N; A.cz = A.cy + N; A.czlo = A.cz + N;
+    return A;
+}
+
+/* Poisson (Sec 2.1) in reduced units:  -lap phi = 4 pi lB (rho_f + sum q rho),
+ * unit face coefficients (h = 1), no-flux walls carry a zero coefficient.  */
+static void poisson_operator(const oracle_problem *p, fdop_t *A)
+{
+    long N = (long)p->nx * p->ny * p->nz;
+    for (long k = 0; k < N; ++k) {
+        int i = (int)(k % p->nx), j = (int)((k / p->nx) % p->ny);
+        A->cx[k] = (p->bc[0] == 2 && i == p->nx - 1) ? 0.0 : 1.0;
+        A->cy[k] = (p->bc[1] == 2 && j == p->ny - 1) ? 0.0 : 1.0;
+        A->cz[k] = 1.0;
+        A->czlo[k] = 1.0;
+    }
+}
+
+/* Solve the Poisson equation for the given densities; phi holds the initial
+ * guess on entry.  Exposed for the linear-solve pins.                      */
+int oracle_poisson(const oracle_problem *p, const double *rho, double *phi, double *relres)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    fdop_t A = fd_alloc(p);
+    poisson_operator(p, &A);
+    double *b = malloc(sizeof(double) * N);
+    for (long k = 0; k < N; ++k) {
+        double c = p->rho_f ? p->rho_f[k] : 0.0;
+        for (int i = 0; i < p->s; ++i) c += p->q[i] * rho[i * N + k];
+        b[k] = 4.0 * M_PI * p->lB * c;
+    }
+    for (long k = 0; k < plane; ++k) {
+        b[k] += A.czlo[k] * p->phi_lo;
+        b[N - plane + k] += A.cz[N - plane + k] * p->phi_hi;
+    }
+    int it = pcg(&A, b, phi, p->lin_tol, p->lin_max_iter, relres);
+    free(b); free(A.cx);
+    return it;
+}
+
+/* Slotboom Nernst-Planck solve (Sec 2.1 and 3.1) for species i:
+ *   Dbar = D exp(-(q phi + mu)),  face coefficient = harmonic mean of the two
+ *   node values, Dirichlet rhobar on the z faces from the reservoir
+ *   rhobar_face = rho_b exp(q phi_face + mu_b), Dbar_face from phi_face, mu_b.
+ * rhobar holds the initial guess on entry.                                  */
+int oracle_np(const oracle_problem *p, int i, const double *phi, const double *mu, double mu_b,
+              double *rhobar, double *relres)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    double Di = p->D ? p->D[i] : 1.0;
+    int qi = p->q[i];
+    fdop_t A = fd_alloc(p);
+    double *Db = malloc(sizeof(double) * N), *b = calloc(N, sizeof(double));
+    for (long k = 0; k < N; ++k) Db[k] = Di * exp(-(qi * phi[k] + mu[k]));
+    double Dlo = Di * exp(-(qi * p->phi_lo + mu_b)), Dhi = Di * exp(-(qi * p->phi_hi + mu_b));
+    double rlo = p->rho_b[i] * exp(qi * p->phi_lo + mu_b), rhi = p->rho_b[i] * exp(qi * p->phi_hi + mu_b);
+    for (long k = 0; k < N; ++k) {
+        int ok;
+        int x = (int)(k % p->nx), y = (int)((k / p->nx) % p->ny), z = (int)(k / plane);
+        long qx = nbr(&A, k, 0, +1, &ok);
+        A.cx[k] = (p->bc[0] == 2 && x == p->nx - 1) ? 0.0 : 2.0 * Db[k] * Db[qx] / (Db[k] + Db[qx]);
+        long qy = nbr(&A, k, 1, +1, &ok);
+        A.cy[k] = (p->bc[1] == 2 && y == p->ny - 1) ? 0.0 : 2.0 * Db[k] * Db[qy] / (Db[k] + Db[qy]);
+        if (z == p->nz - 1) A.cz[k] = 2.0 * Db[k] * Dhi / (Db[k] + Dhi);
+        else A.cz[k] = 2.0 * Db[k] * Db[k + plane] / (Db[k] + Db[k + plane]);
+        A.czlo[k] = (z == 0) ? 2.0 * Db[k] * Dlo / (Db[k] + Dlo) : 0.0;
+    }
+    for (long k = 0; k < plane; ++k) {
+        b[k] += A.czlo[k] * rlo;
+        b[N - plane + k] += A.cz[N - plane + k] * rhi;
+    }
+    int it = pcg(&A, b, rhobar, p->lin_tol, p->lin_max_iter, relres);
+    free(Db); free(b); free(A.cx);
+    return it;
+}
+
+/* Discrete z-flux of species i through the face between planes k and k+1
+ * (k = -1 .. nz-1), summed over the plane: J = sum c_f (rhobar_k - rhobar_k+1). */
+void oracle_np_flux(const oracle_problem *p, int i, const double *phi, const double *mu, double mu_b,
+                    const double *rhobar, double *flux /* nz+1 */)
+{
+    long plane = (long)p->nx * p->ny;
+    double Di = p->D ? p->D[i] : 1.0;
+    int qi = p->q[i];
+    double Dlo = Di * exp(-(qi * p->phi_lo + mu_b)), Dhi = Di * exp(-(qi * p->phi_hi + mu_b));
+    double rlo = p->rho_b[i] * exp(qi * p->phi_lo + mu_b), rhi = p->rho_b[i] * exp(qi * p->phi_hi + mu_b);
+    for (int kf = -1; kf < p->nz; ++kf) {
+        double J = 0.0;
+        for (long c = 0; c < plane; ++c) {
+            double Da, Dbv, ra, rb;
+            if (kf < 0) { Da = Dlo; ra = rlo; }
+            else { long a = kf * plane + c; Da = Di * exp(-(qi * phi[a] + mu[a])); ra = rhobar[a]; }
+            if (kf + 1 >= p->nz) { Dbv = Dhi; rb = rhi; }
+            else { long b = (kf + 1) * plane + c; Dbv = Di * exp(-(qi * phi[b] + mu[b])); rb = rhobar[b]; }
+            J += 2.0 * Da * Dbv / (Da + Dbv) * (ra - rb);
+        }
+        flux[kf + 1] = J;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Relaxed Gummel iteration (Sec 3.2):
+ *   mu_ex from rho^{n-1}; Poisson -> phi*; phi^n = l1 phi* + (1-l1) phi^{n-1};
+ *   per species Slotboom NP solve with Dbar from phi^n and mu_ex -> rhobar;
+ *   rho* = rhobar exp(-(q phi^n + mu_ex)); rho^n = l2 rho* + (1-l2) rho^{n-1}
+ *   (rho_mix 0, as printed) or rho^n = rho^{n-1} (rho* / rho^{n-1})^l2
+ *   (rho_mix 1: the same update to first order, kept positive and bounded for
+ *   the large first steps of a dense fluid next to a hard wall);
+ *   stop when max(|dphi|_inf, max_i |drho_i|_inf / rho_b,i) < tol.
+ * Initial state (when phi0/rho0 are NULL): phi linear in z between the
+ * Dirichlet values, rho = rho_b.  Returns 0 converged, 1 not converged,
+ * 2 packing error.  hist (max_iter entries, nullable) gets the residuals. */
+int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho0,
+                  double *phi, double *rho, int *iters, double *hist, long *lin_iters)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    int s = p->s;
+    double *mu = malloc(sizeof(double) * s * N);
+    double *phis = malloc(sizeof(double) * N);
+    double *rb = malloc(sizeof(double) * N);
+    double *mub = malloc(sizeof(double) * s);
+    double *rho_new = malloc(sizeof(double) * s * N);
+    oracle_bulk_mu(s, p->R, p->rho_b, mub);
+    if (phi0) memcpy(phi, phi0, sizeof(double) * N);
+    else
+        for (long k = 0; k < N; ++k) {
+            int z = (int)(k / plane);
+            phi[k] = p->phi_lo + (p->phi_hi - p->phi_lo) * (z + 1.0) / (p->nz + 1.0);
+        }
+    if (rho0) memcpy(rho, rho0, sizeof(double) * s * N);
+    else
+        for (int i = 0; i < s; ++i)
+            for (long k = 0; k < N; ++k) rho[i * N + k] = p->rho_b[i];
+    long lin = 0;
+    int status = 1, n;
+    double rr = 0.0;
+    for (n = 1; n <= p->max_iter; ++n) {
+        if (oracle_excess_mu(p, rho, mu) > 0) { status = 2; break; }
+        memcpy(phis, phi, sizeof(double) * N);
+        lin += oracle_poisson(p, rho, phis, 0);
+        double dphi = 0.0;
+        for (long k = 0; k < N; ++k) {
+            double v = p->lambda_phi * phis[k] + (1.0 - p->lambda_phi) * phi[k];
+            double d = fabs(v - phi[k]);
+            if (d > dphi) dphi = d;
+            phi[k] = v;
+        }
+        rr = dphi;
+        for (int i = 0; i < s; ++i) {
+            const double *mui = mu + i * N;
+            /* initial guess: Slotboom variable of the current density */
+            for (long k = 0; k < N; ++k) rb[k] = rho[i * N + k] * exp(p->q[i] * phi[k] + mui[k]);
+            lin += oracle_np(p, i, phi, mui, mub[i], rb, 0);
+            double drho = 0.0;
+            for (long k = 0; k < N; ++k) {
+                double rs = rb[k] * exp(-(p->q[i] * phi[k] + mui[k]));
+                double v = p->rho_mix == 1
+                               ? rho[i * N + k] * exp(p->lambda_rho * log(rs / rho[i * N + k]))
+                               : p->lambda_rho * rs + (1.0 - p->lambda_rho) * rho[i * N + k];
+                double d = fabs(v - rho[i * N + k]) / p->rho_b[i];
+                if (d > drho) drho = d;
+                rho_new[i * N + k] = v;
+            }
+            if (drho > rr) rr = drho;
+        }
+        memcpy(rho, rho_new, sizeof(double) * s * N);
+        if (hist) hist[n - 1] = rr;
+        if (rr < p->tol) { status = 0; break; }
+    }
+    if (iters) *iters = n > p->max_iter ? p->max_iter : n;
+    if (lin_iters) *lin_iters = lin;
+    free(mu); free(phis); free(rb); free(mub); free(rho_new);
+    return status;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
