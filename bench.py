@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the mu_ex hot path: one step = one evaluation of the cDFT
+excess chemical potentials (FMT hard spheres, Rosenfeld) of a 128^3 grid with
+three species of radius 1.5h, 2h, 3h (packing 0.1 each, densities rho_b x
+lognormal(0, 0.1), seed 2), zero-padded to 256^3, through the C ABI
+(pnp_excess_mu_device) with inputs resident in device memory.
+
+Prints one JSON line (rank 0).  Metric: mu_ex Gpoints/s = output grid points /
+time.  The headline is the FP64 path; the FP32-FFT variant (FP64 derivatives)
+is reported beside it.  `e2e` times pnp_excess_mu with host buffers (pinned),
+host->device and device->host copies inside the timed region.
+
+`--impl reference` times the FP64 CPU oracle (direct real-space quadrature
+sums) on a bounded sample of the same workload; it is the reference arm.
+
+Multi-GPU: the workload does not shard, so N ranks run N independent replicas
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EDGE = 128
+PAD = 256
+SPECIES = 3
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=40, help="edge of the oracle sample box")
+    ap.add_argument("--ref-sample", type=int, default=24, help="edge of the reference-arm sample box")
+    return ap.parse_args()
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(world, v):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sub_box(spec, rho, m):
+    import copy
+    s2 = copy.copy(spec)
+    s2.nx = s2.ny = s2.nz = m
+    s2.fft_len = (0, 0, 0)
+    import numpy as np
+    return s2, np.ascontiguousarray(rho[:, :m, :m, :m])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def stage_bytes(name, dims, cs, s):
+    """Algorithmic DRAM bytes of one launch of a pipeline stage: every array
+    element the pass must read plus every element it must write (complex
+    element cs bytes, real FP64 fields 8 bytes), spectra octants once."""
+    nx, ny, nz, Lx, Ly, Lz = dims
+    Wx = Lx // 2 + 1
+    A1 = nz * ny * Wx * cs           # one field, x-spectra
+    B1 = nz * Ly * Wx * cs           # one field, y-spectra
+    R1 = nx * ny * nz * 8            # one real field
+    oct_ = (Lx // 2 + 1) * (Ly // 2 + 1) * (Lz // 2 + 1) * (cs // 2) * 5 * s
+    return {
+        "x_fwd": s * (R1 + A1),
+        "y_fwd": s * (A1 + B1),
+        "z_mac": s * B1 + 10 * B1 + oct_,
+        "y_inv": 10 * (B1 + A1),
+        "x_fused": 10 * (A1 + A1),
+        "y_fwd_psi": 10 * (A1 + B1),
+        "z_back": 10 * B1 + s * B1 + oct_,
+        "y_inv_mu": s * (B1 + A1),
+        "x_inv": s * (A1 + R1),
+    }[name]
+
+
+def stage_flops(name, dims, s):
+    """Algorithmic floating-point operations of one launch of a stage: 5 L log2 L
+    per complex transform of length L (a pair of real lines shares one), plus
+    4 flops per species per output element of each spectral multiply-add and
+    about 60 per point for the ten FMT derivatives."""
+    import math
+    nx, ny, nz, Lx, Ly, Lz = dims
+    Wx = Lx // 2 + 1
+    npairs = (ny + 1) // 2
+    fx, fy, fz = (5 * L * math.log2(L) for L in (Lx, Ly, Lz))
+    cols = Ly * Wx
+    mac = 10 * s * 4 * Lz
+    return {
+        "x_fwd": s * nz * npairs * fx,
+        "y_fwd": s * nz * Wx * fy,
+        "z_mac": cols * ((s + 10) * fz + mac),
+        "y_inv": 10 * nz * Wx * fy,
+        "x_fused": nz * npairs * 20 * fx + nx * ny * nz * 60,
+        "y_fwd_psi": 10 * nz * Wx * fy,
+        "z_back": cols * ((s + 10) * fz + mac),
+        "y_inv_mu": s * nz * Wx * fy,
+        "x_inv": s * nz * npairs * fx,
+    }[name]
+
+
+# FP64 peak of the part, from its unit counts and clock: 152 SMs x 2 FP64 FMA
+# per clock x 2 flops x 2.07 GHz (an FMA-chain probe measured 1.195 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle
+    from workloads import mu_microbench
+    spec, rho = mu_microbench(N_EDGE, fft_len=PAD)
+    m = args.ref_sample
+    s2, r2 = sub_box(spec, rho, m)
+    for _ in range(args.warmup):
+        oracle.excess_mu(s2, r2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.excess_mu(s2, r2)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = m ** 3 / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "mu_ex Gpoints/s", "value": v, "unit": "Gpoints/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"mu_ex {N_EDGE}^3 x {SPECIES} species (R 1.5/2/3 h), zero-padded {PAD}^3",
+                   "sample": f"{m}^3 sub-box per step", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{m}^3 sub-box of the {N_EDGE}^3 workload, full mu_ex per step"},
+        "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1407_0674_gb300 import build as lb
+    from paper_1407_0674_gb300 import pnp
+    from workloads import mu_microbench
+
+    torch.cuda.set_device(local)
+    lb.build()
+    spec, rho = mu_microbench(N_EDGE, fft_len=PAD)
+    npts = spec.npoints
+    P = pnp.Problem(spec)
+    info = P.info()
+    d_rho = torch.from_numpy(rho).cuda()
+    d_mu = torch.empty_like(d_rho)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # a dedicated stream: the library, the L2 flush and the timing events all
+    # run on it (handle 0 would mean the library's own stream)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    torch.cuda.set_stream(stream)
+
+    def step(prec):
+        P.excess_mu_device(d_rho, d_mu, precision=prec, stream=sh)
+
+    for prec in ("fp64", "fp32"):
+        for _ in range(args.warmup):
+            step(prec)
+    torch.cuda.synchronize()
+    rc = P.status()
+    if rc != 0:
+        raise RuntimeError(f"device status {rc} after warm-up")
+
+    results = {}
+    clocks = None
+    for prec in ("fp64", "fp32"):
+        P.stage_times()                      # reset the record
+        P.stage_timing(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sampler = ClockSampler(local) if prec == "fp64" else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()                    # evict L2 between steps (outside the events)
+            ev[k][0].record(stream)
+            step(prec)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        if sampler:
+            clocks = sampler.stop()
+        P.stage_timing(False)
+        st = P.stage_times()
+        rc = P.status()
+        if rc != 0:
+            raise RuntimeError(f"device status {rc}")
+        ms = [a.elapsed_time(b) for a, b in ev]
+        ms_step = reduce_max(world, sum(ms) / len(ms))
+        results[prec] = {"ms": ms_step, "stages": st}
+
+    # end to end through the host-pointer entry point, pinned host buffers
+    h_rho = torch.from_numpy(rho).pin_memory().numpy()
+    h_mu = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
+    lib = pnp.lib()
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    for _ in range(2):
+        lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), 0)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), 0)
+        if r != 0:
+            raise RuntimeError(f"pnp_excess_mu {r}")
+    e2e_ms = reduce_max(world, (time.perf_counter() - t0) / args.steps * 1e3)
+    barrier(world)
+
+    # roofline of the dominant FP64 kernel and of the FP32 variant's
+    peak, peak_kind = measured_peaks()
+    dims = (spec.nx, spec.ny, spec.nz) + tuple(info["fft_len"])
+
+    def roof(prec):
+        st = results[prec]["stages"]
+        cs = 16 if prec == "fp64" else 8
+        name = max(st, key=lambda k: st[k][0])
+        tot, n = st[name]
+        avg = tot / max(n, 1)
+        share = tot / sum(v[0] for v in st.values())
+        b = stage_bytes(name, dims, cs, SPECIES)
+        f = stage_flops(name, dims, SPECIES)
+        hbm = {"achieved_gbs": b / (avg * 1e-3) / 1e9, "bytes_per_launch": b}
+        hbm["frac"] = hbm["achieved_gbs"] / peak
+        if prec == "fp64":
+            ach = f / (avg * 1e-3) / 1e12
+            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "flops_per_launch": f,
+                    "avg_launch_ms": avg, "share_of_step": share,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz", "hbm": hbm}
+        ach = b / (avg * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "bytes_per_launch": b, "avg_launch_ms": avg,
+                "share_of_step": share, "peak_source": peak_kind,
+                "fp32_tflops": f / (avg * 1e-3) / 1e12}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle
+        m = args.cpu_sample
+        s2, r2 = sub_box(spec, rho, m)
+        t0 = time.perf_counter()
+        oracle.excess_mu(s2, r2)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m ** 3 / dt / 1e9, "unit": "Gpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{m}^3 sub-box of the {N_EDGE}^3 workload (same radii and densities), one full mu_ex, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        v64 = world * npts / (results["fp64"]["ms"] * 1e-3) / 1e9
+        v32 = world * npts / (results["fp32"]["ms"] * 1e-3) / 1e9
+        launches = sum(n for _, n in results["fp64"]["stages"].values())
+        line = {
+            "metric": "mu_ex Gpoints/s", "value": v64, "unit": "Gpoints/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["fp64"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"mu_ex {N_EDGE}^3 x {SPECIES} species (R 1.5/2/3 h, packing 0.1 each, "
+                                   f"lognormal(0,0.1) seed 2), zero-padded {PAD}^3",
+                       "fft_len": list(info["fft_len"]), "parallelism": f"replicas x{world}",
+                       "l2": "flushed before each step (256 MB write)"},
+            "e2e": {"value": world * npts / (e2e_ms * 1e-3) / 1e9, "unit": "Gpoints/s",
+                    "h2d_bytes_per_step": int(rho.nbytes), "d2h_bytes_per_step": int(rho.nbytes),
+                    "ms_per_step": e2e_ms},
+            "roofline": roof("fp64"),
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "variants": {"fp32_fft": {"value": v32, "unit": "Gpoints/s", "ms_per_step": results["fp32"]["ms"],
+                                      "dtype": "f32 FFT / f64 derivatives", "roofline": roof("fp32")}},
+            "stages_ms": {p: {k: v[0] / max(v[1], 1) for k, v in results[p]["stages"].items()}
+                          for p in results},
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

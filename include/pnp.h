@@ -1,0 +1,222 @@
+/*
+ * pnp.h -- C ABI of the GB300 PNP-cDFT library (libpnp_gb300.so).
+ *
+ * The library evaluates the cDFT excess chemical potentials of a mixture of
+ * charged hard spheres on a uniform grid with zero-padded FFT convolutions, and
+ * runs the relaxed Gummel iteration of the steady Poisson-Nernst-Planck system
+ * around it on one GPU, following Meng, Zheng, Lin & Sushko, "Numerical
+ * solution of 3D Poisson-Nernst-Planck equations coupled with classical density
+ * functional theory ..." (arXiv:1407.0674).
+ *
+ * Conventions (all entry points):
+ *  - Units are reduced: lengths in grid spacings h, densities in h^-3,
+ *    potentials in kT/e, chemical potentials in kT.  The Bjerrum length is
+ *    derived from temperature_K, eps_r and h_nm (Sec 2.3.3, Table 1).
+ *  - Fields are C order [species][z][y][x] (x fastest), FP64 at the boundary
+ *    for every precision variant.
+ *  - Every pointer argument is owned by the caller.  Inputs are copied before
+ *    the call returns; the library keeps no caller pointer.  Handles are opaque.
+ *  - A pnp_problem is used by one host thread at a time.  A pnp_server is safe
+ *    for concurrent pnp_submit / pnp_poll.
+ *  - Errors are negative return codes (pnp_error_string gives a message); no
+ *    entry point aborts the process.  Device faults surface as PNP_ERR_CUDA.
+ *  - Entry points whose name ends in _device take device pointers and a
+ *    cudaStream_t (passed as void*, NULL = the problem's own stream); they
+ *    enqueue work and return without synchronising.  pnp_status() then
+ *    synchronises and reports deferred device-side errors.
+ */
+#ifndef PNP_GB300_H
+#define PNP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    PNP_OK = 0,
+    PNP_PENDING = 1,               /* pnp_poll: not finished yet */
+    PNP_ERR_INVALID = -1,          /* bad argument or descriptor */
+    PNP_ERR_NOMEM = -2,            /* device or host allocation failed */
+    PNP_ERR_CUDA = -3,             /* CUDA runtime error */
+    PNP_ERR_NOT_CONVERGED = -4,    /* Gummel reached max_iter */
+    PNP_ERR_PACKING = -5,          /* n3 >= 1 or a non-finite value in mu_ex */
+    PNP_ERR_OVERFLOW = -6,         /* Slotboom exponential overflowed (Sec 2.1) */
+    PNP_ERR_BUSY = -7,             /* server: over the HBM budget or queue full */
+    PNP_ERR_TIMEOUT = -8,          /* a bounded device wait gave up */
+    PNP_ERR_UNKNOWN_TICKET = -9    /* server: no such request */
+};
+
+/* boundary type per axis.  For the cDFT integrals every non-periodic axis is
+ * zero-extended (Sec 3.5).  The Gummel solve needs z = DIRICHLET and x, y
+ * PERIODIC or NOFLUX (Sec 2.2, with the paper's y axis as z). */
+enum { PNP_BC_PERIODIC = 0, PNP_BC_DIRICHLET = 1, PNP_BC_NOFLUX = 2 };
+
+/* arithmetic of the FFT convolutions; the FMT derivatives, the Gummel update,
+ * its norms and the linear solves are FP64 in every variant. */
+enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1 };
+
+/* density relaxation of the Gummel update (Sec 3.2): the printed linear form
+ * rho <- l2 rho* + (1 - l2) rho, or the geometric form
+ * rho <- rho (rho* / rho)^l2, equal to first order and positive for large steps. */
+enum { PNP_MIX_LINEAR = 0, PNP_MIX_GEOMETRIC = 1 };
+
+typedef struct {
+    int nx, ny, nz;                /* grid points per axis */
+    int bc[3];                     /* PNP_BC_* for x, y, z */
+    int nspecies;                  /* mobile species s >= 1 */
+    const int *valence;            /* [s] q_i (Sec 2.1) */
+    const double *radius;          /* [s] hard-sphere radius R_i (h), Sec 2.3.1 */
+    const double *rho_bulk;        /* [s] reservoir density (h^-3), Sec 2.2 */
+    const double *diffusivity;     /* [s] D_i, NULL -> 1 */
+    const double *well_depth;      /* [s] square-well depth eps_i (kT), NULL -> 0, Sec 2.3.2 */
+    double well_inner, well_outer; /* square-well shell radii sigma_ab and gamma*sigma_ab (h) */
+    int nsites;                    /* stationary sites (Sec 2.3.2) */
+    const double *site_xyz;        /* [nsites][3] site centres in grid-index units */
+    double site_alpha;             /* Gaussian exponent of the site density (h^-2) */
+    const double *rho_fixed;       /* [nz][ny][nx] fixed charge (e h^-3), NULL -> 0 */
+    double temperature_K, eps_r;   /* -> Bjerrum length (Sec 2.3.3) */
+    double h_nm;                   /* grid spacing in nm */
+    double phi_lo, phi_hi;         /* Dirichlet potentials on the z = 0 and z = top faces (kT/e) */
+    double lambda_phi, lambda_rho; /* Gummel relaxation lambda_1, lambda_2 (Sec 3.2) */
+    int rho_mix;                   /* PNP_MIX_* */
+    double tol;                    /* stop when max(|dphi|, max_i |drho_i| / rho_b,i) < tol */
+    int max_iter;                  /* Gummel iteration cap */
+    int quad_nmu, quad_ntheta, quad_nr;   /* FMT quadrature counts, 0 = default rule */
+    int well_nmu, well_ntheta, well_nr;   /* square-well quadrature counts, 0 = default */
+    int sw_half;                   /* 1: mu_sh keeps the factor 1/2 of Sec 2.3.2 */
+    int fft_len[3];                /* padded FFT length per axis, 0 = smallest legal */
+    int precision;                 /* PNP_PREC_FP64 / FP32: default for the calls below */
+    double lin_tol;                /* relative residual of the linear solves, 0 -> 1e-12 */
+    unsigned flags;                /* reserved, 0 */
+} pnp_problem_desc;
+
+typedef struct {
+    int status;                    /* PNP_OK or the error of the solve */
+    int iterations;                /* Gummel iterations done */
+    double residual;               /* last Gummel residual */
+    long long linear_iterations;   /* PCG iterations summed over all solves */
+    double seconds;                /* wall time of the call */
+} pnp_stats;
+
+typedef struct {
+    int fft_len[3];                /* padded lengths chosen */
+    int stencil_halfwidth;         /* S of the FMT stencils (h) */
+    int well_halfwidth;            /* S of the square-well stencil (h) */
+    size_t device_bytes;           /* device memory held by the problem */
+    int mg_levels;                 /* multigrid levels of the linear solves */
+} pnp_problem_info;
+
+typedef struct pnp_problem pnp_problem;
+typedef struct pnp_server pnp_server;
+
+/* Fill a descriptor with the defaults (all zero / NULL except lambda 0.3,
+ * rho_mix LINEAR, tol 1e-8, max_iter 500, sw_half 1, temperature 300 K,
+ * eps_r 16.6, h_nm 1, site_alpha 1).  Returns PNP_OK, or PNP_ERR_INVALID for NULL. */
+int pnp_desc_init(pnp_problem_desc *desc);
+
+/* Validate `desc`, plan the padded FFT lengths (each zero-extended axis needs
+ * L >= n + S with S the stencil half-width, Sec 3.4), build the quadrature
+ * stencils of Sec 3.5 and their spectra, the site field of Sec 2.3.2 and the
+ * square-well potential mu_sh, and allocate the device state on the current
+ * CUDA device.  On success *out owns all of it.
+ * Errors: PNP_ERR_INVALID (descriptor), PNP_ERR_NOMEM, PNP_ERR_CUDA. */
+int pnp_create_problem(const pnp_problem_desc *desc, pnp_problem **out);
+
+/* Free everything a problem holds.  NULL is ignored. */
+void pnp_destroy_problem(pnp_problem *p);
+
+/* Report the plan of a problem. */
+int pnp_get_problem_info(const pnp_problem *p, pnp_problem_info *info);
+
+/* mu_ex,i = mu_hs,i + mu_sh,i (Sec 2.3, Eq. potential-energy-relation) for
+ * the densities rho [s][nz][ny][nx] (host, FP64, >= 0).  Weighted densities
+ * n_alpha (Sec 2.3.1) by zero-padded FFT correlation with the weight stencils,
+ * the Rosenfeld derivatives dPhi/dn_alpha in FP64, masked to the domain, and
+ * their back-convolution (Sec 2.3.1, Sec 3.4); plus the cached square-well
+ * term (Sec 2.3.2).  Writes mu_ex [s][nz][ny][nx] (host).  Blocks until done.
+ * Errors: PNP_ERR_INVALID, PNP_ERR_PACKING (n3 >= 1 somewhere), PNP_ERR_CUDA. */
+int pnp_excess_mu(pnp_problem *p, const double *rho, double *mu_ex, int precision);
+
+/* As pnp_excess_mu with device pointers, enqueued on `stream` (a
+ * cudaStream_t, NULL = the problem's stream).  Does not synchronise; a
+ * packing error is reported by the next pnp_status(). */
+int pnp_excess_mu_device(pnp_problem *p, const double *d_rho, double *d_mu_ex, int precision,
+                         void *stream);
+
+/* Synchronise the problem's last stream and return the deferred device status
+ * (PNP_OK, PNP_ERR_PACKING, PNP_ERR_OVERFLOW or PNP_ERR_CUDA), clearing it. */
+int pnp_status(pnp_problem *p);
+
+/* Per-kernel timing of the mu_ex pipeline.  While enabled, every kernel the
+ * library launches for pnp_excess_mu / pnp_excess_mu_device is bracketed by
+ * CUDA events on its stream.  pnp_stage_times synchronises, sums the elapsed
+ * times per stage since the last reset into ms[k] and the launch counts into
+ * launches[k] (k < max_stages, stage k named by pnp_stage_name), resets the
+ * record and returns the number of stages.  Stage names: x_fwd, y_fwd, z_mac,
+ * y_inv, x_fused, y_fwd_psi, z_back, y_inv_mu, x_inv. */
+int pnp_stage_timing(pnp_problem *p, int enable);
+int pnp_stage_times(pnp_problem *p, double *ms, int *launches, int max_stages);
+const char *pnp_stage_name(int stage);
+
+/* Relaxed Gummel iteration (Sec 3.2) on the device: per iteration mu_ex from
+ * rho (above), the Poisson equation (Sec 2.1) for phi* and
+ * phi <- l1 phi* + (1-l1) phi, then per species the Slotboom Nernst-Planck
+ * equation -div(Dbar grad rhobar) = 0 (Sec 2.1) with the 7-point harmonic-mean
+ * stencil of Sec 3.1, rho* = rhobar exp(-(q phi + mu_ex)) and the density
+ * relaxation; both linear systems by multigrid-preconditioned CG (Sec 3.3).
+ * Stops when the max-norm update is below tol.  phi0 [nz][ny][nx] and rho0
+ * [s][nz][ny][nx] (host, nullable) give a warm start; the default start is
+ * phi linear in z between the Dirichlet values and rho = rho_bulk.  Writes
+ * phi_out and rho_out (host, nullable) and *stats (nullable).
+ * Errors: PNP_ERR_NOT_CONVERGED (results still written), PNP_ERR_PACKING,
+ * PNP_ERR_OVERFLOW, PNP_ERR_INVALID, PNP_ERR_CUDA. */
+int pnp_gummel_solve(pnp_problem *p, const double *phi0, const double *rho0, double *phi_out,
+                     double *rho_out, pnp_stats *stats);
+
+/* Serving: a queue of independent Gummel solves that run concurrently on one
+ * GPU.  Requests are admitted as slots and the device-memory budget allow;
+ * each keeps its state resident until it finishes; finished results wait in
+ * host memory until polled. */
+typedef struct {
+    size_t hbm_budget_bytes;       /* device memory the server may hold, 0 -> 150 GB */
+    int max_slots;                 /* concurrently resident solves, 0 -> 64 */
+    int max_queue;                 /* waiting requests, 0 -> 4096 */
+} pnp_server_opts;
+
+typedef struct {
+    long long submitted, completed, failed, rejected;
+    int active, queued;
+    size_t bytes_in_use;
+} pnp_server_stats;
+
+int pnp_server_create(const pnp_server_opts *opts, pnp_server **out);
+
+/* Stop the worker, drop pending requests and free everything. */
+void pnp_server_destroy(pnp_server *s);
+
+/* Enqueue a Gummel solve of `desc` (copied, including every array it points
+ * to) with an optional warm start.  Non-blocking.  *ticket identifies it.
+ * Errors: PNP_ERR_INVALID, PNP_ERR_BUSY (queue full, or the request alone
+ * exceeds the budget). */
+int pnp_submit(pnp_server *s, const pnp_problem_desc *desc, const double *phi0, const double *rho0,
+               uint64_t *ticket);
+
+/* Non-blocking.  PNP_PENDING while the request waits or runs; otherwise
+ * copies phi_out [nz][ny][nx] and rho_out [s][nz][ny][nx] (nullable), fills
+ * *stats, forgets the ticket and returns the solve's status.
+ * PNP_ERR_UNKNOWN_TICKET for a ticket never issued or already polled. */
+int pnp_poll(pnp_server *s, uint64_t ticket, double *phi_out, double *rho_out, pnp_stats *stats);
+
+int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
+
+/* Static message for an error code. */
+const char *pnp_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNP_GB300_H */

@@ -92,6 +92,7 @@ def _declare(L):
     L.oracle_excess_mu.restype = ctypes.c_long
     L.oracle_excess_mu.argtypes = [P, _dp, _dp]
     L.oracle_bulk_mu.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+    L.oracle_excess_mu_sampled.argtypes = [P, _dp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), _dp]
     L.oracle_poisson.restype = ctypes.c_int
     L.oracle_poisson.argtypes = [P, _dp, _dp, _dp]
     L.oracle_np.restype = ctypes.c_int
@@ -242,6 +243,18 @@ def excess_mu(spec, rho):
     out = np.zeros((P.s,) + P.shape)
     bad = lib().oracle_excess_mu(P.ref, _ptr(r), _ptr(out))
     return out, int(bad)
+
+
+def excess_mu_sampled(spec, rho, flat_idx):
+    """mu_ex at the given flat grid indices only (same sums as excess_mu).
+    Returns [s, nsamp]."""
+    P = Problem(spec)
+    r = _f64(rho)
+    idx = np.ascontiguousarray(np.asarray(flat_idx, dtype=np.int64))
+    out = np.zeros((P.s, len(idx)))
+    lib().oracle_excess_mu_sampled(P.ref, _ptr(r), len(idx), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                   _ptr(out))
+    return out
 
 
 def bulk_mu(R, rho_b):

@@ -473,6 +473,140 @@ long oracle_excess_mu(const oracle_problem *p, const double *rho, double *mu)
     return bad;
 }
 
+/* mu_ex at selected grid points only (for checks of large grids): the
+ * weighted densities and derivatives are evaluated on the union of the boxes
+ * of half-width S around each sample (every point the back-convolution at the
+ * sample reads), then the same sums as oracle_excess_mu at the samples.
+ * out[i*nsamp + k] for species i and sample k.                              */
+void oracle_excess_mu_sampled(const oracle_problem *p, const double *rho, int nsamp, const long *idx,
+                              double *out)
+{
+    grid_t g = cdft_grid(p);
+    long N = (long)p->nx * p->ny * p->nz;
+    int n3d[3] = {p->nx, p->ny, p->nz};
+    double Rmax = 0.0;
+    for (int i = 0; i < p->s; ++i) if (p->R[i] > Rmax) Rmax = p->R[i];
+    int S = (int)ceil(Rmax) + 1;
+    double Rw = p->well_outer;
+    int Sw = (int)ceil(Rw) + 1;
+    char *mask = calloc(N, 1);
+    for (int k = 0; k < nsamp; ++k) {
+        long c[3] = {idx[k] % p->nx, (idx[k] / p->nx) % p->ny, idx[k] / ((long)p->nx * p->ny)};
+        for (int dz = -S; dz <= S; ++dz)
+            for (int dy = -S; dy <= S; ++dy)
+                for (int dx = -S; dx <= S; ++dx) {
+                    long q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                    int ok = 1;
+                    for (int d = 0; d < 3; ++d) {
+                        if (g.periodic[d]) q[d] = ((q[d] % n3d[d]) + n3d[d]) % n3d[d];
+                        else if (q[d] < 0 || q[d] >= n3d[d]) ok = 0;
+                    }
+                    if (ok) mask[(q[2] * p->ny + q[1]) * p->nx + q[0]] = 1;
+                }
+    }
+    double *n = calloc(10 * N, sizeof(double));
+    double *psi = calloc(10 * N, sizeof(double));
+    for (int i = 0; i < p->s; ++i) {
+        double R = p->R[i];
+        nodes_t sh = make_nodes(0, 0.0, R, p->nmu, p->ntheta, p->nr);
+        nodes_t ba = make_nodes(1, 0.0, R, p->nmu, p->ntheta, p->nr);
+        const double *rho_i = rho + i * N;
+        double c0 = 1.0 / (4.0 * M_PI * R * R), c1 = 1.0 / (4.0 * M_PI * R);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (long pt = 0; pt < N; ++pt) {
+            if (!mask[pt]) continue;
+            double X = (double)(pt % p->nx), Y = (double)((pt / p->nx) % p->ny);
+            double Z = (double)(pt / ((long)p->nx * p->ny));
+            double n2 = 0, v2x = 0, v2y = 0, v2z = 0, n3 = 0;
+            for (int q = 0; q < sh.n; ++q) {
+                double v = interp(&g, rho_i, X + sh.px[q], Y + sh.py[q], Z + sh.pz[q]);
+                n2 += sh.w[q] * v;
+                v2x += sh.w[q] * sh.ux[q] * v;
+                v2y += sh.w[q] * sh.uy[q] * v;
+                v2z += sh.w[q] * sh.uz[q] * v;
+            }
+            for (int q = 0; q < ba.n; ++q)
+                n3 += ba.w[q] * interp(&g, rho_i, X + ba.px[q], Y + ba.py[q], Z + ba.pz[q]);
+            n[0 * N + pt] += c0 * n2; n[1 * N + pt] += c1 * n2; n[2 * N + pt] += n2; n[3 * N + pt] += n3;
+            n[4 * N + pt] += c1 * v2x; n[5 * N + pt] += c1 * v2y; n[6 * N + pt] += c1 * v2z;
+            n[7 * N + pt] += v2x; n[8 * N + pt] += v2y; n[9 * N + pt] += v2z;
+        }
+        free_nodes(&sh);
+        free_nodes(&ba);
+    }
+    /* derivatives at the masked points (zero elsewhere, as off Omega) */
+    double a[10], b[10];
+    for (long pt = 0; pt < N; ++pt) {
+        if (!mask[pt]) continue;
+        for (int k = 0; k < 10; ++k) a[k] = n[k * N + pt];
+        oracle_dphi(1, a, b);
+        for (int k = 0; k < 10; ++k) psi[k * N + pt] = b[k];
+    }
+    double *rs = 0;
+    nodes_t ws = {0};
+    if (p->nsites > 0 && p->depth) {
+        /* site density on the union of boxes of half-width Sw around samples */
+        char *mw = calloc(N, 1);
+        for (int k = 0; k < nsamp; ++k) {
+            long c[3] = {idx[k] % p->nx, (idx[k] / p->nx) % p->ny, idx[k] / ((long)p->nx * p->ny)};
+            for (int dz = -Sw; dz <= Sw; ++dz)
+                for (int dy = -Sw; dy <= Sw; ++dy)
+                    for (int dx = -Sw; dx <= Sw; ++dx) {
+                        long q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                        int ok = 1;
+                        for (int d = 0; d < 3; ++d) {
+                            if (g.periodic[d]) q[d] = ((q[d] % n3d[d]) + n3d[d]) % n3d[d];
+                            else if (q[d] < 0 || q[d] >= n3d[d]) ok = 0;
+                        }
+                        if (ok) mw[(q[2] * p->ny + q[1]) * p->nx + q[0]] = 1;
+                    }
+        }
+        double *full = malloc(sizeof(double) * N);
+        oracle_site_density(p, full);   /* exact at every node */
+        rs = calloc(N, sizeof(double));
+        for (long pt = 0; pt < N; ++pt) if (mw[pt]) rs[pt] = full[pt];
+        free(full);
+        free(mw);
+        ws = make_nodes(2, p->well_inner, p->well_outer, p->w_nmu, p->w_ntheta, p->w_nr);
+    }
+    double half = p->sw_half ? 0.5 : 1.0;
+    for (int i = 0; i < p->s; ++i) {
+        double R = p->R[i];
+        nodes_t sh = make_nodes(0, 0.0, R, p->nmu, p->ntheta, p->nr);
+        nodes_t ba = make_nodes(1, 0.0, R, p->nmu, p->ntheta, p->nr);
+        double c0 = 1.0 / (4.0 * M_PI * R * R), c1 = 1.0 / (4.0 * M_PI * R);
+        double eps = p->depth ? p->depth[i] : 0.0;
+        for (int k = 0; k < nsamp; ++k) {
+            long pt = idx[k];
+            double X = (double)(pt % p->nx), Y = (double)((pt / p->nx) % p->ny);
+            double Z = (double)(pt / ((long)p->nx * p->ny));
+            double acc = 0.0;
+            for (int q = 0; q < sh.n; ++q) {
+                double x = X - sh.px[q], y = Y - sh.py[q], z = Z - sh.pz[q];
+                double scal = c0 * interp(&g, psi + 0 * N, x, y, z) + c1 * interp(&g, psi + 1 * N, x, y, z)
+                              + interp(&g, psi + 2 * N, x, y, z);
+                double vec = sh.ux[q] * (c1 * interp(&g, psi + 4 * N, x, y, z) + interp(&g, psi + 7 * N, x, y, z))
+                             + sh.uy[q] * (c1 * interp(&g, psi + 5 * N, x, y, z) + interp(&g, psi + 8 * N, x, y, z))
+                             + sh.uz[q] * (c1 * interp(&g, psi + 6 * N, x, y, z) + interp(&g, psi + 9 * N, x, y, z));
+                acc += sh.w[q] * (scal + vec);
+            }
+            for (int q = 0; q < ba.n; ++q)
+                acc += ba.w[q] * interp(&g, psi + 3 * N, X - ba.px[q], Y - ba.py[q], Z - ba.pz[q]);
+            if (rs && eps != 0.0) {
+                double a2 = 0.0;
+                for (int q = 0; q < ws.n; ++q)
+                    a2 += ws.w[q] * interp(&g, rs, X + ws.px[q], Y + ws.py[q], Z + ws.pz[q]);
+                acc += half * (-eps) * a2;
+            }
+            out[i * nsamp + k] = acc;
+        }
+        free_nodes(&sh);
+        free_nodes(&ba);
+    }
+    if (rs) { free(rs); free_nodes(&ws); }
+    free(mask); free(n); free(psi);
+}
+
 /* Bulk mu_ex of the uniform reservoir: dPhi/dn_a at the bulk weighted
  * densities times the weight integrals (1, R, 4 pi R^2, 4 pi R^3 / 3).    */
 void oracle_bulk_mu(int s, const double *R, const double *rho_b, double *mu_b)

@@ -1,0 +1,265 @@
+// C ABI of libpnp_gb300 (include/pnp.h): argument checking, device state
+// lifetime, host<->device staging and error mapping.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pnp_internal.h"
+
+namespace pnp {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PNP_OK;
+    if (e == cudaErrorMemoryAllocation) return PNP_ERR_NOMEM;
+    return PNP_ERR_CUDA;
+}
+
+void destroy_problem_internal(Problem *p) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    gummel_free(p);
+    mu_ex_free(p);
+    cudaFree(p->d_flag);
+    cudaFree(p->d_io);
+    cudaFree(p->d_sh_coef);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why) {
+    Problem *p = new (std::nothrow) Problem();
+    if (!p) return PNP_ERR_NOMEM;
+    int rc = validate_and_copy(desc, p, why);
+    if (rc) {
+        delete p;
+        return rc;
+    }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_flag, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        rc = cuda_status(e);
+        destroy_problem_internal(p);
+        return rc;
+    }
+    p->last_stream = p->stream;
+    rc = mu_ex_setup(p);
+    if (rc) {
+        destroy_problem_internal(p);
+        return rc;
+    }
+    *out = p;
+    return PNP_OK;
+}
+
+static int read_flag(Problem *p, cudaStream_t st) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h) {
+        cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+    }
+    if (h & kFlagTimeout) return PNP_ERR_TIMEOUT;
+    if (h & kFlagOverflow) return PNP_ERR_OVERFLOW;
+    if (h & (kFlagPacking | kFlagNonFinite)) return PNP_ERR_PACKING;
+    return PNP_OK;
+}
+
+static int resolve_prec(const Problem *p, int prec) {
+    if (prec == PNP_PREC_DEFAULT) return p->precision;
+    if (prec == PNP_PREC_FP64 || prec == PNP_PREC_FP32) return prec;
+    return -100;
+}
+
+}  // namespace pnp
+
+using namespace pnp;
+
+extern "C" {
+
+int pnp_desc_init(pnp_problem_desc *d) {
+    if (!d) return PNP_ERR_INVALID;
+    std::memset(d, 0, sizeof(*d));
+    d->lambda_phi = 0.3;
+    d->lambda_rho = 0.3;
+    d->rho_mix = PNP_MIX_LINEAR;
+    d->tol = 1e-8;
+    d->max_iter = 500;
+    d->sw_half = 1;
+    d->temperature_K = 300.0;
+    d->eps_r = 16.6;
+    d->h_nm = 1.0;
+    d->site_alpha = 1.0;
+    d->precision = PNP_PREC_FP64;
+    return PNP_OK;
+}
+
+int pnp_create_problem(const pnp_problem_desc *desc, pnp_problem **out) {
+    if (!desc || !out) return PNP_ERR_INVALID;
+    *out = nullptr;
+    Problem *impl = nullptr;
+    std::string why;
+    int rc = create_problem_internal(desc, &impl, &why);
+    if (rc) return rc;
+    pnp_problem *h = new (std::nothrow) pnp_problem{impl};
+    if (!h) {
+        destroy_problem_internal(impl);
+        return PNP_ERR_NOMEM;
+    }
+    *out = h;
+    return PNP_OK;
+}
+
+void pnp_destroy_problem(pnp_problem *p) {
+    if (!p) return;
+    destroy_problem_internal(p->impl);
+    delete p;
+}
+
+int pnp_get_problem_info(const pnp_problem *h, pnp_problem_info *info) {
+    if (!h || !info) return PNP_ERR_INVALID;
+    const Problem *p = h->impl;
+    for (int c = 0; c < 3; ++c) info->fft_len[c] = p->L[c];
+    info->stencil_halfwidth = p->S;
+    info->well_halfwidth = p->Ssw;
+    info->device_bytes = p->device_bytes;
+    info->mg_levels = p->mg_levels;
+    return PNP_OK;
+}
+
+int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precision) {
+    if (!h || !rho || !mu_ex) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    int prec = resolve_prec(p, precision);
+    if (prec < 0) return PNP_ERR_INVALID;
+    const size_t n = p->npts() * p->s;
+    for (size_t k = 0; k < n; ++k)
+        if (!(rho[k] >= 0.0) || !std::isfinite(rho[k])) return PNP_ERR_INVALID;
+    if (!p->d_io) {
+        if (cudaMalloc(&p->d_io, sizeof(double) * (2 * n + p->npts())) != cudaSuccess) return PNP_ERR_NOMEM;
+        p->device_bytes += sizeof(double) * (2 * n + p->npts());
+    }
+    cudaStream_t st = p->stream;
+    p->last_stream = st;
+    cudaError_t e = cudaMemcpyAsync(p->d_io, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = mu_ex_enqueue(p, prec, p->d_io, p->d_io + n, st);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(mu_ex, p->d_io + n, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return read_flag(p, st);
+}
+
+int pnp_excess_mu_device(pnp_problem *h, const double *d_rho, double *d_mu_ex, int precision, void *stream) {
+    if (!h || !d_rho || !d_mu_ex) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    int prec = resolve_prec(p, precision);
+    if (prec < 0) return PNP_ERR_INVALID;
+    cudaStream_t st = stream ? (cudaStream_t)stream : p->stream;
+    p->last_stream = st;
+    return mu_ex_enqueue(p, prec, d_rho, d_mu_ex, st);
+}
+
+int pnp_status(pnp_problem *h) {
+    if (!h) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = p->deferred;
+    p->deferred = 0;
+    int f = read_flag(p, p->last_stream);
+    return rc ? rc : f;
+}
+
+int pnp_gummel_solve(pnp_problem *h, const double *phi0, const double *rho0, double *phi_out, double *rho_out,
+                     pnp_stats *stats) {
+    if (!h) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t N = p->npts(), n = N * p->s;
+    if (rho0)
+        for (size_t k = 0; k < n; ++k)
+            if (!(rho0[k] > 0.0) || !std::isfinite(rho0[k])) return PNP_ERR_INVALID;
+    if (phi0)
+        for (size_t k = 0; k < N; ++k)
+            if (!std::isfinite(phi0[k])) return PNP_ERR_INVALID;
+    if (!p->d_io) {
+        if (cudaMalloc(&p->d_io, sizeof(double) * (2 * n + N)) != cudaSuccess) return PNP_ERR_NOMEM;
+        p->device_bytes += sizeof(double) * (2 * n + N);
+    }
+    cudaStream_t st = p->stream;
+    p->last_stream = st;
+    double *d_rho = p->d_io, *d_phi = p->d_io + n, *d_rho0 = nullptr, *d_phi0 = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (rho0) {
+        e = cudaMemcpyAsync(d_rho, rho0, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+        d_rho0 = d_rho;
+    }
+    if (phi0 && e == cudaSuccess) {
+        e = cudaMemcpyAsync(d_phi, phi0, sizeof(double) * N, cudaMemcpyHostToDevice, st);
+        d_phi0 = d_phi;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    pnp_stats local{};
+    int rc = gummel_run(p, d_phi0, d_rho0, d_phi, d_rho, &local, st);
+    if (rc == PNP_OK || rc == PNP_ERR_NOT_CONVERGED) {
+        if (phi_out) e = cudaMemcpyAsync(phi_out, d_phi, sizeof(double) * N, cudaMemcpyDeviceToHost, st);
+        if (rho_out && e == cudaSuccess)
+            e = cudaMemcpyAsync(rho_out, d_rho, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    local.status = rc;
+    local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = local;
+    return rc;
+}
+
+int pnp_stage_timing(pnp_problem *h, int enable) {
+    if (!h) return PNP_ERR_INVALID;
+    h->impl->timer.enabled = enable != 0;
+    return PNP_OK;
+}
+
+int pnp_stage_times(pnp_problem *h, double *ms, int *launches, int max_stages) {
+    if (!h || max_stages < 0) return PNP_ERR_INVALID;
+    return h->impl->timer.collect(ms, launches, max_stages);
+}
+
+const char *pnp_stage_name(int stage) {
+    static const char *names[kNumStages] = {"x_fwd", "y_fwd", "z_mac", "y_inv", "x_fused",
+                                            "y_fwd_psi", "z_back", "y_inv_mu", "x_inv"};
+    if (stage < 0 || stage >= kNumStages) return "";
+    return names[stage];
+}
+
+const char *pnp_error_string(int code) {
+    switch (code) {
+        case PNP_OK: return "ok";
+        case PNP_PENDING: return "pending";
+        case PNP_ERR_INVALID: return "invalid argument or descriptor";
+        case PNP_ERR_NOMEM: return "out of memory";
+        case PNP_ERR_CUDA: return "CUDA error";
+        case PNP_ERR_NOT_CONVERGED: return "Gummel iteration did not converge";
+        case PNP_ERR_PACKING: return "packing fraction n3 >= 1 or non-finite value in mu_ex";
+        case PNP_ERR_OVERFLOW: return "Slotboom exponential overflow";
+        case PNP_ERR_BUSY: return "server busy or request over the memory budget";
+        case PNP_ERR_TIMEOUT: return "device wait timed out";
+        case PNP_ERR_UNKNOWN_TICKET: return "unknown ticket";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,639 @@
+// Relaxed Gummel iteration on the device (Sec 3.2) with multigrid-
+// preconditioned conjugate gradients for the Poisson equation (Sec 2.1) and
+// the Slotboom-transformed Nernst-Planck equations (Sec 2.1, 7-point
+// harmonic-mean stencil of Sec 3.1).
+//
+// Operators are matrix-free: per grid level, face coefficients cx[p] (face to
+// the +x neighbour, wrapping; zero across a no-flux wall), cy[p], cz[p] (face
+// to +z; on the top plane the face to the upper Dirichlet plane) and czlo[p]
+// (face to the lower Dirichlet plane, plane 0 only);
+//   (A u)_p = sum_faces c (u_p - u_nbr),  Dirichlet neighbours moved to b.
+// Multigrid (replacing the paper's external algebraic multigrid, Sec 3.3):
+// cells are aggregated 2x2x2 (per axis while even and >= 4); the coarse
+// operator is the Galerkin product with piecewise-constant interpolation,
+// i.e. coarse face coefficients are sums of the fine faces between two
+// aggregates; restriction sums the 8 fine residuals, prolongation adds the
+// coarse value.  One V(1,1) cycle with red-black sweeps (red-black before,
+// black-red after, so the cycle is a symmetric operator) preconditions CG;
+// the coarsest level gets 40 symmetric sweeps in one CTA.  All dot products
+// use a fixed-shape two-stage reduction, so results are bitwise reproducible.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pnp_internal.h"
+
+namespace pnp {
+
+struct Op {
+    int nx, ny, nz;
+    const double *cx, *cy, *cz, *czlo;
+};
+
+struct Level {
+    int nx, ny, nz;
+    size_t n;
+    int fx, fy, fz;                // aggregation factors to the next level
+    double *cx, *cy, *cz, *czlo;   // operator being solved (Poisson or NP)
+    double *pcx, *pcy, *pcz, *pczlo;   // Poisson copy (built once)
+    double *x, *b, *r;
+};
+
+constexpr int kRedBlocks = 512;
+constexpr int kCoarseSweeps = 40;
+
+struct GummelState {
+    std::vector<Level> lv;
+    double *mu = nullptr, *rho_new = nullptr;
+    double *rhs = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr;
+    double *partial = nullptr;     // kRedBlocks
+    double *scal = nullptr;        // device scalars
+    unsigned long long *dmax = nullptr;
+    double *h_pinned = nullptr;    // host mirror of a few scalars
+    size_t bytes = 0;
+    bool poisson_ready = false;
+};
+
+enum { S_RZ = 0, S_PAP, S_RR, S_ALPHA, S_BETA, S_RZNEW, S_BB, S_COUNT };
+
+__device__ __forceinline__ size_t pidx(int i, int j, int k, int nx, int ny) {
+    return ((size_t)k * ny + j) * nx + i;
+}
+
+__device__ __forceinline__ double op_diag(const Op &A, int i, int j, int k, size_t p) {
+    const int im = i == 0 ? A.nx - 1 : i - 1, jm = j == 0 ? A.ny - 1 : j - 1;
+    double d = A.cx[p] + A.cy[p] + A.cz[p];
+    d += A.cx[pidx(im, j, k, A.nx, A.ny)] + A.cy[pidx(i, jm, k, A.nx, A.ny)];
+    d += k > 0 ? A.cz[p - (size_t)A.nx * A.ny] : A.czlo[p];
+    return d;
+}
+
+__device__ __forceinline__ double op_nbr(const Op &A, const double *__restrict__ u, int i, int j, int k, size_t p) {
+    const int ip = i + 1 == A.nx ? 0 : i + 1, im = i == 0 ? A.nx - 1 : i - 1;
+    const int jp = j + 1 == A.ny ? 0 : j + 1, jm = j == 0 ? A.ny - 1 : j - 1;
+    const size_t plane = (size_t)A.nx * A.ny;
+    const size_t pxm = pidx(im, j, k, A.nx, A.ny), pym = pidx(i, jm, k, A.nx, A.ny);
+    double s = A.cx[p] * u[pidx(ip, j, k, A.nx, A.ny)] + A.cx[pxm] * u[pxm];
+    s += A.cy[p] * u[pidx(i, jp, k, A.nx, A.ny)] + A.cy[pym] * u[pym];
+    if (k + 1 < A.nz) s += A.cz[p] * u[p + plane];
+    if (k > 0) s += A.cz[p - plane] * u[p - plane];
+    return s;
+}
+
+#define GRID_LOOP(p, n) for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < (n); p += (size_t)gridDim.x * blockDim.x)
+
+__global__ void k_residual(Op A, const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ r) {
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+        r[p] = b[p] - (op_diag(A, i, j, k, p) * x[p] - op_nbr(A, x, i, j, k, p));
+    }
+}
+
+__global__ void k_apply(Op A, const double *__restrict__ x, double *__restrict__ y) {
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+        y[p] = op_diag(A, i, j, k, p) * x[p] - op_nbr(A, x, i, j, k, p);
+    }
+}
+
+// one colour of a red-black sweep: x_p = (b_p + sum c x_nbr) / diag_p for
+// points with (i + j + k) % 2 == color.  With zero_init the other colour is
+// taken as zero (first sweep from x = 0).
+__global__ void k_color_sweep(Op A, double *__restrict__ x, const double *__restrict__ b, int color) {
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+        if (((i + j + k) & 1) != color) continue;
+        x[p] = (b[p] + op_nbr(A, x, i, j, k, p)) / op_diag(A, i, j, k, p);
+    }
+}
+
+// coarsest level: x = 0, then kCoarseSweeps symmetric (red, black, black, red) sweeps in one CTA
+__global__ void k_coarse_solve(Op A, double *__restrict__ x, const double *__restrict__ b) {
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    for (size_t p = threadIdx.x; p < n; p += blockDim.x) x[p] = 0.0;
+    __syncthreads();
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+        const int order[4] = {0, 1, 1, 0};
+        for (int c = 0; c < 4; ++c) {
+            for (size_t p = threadIdx.x; p < n; p += blockDim.x) {
+                const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+                if (((i + j + k) & 1) != order[c]) continue;
+                x[p] = (b[p] + op_nbr(A, x, i, j, k, p)) / op_diag(A, i, j, k, p);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// coarse face coefficients: sums of the fine faces leaving each aggregate
+__global__ void k_coarsen(Op F, int fx, int fy, int fz, int cnx, int cny, int cnz, double *__restrict__ cx,
+                          double *__restrict__ cy, double *__restrict__ cz, double *__restrict__ czlo) {
+    const size_t n = (size_t)cnx * cny * cnz;
+    GRID_LOOP(q, n) {
+        const int I = q % cnx, J = (q / cnx) % cny, K = q / ((size_t)cnx * cny);
+        double sx = 0, sy = 0, sz = 0, sl = 0;
+        for (int c = 0; c < fz; ++c)
+            for (int b = 0; b < fy; ++b)
+                for (int a = 0; a < fx; ++a) {
+                    const int i = I * fx + a, j = J * fy + b, k = K * fz + c;
+                    const size_t p = pidx(i, j, k, F.nx, F.ny);
+                    if (a == fx - 1) sx += F.cx[p];
+                    if (b == fy - 1) sy += F.cy[p];
+                    if (c == fz - 1) sz += F.cz[p];
+                    if (c == 0 && K == 0) sl += F.czlo[p];
+                }
+        cx[q] = sx;
+        cy[q] = sy;
+        cz[q] = sz;
+        czlo[q] = sl;
+    }
+}
+
+__global__ void k_restrict(const double *__restrict__ rf, int nx, int ny, int fx, int fy, int fz, int cnx, int cny,
+                           int cnz, double *__restrict__ bc) {
+    const size_t n = (size_t)cnx * cny * cnz;
+    GRID_LOOP(q, n) {
+        const int I = q % cnx, J = (q / cnx) % cny, K = q / ((size_t)cnx * cny);
+        double s = 0;
+        for (int c = 0; c < fz; ++c)
+            for (int b = 0; b < fy; ++b)
+                for (int a = 0; a < fx; ++a) s += rf[pidx(I * fx + a, J * fy + b, K * fz + c, nx, ny)];
+        bc[q] = s;
+    }
+}
+
+__global__ void k_prolong_add(double *__restrict__ xf, int nx, int ny, int nz, int fx, int fy, int fz, int cnx,
+                              int cny, const double *__restrict__ xc) {
+    const size_t n = (size_t)nx * ny * nz;
+    GRID_LOOP(p, n) {
+        const int i = p % nx, j = (p / nx) % ny, k = p / ((size_t)nx * ny);
+        xf[p] += xc[pidx(i / fx, j / fy, k / fz, cnx, cny)];
+    }
+}
+
+__global__ void k_fill(double *__restrict__ a, double v, size_t n) {
+    GRID_LOOP(p, n) a[p] = v;
+}
+
+// deterministic dot product, stage 1: fixed grid of kRedBlocks blocks
+__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, size_t n,
+                              double *__restrict__ partial) {
+    __shared__ double sh[256];
+    double s = 0;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        s += a[p] * b[p];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// stage 2: one block sums the partials into scal[slot]
+__global__ void k_dot_final(const double *__restrict__ partial, double *__restrict__ scal, int slot) {
+    __shared__ double sh[kRedBlocks];
+    for (int t = threadIdx.x; t < kRedBlocks; t += blockDim.x) sh[t] = partial[t];
+    __syncthreads();
+    for (int w = kRedBlocks / 2; w > 0; w >>= 1) {
+        for (int t = threadIdx.x; t < w; t += blockDim.x) sh[t] += sh[t + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[slot] = sh[0];
+}
+
+__global__ void k_scalars_alpha(double *scal) {
+    scal[S_ALPHA] = scal[S_RZ] / scal[S_PAP];
+}
+
+__global__ void k_scalars_beta(double *scal) {
+    scal[S_BETA] = scal[S_RZNEW] / scal[S_RZ];
+    scal[S_RZ] = scal[S_RZNEW];
+}
+
+// x += alpha p ; r -= alpha Ap
+__global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const double *__restrict__ Ap, const double *__restrict__ scal, size_t n) {
+    const double a = scal[S_ALPHA];
+    GRID_LOOP(k, n) {
+        x[k] += a * p[k];
+        r[k] -= a * Ap[k];
+    }
+}
+
+// p = z + beta p
+__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ scal,
+                           size_t n) {
+    const double b = scal[S_BETA];
+    GRID_LOOP(k, n) p[k] = z[k] + b * p[k];
+}
+
+__global__ void k_copy(double *__restrict__ d, const double *__restrict__ s, size_t n) {
+    GRID_LOOP(k, n) d[k] = s[k];
+}
+
+// ---------------------------------------------------------------------------
+// physics kernels
+struct PhysConst {
+    int nx, ny, nz, bcx, bcy;
+    double lB;
+    double phi_lo, phi_hi;
+};
+
+// Poisson face coefficients (h = 1): 1, zero across no-flux walls
+__global__ void k_poisson_coefs(PhysConst c, double *cx, double *cy, double *cz, double *czlo) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    GRID_LOOP(p, n) {
+        const int i = p % c.nx, j = (p / c.nx) % c.ny, k = p / ((size_t)c.nx * c.ny);
+        cx[p] = (c.bcx == PNP_BC_NOFLUX && i == c.nx - 1) ? 0.0 : 1.0;
+        cy[p] = (c.bcy == PNP_BC_NOFLUX && j == c.ny - 1) ? 0.0 : 1.0;
+        cz[p] = 1.0;
+        czlo[p] = k == 0 ? 1.0 : 0.0;
+    }
+}
+
+// b = 4 pi lB (rho_f + sum_i q_i rho_i) + Dirichlet contributions
+__global__ void k_poisson_rhs(PhysConst c, const double *__restrict__ rho, int s, const int *__restrict__ q,
+                              const double *__restrict__ rho_f, double *__restrict__ b) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    const size_t plane = (size_t)c.nx * c.ny;
+    GRID_LOOP(p, n) {
+        double ch = rho_f ? rho_f[p] : 0.0;
+        for (int i = 0; i < s; ++i) ch += q[i] * rho[i * n + p];
+        double v = 4.0 * M_PI * c.lB * ch;
+        if (p < plane) v += c.phi_lo;
+        if (p >= n - plane) v += c.phi_hi;
+        b[p] = v;
+    }
+}
+
+// phi_new = l1 phi* + (1 - l1) phi ; track max |phi_new - phi|
+__global__ void k_relax_phi(double *__restrict__ phi, const double *__restrict__ phis, double l1, size_t n,
+                            unsigned long long *__restrict__ dmax) {
+    double m = 0;
+    GRID_LOOP(p, n) {
+        const double v = l1 * phis[p] + (1.0 - l1) * phi[p];
+        m = fmax(m, fabs(v - phi[p]));
+        phi[p] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+}
+
+struct NpConst {
+    double D, q, Dlo, Dhi, rlo, rhi;
+};
+
+// Slotboom coefficients (Sec 2.1) and the harmonic-mean face coefficients
+// (Sec 3.1): Dbar = D exp(-(q phi + mu)); faces to the Dirichlet planes use
+// the reservoir value D exp(-(q phi_face + mu_b)).  Also writes the Dirichlet
+// right-hand side and the initial guess rhobar = rho exp(q phi + mu).
+__global__ void k_np_setup(PhysConst c, NpConst s, const double *__restrict__ phi, const double *__restrict__ mu,
+                           const double *__restrict__ rho, double *__restrict__ cx, double *__restrict__ cy,
+                           double *__restrict__ cz, double *__restrict__ czlo, double *__restrict__ b,
+                           double *__restrict__ x0, int *__restrict__ flag) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    const size_t plane = (size_t)c.nx * c.ny;
+    bool bad = false;
+    GRID_LOOP(p, n) {
+        const int i = p % c.nx, j = (p / c.nx) % c.ny, k = p / plane;
+        auto Db = [&](size_t t) { return s.D * exp(-(s.q * phi[t] + mu[t])); };
+        const double d0 = Db(p);
+        const size_t pxp = pidx(i + 1 == c.nx ? 0 : i + 1, j, k, c.nx, c.ny);
+        const size_t pyp = pidx(i, j + 1 == c.ny ? 0 : j + 1, k, c.nx, c.ny);
+        double vx = 0, vy = 0;
+        if (!(c.bcx == PNP_BC_NOFLUX && i == c.nx - 1)) {
+            const double d1 = Db(pxp);
+            vx = 2.0 * d0 * d1 / (d0 + d1);
+        }
+        if (!(c.bcy == PNP_BC_NOFLUX && j == c.ny - 1)) {
+            const double d1 = Db(pyp);
+            vy = 2.0 * d0 * d1 / (d0 + d1);
+        }
+        double vz;
+        if (k + 1 < c.nz) {
+            const double d1 = Db(p + plane);
+            vz = 2.0 * d0 * d1 / (d0 + d1);
+        } else {
+            vz = 2.0 * d0 * s.Dhi / (d0 + s.Dhi);
+        }
+        const double vl = k == 0 ? 2.0 * d0 * s.Dlo / (d0 + s.Dlo) : 0.0;
+        cx[p] = vx;
+        cy[p] = vy;
+        cz[p] = vz;
+        czlo[p] = vl;
+        double bv = 0;
+        if (k == 0) bv += vl * s.rlo;
+        if (k + 1 == c.nz) bv += vz * s.rhi;
+        b[p] = bv;
+        const double x = rho[p] * exp(s.q * phi[p] + mu[p]);
+        x0[p] = x;
+        if (!isfinite(d0) || !isfinite(x) || !(d0 > 0)) bad = true;
+    }
+    if (bad) atomicOr(flag, kFlagOverflow);
+}
+
+// rho* = rhobar exp(-(q phi + mu)); relaxation (linear or geometric); track
+// max |rho_new - rho| / rho_b
+__global__ void k_np_finish(size_t n, double q, double l2, int mix, double inv_rb, const double *__restrict__ phi,
+                            const double *__restrict__ mu, const double *__restrict__ rbar, double *__restrict__ rho,
+                            unsigned long long *__restrict__ dmax, int *__restrict__ flag) {
+    double m = 0;
+    bool bad = false;
+    GRID_LOOP(p, n) {
+        const double rs = rbar[p] * exp(-(q * phi[p] + mu[p]));
+        const double old = rho[p];
+        const double v = mix == PNP_MIX_GEOMETRIC ? old * exp(l2 * log(rs / old)) : l2 * rs + (1.0 - l2) * old;
+        if (!isfinite(v) || !(v > 0)) bad = true;
+        m = fmax(m, fabs(v - old) * inv_rb);
+        rho[p] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+    if (bad) atomicOr(flag, kFlagOverflow);
+}
+
+__global__ void k_init_phi(PhysConst c, double *__restrict__ phi) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    GRID_LOOP(p, n) {
+        const int k = p / ((size_t)c.nx * c.ny);
+        phi[p] = c.phi_lo + (c.phi_hi - c.phi_lo) * (k + 1.0) / (c.nz + 1.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+static int grid_for(size_t n) { return (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16); }
+
+static Op op_of(const Level &L) { return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo}; }
+
+static void vcycle(GummelState *g, int l, cudaStream_t st) {
+    Level &L = g->lv[l];
+    const Op A = op_of(L);
+    const int G = grid_for(L.n);
+    if (l + 1 == (int)g->lv.size()) {
+        k_coarse_solve<<<1, 512, 0, st>>>(A, L.x, L.b);
+        return;
+    }
+    Level &C = g->lv[l + 1];
+    k_fill<<<G, 256, 0, st>>>(L.x, 0.0, L.n);
+    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 0);
+    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 1);
+    k_residual<<<G, 256, 0, st>>>(A, L.x, L.b, L.r);
+    k_restrict<<<grid_for(C.n), 256, 0, st>>>(L.r, L.nx, L.ny, L.fx, L.fy, L.fz, C.nx, C.ny, C.nz, C.b);
+    vcycle(g, l + 1, st);
+    k_prolong_add<<<G, 256, 0, st>>>(L.x, L.nx, L.ny, L.nz, L.fx, L.fy, L.fz, C.nx, C.ny, C.x);
+    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 1);
+    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 0);
+}
+
+static void coarsen_all(GummelState *g, cudaStream_t st) {
+    for (size_t l = 0; l + 1 < g->lv.size(); ++l) {
+        Level &F = g->lv[l], &C = g->lv[l + 1];
+        k_coarsen<<<grid_for(C.n), 256, 0, st>>>(op_of(F), F.fx, F.fy, F.fz, C.nx, C.ny, C.nz, C.cx, C.cy, C.cz,
+                                                 C.czlo);
+    }
+}
+
+static void dot(GummelState *g, const double *a, const double *b, size_t n, int slot, cudaStream_t st) {
+    k_dot_partial<<<kRedBlocks, 256, 0, st>>>(a, b, n, g->partial);
+    k_dot_final<<<1, 256, 0, st>>>(g->partial, g->scal, slot);
+}
+
+// MG-preconditioned CG on level 0's operator; x holds the initial guess.
+// Stops when ||r||_2 <= tol ||b||_2.  Returns iterations or a negative code.
+static int pcg(GummelState *g, double *x, const double *b, double tol, int maxit, cudaStream_t st) {
+    Level &L0 = g->lv[0];
+    const Op A = op_of(L0);
+    const size_t n = L0.n;
+    const int G = grid_for(n);
+    double *r = g->r, *z = g->z, *p = g->pv, *Ap = g->Ap;
+    dot(g, b, b, n, S_BB, st);
+    k_residual<<<G, 256, 0, st>>>(A, x, b, r);
+    dot(g, r, r, n, S_RR, st);
+    cudaMemcpyAsync(g->h_pinned, g->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    double bb = g->h_pinned[S_BB], rr = g->h_pinned[S_RR];
+    if (!(bb > 0)) bb = 1.0;
+    const double target = tol * tol * bb;
+    if (!std::isfinite(rr)) return PNP_ERR_OVERFLOW;
+    if (rr <= target) return 0;
+    // z = M r
+    k_copy<<<G, 256, 0, st>>>(L0.b, r, n);
+    vcycle(g, 0, st);
+    k_copy<<<G, 256, 0, st>>>(z, L0.x, n);
+    k_copy<<<G, 256, 0, st>>>(p, z, n);
+    dot(g, r, z, n, S_RZ, st);
+    int it = 0;
+    while (it < maxit) {
+        k_apply<<<G, 256, 0, st>>>(A, p, Ap);
+        dot(g, p, Ap, n, S_PAP, st);
+        k_scalars_alpha<<<1, 1, 0, st>>>(g->scal);
+        k_update_xr<<<G, 256, 0, st>>>(x, r, p, Ap, g->scal, n);
+        ++it;
+        dot(g, r, r, n, S_RR, st);
+        cudaMemcpyAsync(g->h_pinned + S_RR, g->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e);
+        rr = g->h_pinned[S_RR];
+        if (!std::isfinite(rr)) return PNP_ERR_OVERFLOW;
+        if (rr <= target) break;
+        k_copy<<<G, 256, 0, st>>>(L0.b, r, n);
+        vcycle(g, 0, st);
+        k_copy<<<G, 256, 0, st>>>(z, L0.x, n);
+        dot(g, r, z, n, S_RZNEW, st);
+        k_scalars_beta<<<1, 1, 0, st>>>(g->scal);
+        k_update_p<<<G, 256, 0, st>>>(p, z, g->scal, n);
+    }
+    return it;
+}
+
+static void set_operator(GummelState *g, bool poisson) {
+    for (auto &L : g->lv) {
+        if (poisson) {
+            std::swap(L.cx, L.pcx);
+            std::swap(L.cy, L.pcy);
+            std::swap(L.cz, L.pcz);
+            std::swap(L.czlo, L.pczlo);
+        }
+    }
+}
+
+int gummel_setup(Problem *p) {
+    if (p->gs) return PNP_OK;
+    GummelState *g = new GummelState();
+    p->gs = g;
+    auto alloc = [&](double **ptr, size_t n) {
+        if (cudaMalloc(ptr, sizeof(double) * std::max<size_t>(n, 1)) != cudaSuccess) return false;
+        g->bytes += sizeof(double) * std::max<size_t>(n, 1);
+        return true;
+    };
+    // levels
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    while (true) {
+        Level L{};
+        L.nx = nx; L.ny = ny; L.nz = nz;
+        L.n = (size_t)nx * ny * nz;
+        L.fx = (nx % 2 == 0 && nx >= 4) ? 2 : 1;
+        L.fy = (ny % 2 == 0 && ny >= 4) ? 2 : 1;
+        L.fz = (nz % 2 == 0 && nz >= 4) ? 2 : 1;
+        bool last = L.n <= 64 || (L.fx == 1 && L.fy == 1 && L.fz == 1) || g->lv.size() >= 16;
+        if (last) L.fx = L.fy = L.fz = 1;
+        g->lv.push_back(L);
+        if (last) break;
+        nx /= L.fx; ny /= L.fy; nz /= L.fz;
+    }
+    // coarsest must fit the single-CTA solver comfortably
+    const size_t N = p->npts();
+    bool ok = true;
+    for (size_t l = 0; l < g->lv.size() && ok; ++l) {
+        Level &L = g->lv[l];
+        ok = alloc(&L.cx, L.n) && alloc(&L.cy, L.n) && alloc(&L.cz, L.n) && alloc(&L.czlo, L.n) &&
+             alloc(&L.pcx, L.n) && alloc(&L.pcy, L.n) && alloc(&L.pcz, L.n) && alloc(&L.pczlo, L.n) &&
+             alloc(&L.x, L.n) && alloc(&L.b, L.n) && alloc(&L.r, L.n);
+    }
+    ok = ok && alloc(&g->mu, N * p->s) && alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
+         alloc(&g->z, N) && alloc(&g->pv, N) && alloc(&g->Ap, N) && alloc(&g->partial, kRedBlocks) &&
+         alloc(&g->scal, S_COUNT);
+    if (ok) {
+        if (cudaMalloc(&g->dmax, sizeof(unsigned long long)) != cudaSuccess) ok = false;
+        if (ok && cudaMallocHost(&g->h_pinned, sizeof(double) * 16) != cudaSuccess) ok = false;
+    }
+    if (!ok) return PNP_ERR_NOMEM;
+    p->device_bytes += g->bytes;
+    p->mg_levels = (int)g->lv.size();
+    // Poisson operator on every level (into the p* arrays)
+    PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
+    set_operator(g, true);
+    k_poisson_coefs<<<grid_for(N), 256, 0, p->stream>>>(c, g->lv[0].cx, g->lv[0].cy, g->lv[0].cz, g->lv[0].czlo);
+    coarsen_all(g, p->stream);
+    set_operator(g, true);
+    return cuda_status(cudaStreamSynchronize(p->stream));
+}
+
+void gummel_free(Problem *p) {
+    GummelState *g = p->gs;
+    if (!g) return;
+    for (auto &L : g->lv) {
+        for (double *a : {L.cx, L.cy, L.cz, L.czlo, L.pcx, L.pcy, L.pcz, L.pczlo, L.x, L.b, L.r}) cudaFree(a);
+    }
+    for (double *a : {g->mu, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal}) cudaFree(a);
+    cudaFree(g->dmax);
+    cudaFreeHost(g->h_pinned);
+    delete g;
+    p->gs = nullptr;
+}
+
+int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho, pnp_stats *stats,
+               cudaStream_t st) {
+    if (p->bc[2] != PNP_BC_DIRICHLET || p->bc[0] == PNP_BC_DIRICHLET || p->bc[1] == PNP_BC_DIRICHLET)
+        return PNP_ERR_INVALID;
+    int rc = gummel_setup(p);
+    if (rc) return rc;
+    GummelState *g = p->gs;
+    const size_t N = p->npts();
+    const int s = p->s;
+    const int G = grid_for(N);
+    PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
+    // device copies of the per-species integers and the fixed charge
+    int *d_q = nullptr;
+    double *d_rhof = nullptr;
+    cudaError_t e = cudaMalloc(&d_q, sizeof(int) * s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, p->q.data(), sizeof(int) * s, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !p->rho_f.empty()) {
+        e = cudaMalloc(&d_rhof, sizeof(double) * N);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rhof, p->rho_f.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d_q);
+        cudaFree(d_rhof);
+        return cuda_status(e);
+    }
+    // initial state
+    if (d_phi0) {
+        if (d_phi0 != d_phi) k_copy<<<G, 256, 0, st>>>(d_phi, d_phi0, N);
+    } else {
+        k_init_phi<<<G, 256, 0, st>>>(c, d_phi);
+    }
+    if (d_rho0) {
+        if (d_rho0 != d_rho) k_copy<<<G, 256, 0, st>>>(d_rho, d_rho0, N * s);
+    } else {
+        for (int i = 0; i < s; ++i) k_fill<<<G, 256, 0, st>>>(d_rho + i * N, p->rho_b[i], N);
+    }
+    cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+    long long lin = 0;
+    int status = PNP_ERR_NOT_CONVERGED, it = 0;
+    double res = 0;
+    const int maxlin = 2000;
+    for (it = 1; it <= p->max_iter; ++it) {
+        // 1. mu_ex from rho^{n-1}
+        rc = mu_ex_enqueue(p, p->precision, d_rho, g->mu, st);
+        if (rc) { status = rc; break; }
+        // 2. Poisson for phi*, starting from phi
+        cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), st);
+        set_operator(g, true);
+        k_poisson_rhs<<<G, 256, 0, st>>>(c, d_rho, s, d_q, d_rhof, g->rhs);
+        k_copy<<<G, 256, 0, st>>>(g->x, d_phi, N);
+        int li = pcg(g, g->x, g->rhs, p->lin_tol, maxlin, st);
+        set_operator(g, true);
+        if (li < 0) { status = li; break; }
+        lin += li;
+        // 3. relax phi
+        k_relax_phi<<<G, 256, 0, st>>>(d_phi, g->x, p->lambda_phi, N, g->dmax);
+        // 4. Nernst-Planck per species
+        bool fail = false;
+        for (int i = 0; i < s && !fail; ++i) {
+            NpConst nc;
+            nc.D = p->D[i];
+            nc.q = p->q[i];
+            nc.Dlo = p->D[i] * std::exp(-(p->q[i] * p->phi_lo + p->mu_bulk[i]));
+            nc.Dhi = p->D[i] * std::exp(-(p->q[i] * p->phi_hi + p->mu_bulk[i]));
+            nc.rlo = p->rho_b[i] * std::exp(p->q[i] * p->phi_lo + p->mu_bulk[i]);
+            nc.rhi = p->rho_b[i] * std::exp(p->q[i] * p->phi_hi + p->mu_bulk[i]);
+            Level &L0 = g->lv[0];
+            k_np_setup<<<G, 256, 0, st>>>(c, nc, d_phi, g->mu + i * N, d_rho + i * N, L0.cx, L0.cy, L0.cz, L0.czlo,
+                                          g->rhs, g->x, p->d_flag);
+            coarsen_all(g, st);
+            li = pcg(g, g->x, g->rhs, p->lin_tol, maxlin, st);
+            if (li < 0) { status = li; fail = true; break; }
+            lin += li;
+            k_np_finish<<<G, 256, 0, st>>>(N, (double)p->q[i], p->lambda_rho, p->rho_mix, 1.0 / p->rho_b[i], d_phi,
+                                           g->mu + i * N, g->x, d_rho + i * N, g->dmax, p->d_flag);
+        }
+        if (fail) break;
+        // 5. residual and status
+        unsigned long long hm = 0;
+        int hf = 0;
+        cudaMemcpyAsync(&hm, g->dmax, sizeof(hm), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&hf, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { status = cuda_status(e); break; }
+        double m;
+        std::memcpy(&m, &hm, sizeof(m));
+        res = m;
+        if (hf & kFlagPacking) { status = PNP_ERR_PACKING; break; }
+        if (hf & kFlagOverflow) { status = PNP_ERR_OVERFLOW; break; }
+        if (res < p->tol) { status = PNP_OK; break; }
+    }
+    if (it > p->max_iter) it = p->max_iter;
+    cudaStreamSynchronize(st);
+    cudaFree(d_q);
+    cudaFree(d_rhof);
+    if (stats) {
+        stats->iterations = it;
+        stats->residual = res;
+        stats->linear_iterations = lin;
+        stats->status = status;
+    }
+    return status;
+}
+
+}  // namespace pnp

@@ -1,0 +1,139 @@
+// Internal declarations of libpnp_gb300 (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pnp.h"
+
+namespace pnp {
+
+constexpr int kNumWeighted = 10;   // n0, n1, n2, n3, n1x, n1y, n1z, n2x, n2y, n2z (Sec 2.3.1)
+constexpr int kNumKernels = 5;     // per species: shell, ball, vector shell x, y, z
+constexpr int kMaxStages = 16;
+
+// Mixed-radix (4, 2, 3, 5) Stockham plan of one axis.
+struct FftAxis {
+    int L;
+    int nst;
+    int radix[kMaxStages];
+};
+
+bool smooth235(int n);
+int next_smooth(int n, bool even);
+FftAxis make_axis(int L);
+
+// Quadrature stencil on [-S, S]^3, stored [mz][my][mx] (Sec 3.5 reading).
+struct Stencil {
+    int S = 0;
+    std::vector<double> K;   // (2S+1)^3
+    double &at(int mx, int my, int mz) {
+        int w = 2 * S + 1;
+        return K[((size_t)(mz + S) * w + (my + S)) * w + (mx + S)];
+    }
+};
+
+struct DeviceBuffers;   // per-precision device state of the mu_ex pipeline
+
+constexpr int kNumStages = 9;
+struct StageTimer {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;          // free events
+    std::vector<int> stage;                 // stage id of each recorded pair
+    std::vector<cudaEvent_t> ev0, ev1;      // recorded pairs
+    cudaEvent_t get();
+    void begin(int s, cudaStream_t st);
+    void end(cudaStream_t st);
+    int collect(double *ms, int *launches, int max);
+    void release();
+};
+struct GummelState;     // device state of the Gummel solve
+
+struct Problem {
+    // ---- descriptor (copied) ----
+    int nx = 0, ny = 0, nz = 0;
+    int bc[3] = {0, 0, 0};
+    int s = 0;
+    std::vector<int> q;
+    std::vector<double> R, rho_b, D, depth;
+    double well_inner = 0, well_outer = 0;
+    std::vector<double> sites;
+    double site_alpha = 1.0;
+    std::vector<double> rho_f;
+    double temperature_K = 300, eps_r = 16.6, h_nm = 1.0, lB = 0;
+    double phi_lo = 0, phi_hi = 0, lambda_phi = 0.3, lambda_rho = 0.3;
+    int rho_mix = 0;
+    double tol = 1e-8;
+    int max_iter = 500;
+    int quad[3] = {0, 0, 0}, wquad[3] = {0, 0, 0};
+    int sw_half = 1;
+    int precision = 0;
+    double lin_tol = 1e-12;
+    bool has_wells = false;
+
+    // ---- plan ----
+    int L[3] = {0, 0, 0};
+    int S = 0, Ssw = 0;
+    FftAxis ax[3];
+    std::vector<double> mu_bulk;      // reservoir mu_ex (bulk Rosenfeld)
+
+    // ---- device ----
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int *d_flag = nullptr;            // device status bits
+    double *d_U = nullptr;            // square-well field sum_m K_sw[m] rho_s(r+m)
+    std::vector<double> sh_coef;      // mu_sh,i = sh_coef[i] * U
+    double *d_sh_coef = nullptr;
+    DeviceBuffers *buf[2] = {nullptr, nullptr};   // FP64, FP32
+    void *d_work = nullptr;           // shared FFT workspace
+    size_t work_bytes = 0;
+    double *d_io = nullptr;           // staging for host-pointer calls (s+1 fields)
+    GummelState *gs = nullptr;
+    size_t device_bytes = 0;
+    int deferred = 0;                 // host-side deferred status
+    StageTimer timer;
+    int mg_levels = 0;
+
+    size_t npts() const { return (size_t)nx * ny * nz; }
+};
+
+// plan.cpp
+int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why);
+int plan_lengths(Problem *p, const int fft_len[3]);
+void gauss_legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w);
+void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil out[kNumKernels]);
+void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
+void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
+double bjerrum_length_h(double T, double eps_r, double h_nm);
+void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu);
+
+// mu_ex.cu
+int mu_ex_setup(Problem *p);                 // workspace, spectra, mu_sh
+int mu_ex_prepare(Problem *p, int prec);     // lazily build one precision's buffers
+int mu_ex_enqueue(Problem *p, int prec, const double *d_rho, double *d_mu, cudaStream_t st);
+void mu_ex_free(Problem *p);
+
+// gummel.cu
+int gummel_setup(Problem *p);
+int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho,
+               pnp_stats *stats, cudaStream_t st);
+void gummel_free(Problem *p);
+
+// api.cpp helpers
+int cuda_status(cudaError_t e);
+int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why);
+void destroy_problem_internal(Problem *p);
+
+// device status bits
+enum : int { kFlagPacking = 1, kFlagOverflow = 2, kFlagNonFinite = 4, kFlagTimeout = 8 };
+
+}  // namespace pnp
+
+struct pnp_problem {
+    pnp::Problem *impl;
+};

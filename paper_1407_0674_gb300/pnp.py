@@ -1,0 +1,328 @@
+"""Thin ctypes binding of libpnp_gb300 (include/pnp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The library must have been built (``paper_1407_0674_gb300.build``);
+a missing library raises instead of falling back to anything else.
+
+A problem description is any object with the attributes of
+``workloads.ProblemSpec``.  Host calls take and return numpy arrays; the
+``*_device`` calls take objects exposing ``data_ptr()`` (e.g. CUDA tensors)
+and an optional stream handle (int).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpnp_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "pnp.h")
+
+OK = 0
+PENDING = 1
+ERR_INVALID = -1
+ERR_NOMEM = -2
+ERR_CUDA = -3
+ERR_NOT_CONVERGED = -4
+ERR_PACKING = -5
+ERR_OVERFLOW = -6
+ERR_BUSY = -7
+ERR_TIMEOUT = -8
+ERR_UNKNOWN_TICKET = -9
+
+BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
+PREC = {"fp64": 0, "fp32": 1, None: -1, -1: -1, 0: 0, 1: 1}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class Desc(ctypes.Structure):
+    """Mirror of pnp_problem_desc."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("bc", ctypes.c_int * 3),
+        ("nspecies", ctypes.c_int),
+        ("valence", _ip), ("radius", _dp), ("rho_bulk", _dp), ("diffusivity", _dp), ("well_depth", _dp),
+        ("well_inner", ctypes.c_double), ("well_outer", ctypes.c_double),
+        ("nsites", ctypes.c_int), ("site_xyz", _dp), ("site_alpha", ctypes.c_double),
+        ("rho_fixed", _dp),
+        ("temperature_K", ctypes.c_double), ("eps_r", ctypes.c_double), ("h_nm", ctypes.c_double),
+        ("phi_lo", ctypes.c_double), ("phi_hi", ctypes.c_double),
+        ("lambda_phi", ctypes.c_double), ("lambda_rho", ctypes.c_double),
+        ("rho_mix", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("quad_nmu", ctypes.c_int), ("quad_ntheta", ctypes.c_int), ("quad_nr", ctypes.c_int),
+        ("well_nmu", ctypes.c_int), ("well_ntheta", ctypes.c_int), ("well_nr", ctypes.c_int),
+        ("sw_half", ctypes.c_int),
+        ("fft_len", ctypes.c_int * 3),
+        ("precision", ctypes.c_int),
+        ("lin_tol", ctypes.c_double),
+        ("flags", ctypes.c_uint),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("residual", ctypes.c_double),
+                ("linear_iterations", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("fft_len", ctypes.c_int * 3), ("stencil_halfwidth", ctypes.c_int),
+                ("well_halfwidth", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("mg_levels", ctypes.c_int)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("active", ctypes.c_int), ("queued", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t)]
+
+
+class PnpError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {error_string(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpnp_gb300.so not built ({LIB_PATH}); run paper_1407_0674_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.pnp_desc_init.argtypes = [ctypes.POINTER(Desc)]
+        L.pnp_create_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
+        L.pnp_destroy_problem.argtypes = [vp]
+        L.pnp_destroy_problem.restype = None
+        L.pnp_get_problem_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.pnp_excess_mu.argtypes = [vp, _dp, _dp, ctypes.c_int]
+        L.pnp_excess_mu_device.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.pnp_status.argtypes = [vp]
+        L.pnp_gummel_solve.argtypes = [vp, _dp, _dp, _dp, _dp, ctypes.POINTER(Stats)]
+        L.pnp_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+        L.pnp_server_destroy.argtypes = [vp]
+        L.pnp_server_destroy.restype = None
+        L.pnp_submit.argtypes = [vp, ctypes.POINTER(Desc), _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]
+        L.pnp_poll.argtypes = [vp, ctypes.c_uint64, _dp, _dp, ctypes.POINTER(Stats)]
+        L.pnp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
+        L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
+        L.pnp_stage_name.argtypes = [ctypes.c_int]
+        L.pnp_stage_name.restype = ctypes.c_char_p
+        L.pnp_error_string.argtypes = [ctypes.c_int]
+        L.pnp_error_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/pnp.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pnp_[a-z_]+)\s*\(", txt)))
+
+
+def error_string(code: int) -> str:
+    return lib().pnp_error_string(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise PnpError(rc, where)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+class DescHolder:
+    """pnp_problem_desc filled from a problem description, with the arrays it
+    points to kept alive."""
+
+    def __init__(self, spec, precision="fp64"):
+        d = Desc()
+        lib().pnp_desc_init(ctypes.byref(d))
+        s = len(spec.R)
+        d.nx, d.ny, d.nz = spec.nx, spec.ny, spec.nz
+        for c in range(3):
+            d.bc[c] = BC.get(spec.bc[c], spec.bc[c]) if isinstance(spec.bc[c], int) else BC[spec.bc[c]]
+        d.nspecies = s
+        self._q = np.ascontiguousarray(np.asarray(spec.q, dtype=np.int32))
+        self._R = _f64(spec.R)
+        self._rb = _f64(spec.rho_b)
+        self._D = None if spec.D is None else _f64(spec.D)
+        self._dep = None if spec.depth is None else _f64(spec.depth)
+        sites = None if spec.sites is None else _f64(np.asarray(spec.sites).reshape(-1, 3))
+        self._sites = sites
+        self._rf = None if spec.rho_f is None else _f64(spec.rho_f).reshape(-1)
+        d.valence = self._q.ctypes.data_as(_ip)
+        d.radius = _ptr(self._R)
+        d.rho_bulk = _ptr(self._rb)
+        d.diffusivity = _ptr(self._D)
+        d.well_depth = _ptr(self._dep)
+        d.well_inner, d.well_outer = spec.well_inner, spec.well_outer
+        d.nsites = 0 if sites is None else sites.shape[0]
+        d.site_xyz = _ptr(sites) if d.nsites else None
+        d.site_alpha = spec.site_alpha
+        d.rho_fixed = _ptr(self._rf)
+        d.temperature_K, d.eps_r, d.h_nm = spec.temperature_K, spec.eps_r, spec.h_nm
+        d.phi_lo, d.phi_hi = spec.phi_lo, spec.phi_hi
+        d.lambda_phi, d.lambda_rho = spec.lambda_phi, spec.lambda_rho
+        d.rho_mix = int(getattr(spec, "rho_mix", 0))
+        d.tol, d.max_iter = spec.tol, spec.max_iter
+        d.quad_nmu, d.quad_ntheta, d.quad_nr = spec.quad_nmu, spec.quad_ntheta, spec.quad_nr
+        d.well_nmu, d.well_ntheta, d.well_nr = spec.well_nmu, spec.well_ntheta, spec.well_nr
+        d.sw_half = 1 if spec.sw_half else 0
+        for c in range(3):
+            d.fft_len[c] = int(spec.fft_len[c])
+        d.precision = PREC[precision]
+        d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
+        self.desc = d
+
+
+class Problem:
+    """Owns a pnp_problem handle."""
+
+    def __init__(self, spec, precision="fp64"):
+        self.spec = spec
+        self.s = len(spec.R)
+        self.shape = (spec.nz, spec.ny, spec.nx)
+        self._dh = DescHolder(spec, precision)
+        h = ctypes.c_void_p()
+        _check(lib().pnp_create_problem(ctypes.byref(self._dh.desc), ctypes.byref(h)), "pnp_create_problem")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().pnp_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        i = Info()
+        _check(lib().pnp_get_problem_info(self.h, ctypes.byref(i)), "pnp_get_problem_info")
+        return {"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
+                "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "mg_levels": i.mg_levels}
+
+    def excess_mu(self, rho, precision=None):
+        """pnp_excess_mu on host arrays; returns mu_ex [s, nz, ny, nx]."""
+        r = _f64(rho)
+        assert r.shape == (self.s,) + self.shape
+        out = np.empty_like(r)
+        _check(lib().pnp_excess_mu(self.h, _ptr(r), _ptr(out), PREC[precision]), "pnp_excess_mu")
+        return out
+
+    def excess_mu_device(self, d_rho, d_mu, precision=None, stream=None):
+        """pnp_excess_mu_device on device buffers (objects with data_ptr())."""
+        rc = lib().pnp_excess_mu_device(self.h, ctypes.c_void_p(d_rho.data_ptr()), ctypes.c_void_p(d_mu.data_ptr()),
+                                        PREC[precision], None if stream is None else ctypes.c_void_p(stream))
+        _check(rc, "pnp_excess_mu_device")
+
+    def status(self):
+        return lib().pnp_status(self.h)
+
+    def stage_timing(self, enable=True):
+        _check(lib().pnp_stage_timing(self.h, 1 if enable else 0), "pnp_stage_timing")
+
+    def stage_times(self):
+        """{stage name: (total ms, launches)} since the last read."""
+        ms = np.zeros(16)
+        n = np.zeros(16, dtype=np.int32)
+        k = lib().pnp_stage_times(self.h, _ptr(ms), n.ctypes.data_as(_ip), 16)
+        if k < 0:
+            raise PnpError(k, "pnp_stage_times")
+        return {lib().pnp_stage_name(j).decode(): (float(ms[j]), int(n[j])) for j in range(k)}
+
+    def gummel_solve(self, phi0=None, rho0=None, raise_on_error=True):
+        """pnp_gummel_solve; returns (phi, rho, stats dict)."""
+        phi = np.empty(self.shape)
+        rho = np.empty((self.s,) + self.shape)
+        st = Stats()
+        p0 = None if phi0 is None else _f64(phi0)
+        r0 = None if rho0 is None else _f64(rho0)
+        rc = lib().pnp_gummel_solve(self.h, _ptr(p0), _ptr(r0), _ptr(phi), _ptr(rho), ctypes.byref(st))
+        stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
+                 "linear_iterations": st.linear_iterations, "seconds": st.seconds}
+        if raise_on_error and rc not in (OK,):
+            raise PnpError(rc, "pnp_gummel_solve")
+        return phi, rho, stats
+
+
+class Server:
+    """Owns a pnp_server handle."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=0, max_queue=0):
+        o = ServerOpts(hbm_budget_bytes, max_slots, max_queue)
+        h = ctypes.c_void_p()
+        _check(lib().pnp_server_create(ctypes.byref(o), ctypes.byref(h)), "pnp_server_create")
+        self.h = h
+        self._shapes = {}
+
+    def close(self):
+        if self.h:
+            lib().pnp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, spec, phi0=None, rho0=None):
+        dh = DescHolder(spec)
+        t = ctypes.c_uint64()
+        p0 = None if phi0 is None else _f64(phi0)
+        r0 = None if rho0 is None else _f64(rho0)
+        rc = lib().pnp_submit(self.h, ctypes.byref(dh.desc), _ptr(p0), _ptr(r0), ctypes.byref(t))
+        if rc != OK:
+            return rc, None
+        self._shapes[t.value] = (len(spec.R), (spec.nz, spec.ny, spec.nx))
+        return OK, t.value
+
+    def poll(self, ticket):
+        """Returns (code, phi, rho, stats); phi/rho are None while pending."""
+        s, shape = self._shapes.get(ticket, (1, (1, 1, 1)))
+        phi = np.empty(shape)
+        rho = np.empty((s,) + shape)
+        st = Stats()
+        rc = lib().pnp_poll(self.h, ctypes.c_uint64(ticket), _ptr(phi), _ptr(rho), ctypes.byref(st))
+        if rc == PENDING:
+            return rc, None, None, None
+        self._shapes.pop(ticket, None)
+        stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
+                 "linear_iterations": st.linear_iterations, "seconds": st.seconds}
+        return rc, phi, rho, stats
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().pnp_server_get_stats(self.h, ctypes.byref(st)), "pnp_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}

@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/pnp.h declares, its descriptor layout matches the
+header (checked with the C compiler), and descriptor validation rejects bad
+input before touching the device."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1407_0674_gb300 import build, pnp
+from workloads import ProblemSpec, mu_microbench, film_gummel
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return pnp.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = pnp.header_functions()
+    assert "pnp_create_problem" in names and "pnp_excess_mu" in names and "pnp_gummel_solve" in names
+    assert "pnp_submit" in names and "pnp_poll" in names
+    for n in names:
+        assert hasattr(L, n), f"{n} declared but not exported"
+
+
+def test_descriptor_layout_matches_header(L):
+    fields = [f for f, _ in pnp.Desc._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"pnp.h\"\nint main(void){\n"
+    prog += 'printf("%zu\\n", sizeof(pnp_problem_desc));\n'
+    for f in fields:
+        prog += f'printf("%zu\\n", offsetof(pnp_problem_desc, {f}));\n'
+    for t in ("pnp_stats", "pnp_problem_info", "pnp_server_opts", "pnp_server_stats"):
+        prog += f'printf("%zu\\n", sizeof({t}));\n'
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert out[0] == ctypes.sizeof(pnp.Desc)
+    for f, off in zip(fields, out[1:1 + len(fields)]):
+        assert getattr(pnp.Desc, f).offset == off, f
+    rest = out[1 + len(fields):]
+    assert rest == [ctypes.sizeof(pnp.Stats), ctypes.sizeof(pnp.Info), ctypes.sizeof(pnp.ServerOpts),
+                    ctypes.sizeof(pnp.ServerStats)]
+
+
+def test_error_strings(L):
+    for code in range(-9, 2):
+        assert pnp.error_string(code) != "unknown error"
+    assert pnp.error_string(-42) == "unknown error"
+
+
+def _create(spec):
+    dh = pnp.DescHolder(spec)
+    h = ctypes.c_void_p()
+    return pnp.lib().pnp_create_problem(ctypes.byref(dh.desc), ctypes.byref(h)), dh
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda s: setattr(s, "nx", 0),
+    lambda s: setattr(s, "R", (0.0, 2.0)),
+    lambda s: setattr(s, "rho_b", (-1.0, 0.01)),
+    lambda s: setattr(s, "lambda_phi", 0.0),
+    lambda s: setattr(s, "lambda_rho", 1.5),
+    lambda s: setattr(s, "tol", 0.0),
+    lambda s: setattr(s, "bc", ("P", "P", 7)),
+    lambda s: setattr(s, "fft_len", (0, 0, 33)),          # below n + S on a zero-extended axis
+    lambda s: setattr(s, "fft_len", (48, 0, 0)),          # periodic axis must use L = n
+    lambda s: setattr(s, "nx", 14),                        # periodic length must be 2^a 3^b 5^c
+    lambda s: setattr(s, "rho_b", (0.05, 0.05)),           # bulk packing above 1
+    lambda s: (setattr(s, "well_inner", 5.0), setattr(s, "well_outer", 4.0)),
+])
+def test_invalid_descriptors_rejected_on_host(L, mutate):
+    spec = film_gummel(32, 32, 32)
+    mutate(spec)
+    rc, _ = _create(spec)
+    assert rc == pnp.ERR_INVALID
+
+
+def test_desc_init_defaults(L):
+    d = pnp.Desc()
+    assert L.pnp_desc_init(ctypes.byref(d)) == 0
+    assert d.lambda_phi == 0.3 and d.max_iter == 500 and d.sw_half == 1 and d.eps_r == 16.6
+    assert L.pnp_desc_init(None) == pnp.ERR_INVALID

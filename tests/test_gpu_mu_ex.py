@@ -1,0 +1,155 @@
+"""GPU parity of mu_ex (pnp_excess_mu through the C ABI) against the FP64 oracle.
+
+Bar: FP64 normwise relative error ||mu - mu_ref||_inf / ||mu_ref||_inf <= 1e-10
+per species; FP32 FFT variant <= 2e-5 (FP32 transforms of O(10) fields with
+~2^-24 rounding per butterfly level, a few 1e-7 expected, bound with margin).
+Cases span several FFT tiles, ragged and odd padded lengths (radix 3 and 5),
+periodic and zero-extended axes, square wells, and the full 128^3 / 256^3
+workload on sampled points.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from workloads import ProblemSpec, bulk_density, film_gummel, lognormal_density, mu_microbench
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def pnp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_0674_gb300 import build, pnp as mod
+    build.build()
+    return mod
+
+
+def normwise(a, b):
+    s = a.shape[0]
+    return max(np.abs(a[i] - b[i]).max() / np.abs(b[i]).max() for i in range(s))
+
+
+def film_rho(spec, seed=3):
+    return lognormal_density(spec, seed, sigma=0.2)
+
+
+CASES = {
+    "three_species_16": lambda: mu_microbench(16),
+    "ragged_13x11x9": lambda: mu_microbench(shape=(13, 11, 9)),
+    "pad_2n_16": lambda: mu_microbench(16, fft_len=32),
+    "small_12": lambda: mu_microbench(12),
+    "film_wells_16": lambda: (lambda s: (s, film_rho(s)))(film_gummel(16, 16, 16)),
+    "film_wells_ragged": lambda: (lambda s: (s, film_rho(s)))(film_gummel(10, 12, 9, nsites=4)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mu_ex_fp64_matches_oracle(pnp, case):
+    spec, rho = CASES[case]()
+    ref, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="fp64")
+        mu2 = P.excess_mu(rho, precision="fp64")
+    assert normwise(mu, ref) <= FP64_TOL
+    np.testing.assert_array_equal(mu, mu2)          # deterministic
+
+
+@pytest.mark.parametrize("case", ["three_species_16", "film_wells_16"])
+def test_mu_ex_fp32_bound(pnp, case):
+    spec, rho = CASES[case]()
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="fp32")
+    err = normwise(mu, ref)
+    assert err <= FP32_TOL, err
+
+
+def test_explicit_odd_lengths(pnp):
+    """Padded lengths with radix-3 and radix-5 stages (x even, y/z odd)."""
+    spec, rho = mu_microbench(shape=(12, 10, 11))
+    spec.fft_len = (30, 15, 25)
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (30, 15, 25)
+        mu = P.excess_mu(rho)
+    assert normwise(mu, ref) <= FP64_TOL
+
+
+def test_device_entry_matches_host_entry(pnp):
+    import torch
+    spec, rho = mu_microbench(16)
+    with pnp.Problem(spec) as P:
+        host = P.excess_mu(rho)
+        d_rho = torch.from_numpy(rho).cuda()
+        d_mu = torch.empty_like(d_rho)
+        stream = torch.cuda.Stream()
+        P.excess_mu_device(d_rho, d_mu, stream=stream.cuda_stream)
+        assert P.status() == 0
+        np.testing.assert_array_equal(d_mu.cpu().numpy(), host)
+
+
+def test_full_size_sampled(pnp):
+    """The benchmark workload itself (128^3, 3 species, padded to 256^3) on
+    sampled points, including faces, edges and corners of the domain."""
+    spec, rho = mu_microbench(128, fft_len=256)
+    rng = np.random.default_rng(0)
+    n = 128
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n // 2, n // 2, n // 2), (1, 2, n - 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(15)]
+    flat = np.array([(z * n + y) * n + x for x, y, z in pts])
+    ref = oracle.excess_mu_sampled(spec, rho, flat)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="fp64").reshape(3, -1)
+        mu32 = P.excess_mu(rho, precision="fp32").reshape(3, -1)
+    for i in range(3):
+        scale = np.abs(mu[i]).max()
+        assert np.abs(mu[i, flat] - ref[i]).max() / scale <= FP64_TOL
+        assert np.abs(mu32[i, flat] - ref[i]).max() / scale <= FP32_TOL
+
+
+def test_packing_error_reported(pnp):
+    spec, rho = mu_microbench(12)
+    rho = rho * 12.0     # total packing 3.6 > 1
+    with pnp.Problem(spec) as P:
+        with pytest.raises(pnp.PnpError) as e:
+            P.excess_mu(rho)
+        assert e.value.code == pnp.ERR_PACKING
+        # the problem stays usable
+        P.excess_mu(mu_microbench(12)[1])
+
+
+def test_invalid_density_rejected(pnp):
+    spec, rho = mu_microbench(8)
+    rho[0, 0, 0, 0] = -1.0
+    with pnp.Problem(spec) as P:
+        with pytest.raises(pnp.PnpError) as e:
+            P.excess_mu(rho)
+        assert e.value.code == pnp.ERR_INVALID
+        rho[0, 0, 0, 0] = np.nan
+        with pytest.raises(pnp.PnpError):
+            P.excess_mu(rho)
+
+
+def test_empty_density_gives_zero_hard_sphere_part(pnp):
+    spec, rho = mu_microbench(8)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(np.zeros_like(rho))
+    assert np.abs(mu).max() == 0.0
+
+
+def test_uniform_periodic_bulk_equals_closed_form(pnp):
+    R = 2.0
+    eta = 0.3
+    rb = bulk_density(eta, R)
+    spec = ProblemSpec(nx=16, ny=16, nz=16, bc=("P", "P", "P"), R=(R,), q=(1,), rho_b=(rb,))
+    rho = np.full((1, 16, 16, 16), rb)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho)
+    py = -np.log(1 - eta) + eta * (14 - 13 * eta + 5 * eta ** 2) / (2 * (1 - eta) ** 3)
+    np.testing.assert_allclose(mu, py, rtol=1e-12)
