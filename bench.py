@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=40, help="edge of the oracle sample box")
     ap.add_argument("--ref-sample", type=int, default=24, help="edge of the reference-arm sample box")
+    ap.add_argument("--n", type=int, default=N_EDGE, help="grid edge (profiling runs use smaller cases)")
+    ap.add_argument("--pad", type=int, default=PAD, help="padded FFT length")
+    ap.add_argument("--variants", default="fp64,fp32", help="precisions to time, headline first")
     return ap.parse_args()
 
 
@@ -234,8 +237,9 @@ def run_gpu(args, world, rank, local):
 
     torch.cuda.set_device(local)
     lb.build()
-    spec, rho = mu_microbench(N_EDGE, fft_len=PAD)
+    spec, rho = mu_microbench(args.n, fft_len=args.pad)
     npts = spec.npoints
+    variants = args.variants.split(",")
     P = pnp.Problem(spec)
     info = P.info()
     d_rho = torch.from_numpy(rho).cuda()
@@ -250,7 +254,7 @@ def run_gpu(args, world, rank, local):
     def step(prec):
         P.excess_mu_device(d_rho, d_mu, precision=prec, stream=sh)
 
-    for prec in ("fp64", "fp32"):
+    for prec in variants:
         for _ in range(args.warmup):
             step(prec)
     torch.cuda.synchronize()
@@ -260,12 +264,12 @@ def run_gpu(args, world, rank, local):
 
     results = {}
     clocks = None
-    for prec in ("fp64", "fp32"):
+    for prec in variants:
         P.stage_times()                      # reset the record
         P.stage_timing(True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        sampler = ClockSampler(local) if prec == "fp64" else None
+        sampler = ClockSampler(local) if prec == variants[0] else None
         if sampler:
             sampler.start()
             time.sleep(0.3)
@@ -296,11 +300,11 @@ def run_gpu(args, world, rank, local):
     import ctypes
     dp = ctypes.POINTER(ctypes.c_double)
     for _ in range(2):
-        lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), 0)
+        lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), pnp.PREC[variants[0]])
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r = lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), 0)
+        r = lib.pnp_excess_mu(P.h, h_rho.ctypes.data_as(dp), h_mu.ctypes.data_as(dp), pnp.PREC[variants[0]])
         if r != 0:
             raise RuntimeError(f"pnp_excess_mu {r}")
     e2e_ms = reduce_max(world, (time.perf_counter() - t0) / args.steps * 1e3)
@@ -346,27 +350,30 @@ def run_gpu(args, world, rank, local):
                          f"{dt:.1f} s"}
 
     if rank == 0:
-        v64 = world * npts / (results["fp64"]["ms"] * 1e-3) / 1e9
-        v32 = world * npts / (results["fp32"]["ms"] * 1e-3) / 1e9
-        launches = sum(n for _, n in results["fp64"]["stages"].values())
+        head = variants[0]
+        vals = {p: world * npts / (results[p]["ms"] * 1e-3) / 1e9 for p in variants}
+        launches = sum(n for _, n in results[head]["stages"].values())
         line = {
-            "metric": "mu_ex Gpoints/s", "value": v64, "unit": "Gpoints/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": results["fp64"]["ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": "mu_ex Gpoints/s", "value": vals[head], "unit": "Gpoints/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": results[head]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "f32 FFT / f64 derivatives",
             "data": "synthetic",
-            "config": {"workload": f"mu_ex {N_EDGE}^3 x {SPECIES} species (R 1.5/2/3 h, packing 0.1 each, "
-                                   f"lognormal(0,0.1) seed 2), zero-padded {PAD}^3",
+            "config": {"workload": f"mu_ex {args.n}^3 x {SPECIES} species (R 1.5/2/3 h, packing 0.1 each, "
+                                   f"lognormal(0,0.1) seed 2), zero-padded {args.pad}^3",
                        "fft_len": list(info["fft_len"]), "parallelism": f"replicas x{world}",
                        "l2": "flushed before each step (256 MB write)"},
             "e2e": {"value": world * npts / (e2e_ms * 1e-3) / 1e9, "unit": "Gpoints/s",
                     "h2d_bytes_per_step": int(rho.nbytes), "d2h_bytes_per_step": int(rho.nbytes),
                     "ms_per_step": e2e_ms},
-            "roofline": roof("fp64"),
+            "roofline": roof(head),
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clocks,
-            "variants": {"fp32_fft": {"value": v32, "unit": "Gpoints/s", "ms_per_step": results["fp32"]["ms"],
-                                      "dtype": "f32 FFT / f64 derivatives", "roofline": roof("fp32")}},
+            "variants": {("fp32_fft" if p == "fp32" else p): {
+                "value": vals[p], "unit": "Gpoints/s", "ms_per_step": results[p]["ms"],
+                "dtype": "f64" if p == "fp64" else "f32 FFT / f64 derivatives", "roofline": roof(p)}
+                for p in variants[1:]},
             "stages_ms": {p: {k: v[0] / max(v[1], 1) for k, v in results[p]["stages"].items()}
                           for p in results},
         }

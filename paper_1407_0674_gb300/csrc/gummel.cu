@@ -625,6 +625,14 @@ int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d
     }
     if (it > p->max_iter) it = p->max_iter;
     cudaStreamSynchronize(st);
+    if (status != PNP_OK && status != PNP_ERR_NOT_CONVERGED) {
+        // a packing error in mu_ex poisons everything after it: report it first
+        int hf = 0;
+        if (cudaMemcpy(&hf, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && (hf & kFlagPacking))
+            status = PNP_ERR_PACKING;
+    }
+    cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
     cudaFree(d_q);
     cudaFree(d_rhof);
     if (stats) {

@@ -1,0 +1,128 @@
+"""GPU parity of the relaxed Gummel solve (pnp_gummel_solve through the C ABI)
+against the oracle, plus properties of the converged state.
+
+Bar: converged potentials and densities agree with the oracle to 1e-8
+(normwise relative, phi relative to max(|phi|, phi scale)); fixed-iteration
+trajectories likewise.  Both sides solve their linear systems to a relative
+residual of 1e-13.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from workloads import ProblemSpec, bulk_density, film_gummel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def pnp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1407_0674_gb300 import build, pnp as mod
+    build.build()
+    return mod
+
+
+def dilute(bias_lo, bias_hi, mix=0, tol=1e-11, max_iter=400, shape=(10, 8, 8)):
+    rng = np.random.default_rng(0)
+    nz, ny, nx = shape
+    rb = bulk_density(0.05, 1.0)
+    return ProblemSpec(nx=nx, ny=ny, nz=nz, bc=("P", "P", "D"), R=(1.0, 1.0), q=(1, -1), rho_b=(rb, rb),
+                       depth=(1.0, 0.0), well_inner=2.0, well_outer=3.0,
+                       sites=rng.uniform(0, 1, (3, 3)) * np.array([nx, ny, nz]),
+                       rho_f=rng.normal(0, 0.01, shape), phi_lo=bias_lo, phi_hi=bias_hi,
+                       lambda_phi=0.3, lambda_rho=0.3, rho_mix=mix, tol=tol, max_iter=max_iter, lin_tol=1e-13)
+
+
+def rel(a, b, floor=0.0):
+    return np.abs(a - b).max() / max(np.abs(b).max(), floor)
+
+
+def compare(spec, pnp, phi_floor=1.0):
+    ref = oracle.gummel(spec)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+    assert st["iterations"] == ref["iters"], (st, ref["iters"])
+    assert rel(phi, ref["phi"], phi_floor) <= TOL
+    for i in range(spec.s):
+        assert rel(rho[i], ref["rho"][i]) <= TOL
+    return phi, rho, st, ref
+
+
+@pytest.mark.parametrize("mix", [0, 1])
+def test_trajectory_matches_oracle(pnp, mix):
+    spec = dilute(0.0, 0.5, mix=mix, tol=1e-30, max_iter=6)
+    phi, rho, st, ref = compare(spec, pnp)
+    assert st["status"] == pnp.ERR_NOT_CONVERGED
+
+
+def test_dense_film_trajectory_matches_oracle(pnp):
+    """The film workload's physics (R 2h, packing 0.2 per ion, wells, geometric
+    relaxation 0.05) on a 12^3 grid, five iterations."""
+    spec = film_gummel(12, 12, 12, tol=1e-30, max_iter=5)
+    spec.lin_tol = 1e-13
+    compare(spec, pnp)
+
+
+def test_converged_state_matches_oracle(pnp):
+    spec = dilute(0.0, 0.5)
+    phi, rho, st, ref = compare(spec, pnp)
+    assert st["status"] == 0 and ref["status"] == 0
+
+
+def test_zero_bias_boltzmann(pnp):
+    spec = dilute(0.2, 0.2)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve()
+        mu = P.excess_mu(rho)
+    mub = oracle.bulk_mu(spec.R, spec.rho_b)
+    for i in range(2):
+        q = spec.q[i]
+        ref = spec.rho_b[i] * np.exp(mub[i] + q * 0.2 - q * phi - mu[i])
+        np.testing.assert_allclose(rho[i], ref, rtol=1e-8)
+
+
+def test_flux_conserved_full_size_film(pnp):
+    """The 32^3 film workload converges to 1e-8; the discrete flux through
+    every z plane is then the same for each species."""
+    spec = film_gummel(32, 32, 32, tol=1e-8, max_iter=2000)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve()
+        mu = P.excess_mu(rho)
+    assert st["status"] == 0 and st["residual"] < 1e-8
+    mub = oracle.bulk_mu(spec.R, spec.rho_b)
+    for i in range(2):
+        rbar = rho[i] * np.exp(spec.q[i] * phi + mu[i])
+        f = oracle.np_flux(spec, i, phi, mu[i], mub[i], rbar)
+        assert np.abs(f - f.mean()).max() <= 1e-4 * np.abs(f).max() + 1e-12
+
+
+def test_warm_start_converges_immediately(pnp):
+    spec = dilute(0.0, 0.5)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve()
+        phi2, rho2, st2 = P.gummel_solve(phi0=phi, rho0=rho)
+    assert st2["iterations"] <= 2
+    assert rel(rho2, rho) < 1e-9
+
+
+def test_not_converged_and_invalid(pnp):
+    spec = dilute(0.0, 0.5, max_iter=2)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+        assert st["status"] == pnp.ERR_NOT_CONVERGED and st["iterations"] == 2
+        with pytest.raises(pnp.PnpError) as e:
+            P.gummel_solve(rho0=-np.ones((2,) + spec.shape))
+        assert e.value.code == pnp.ERR_INVALID
+        with pytest.raises(pnp.PnpError) as e:
+            P.gummel_solve(rho0=np.full((2,) + spec.shape, 0.5))    # packing far above 1
+        assert e.value.code == pnp.ERR_PACKING
+    bad = dilute(0.0, 0.5)
+    bad.bc = ("D", "P", "D")
+    with pnp.Problem(bad) as P:
+        with pytest.raises(pnp.PnpError) as e:
+            P.gummel_solve()
+        assert e.value.code == pnp.ERR_INVALID
