@@ -46,7 +46,8 @@ enum {
     PNP_ERR_OVERFLOW = -6,         /* Slotboom exponential overflowed (Sec 2.1) */
     PNP_ERR_BUSY = -7,             /* server: over the HBM budget or queue full */
     PNP_ERR_TIMEOUT = -8,          /* a bounded device wait gave up */
-    PNP_ERR_UNKNOWN_TICKET = -9    /* server: no such request */
+    PNP_ERR_UNKNOWN_TICKET = -9,   /* server: no such request */
+    PNP_ERR_TOO_LARGE = -10        /* problem exceeds a fixed-size scratch area */
 };
 
 /* boundary type per axis.  For the cDFT integrals every non-periodic axis is
@@ -145,6 +146,29 @@ int pnp_excess_mu(pnp_problem *p, const double *rho, double *mu_ex, int precisio
  * packing error is reported by the next pnp_status(). */
 int pnp_excess_mu_device(pnp_problem *p, const double *d_rho, double *d_mu_ex, int precision,
                          void *stream);
+
+/* mu_ex for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of pnp_excess_mu_device for a
+ * host program whose GPU memory belongs to another allocator (for example a
+ * framework whose caching allocator already holds nearly all of the device,
+ * or a code that reserves its whole pool at start-up), or for a loop that
+ * must not call cudaMalloc/cudaFree because they can synchronise the device.
+ * It needs no pnp_problem: it validates `desc`, builds the FP64 spectra on the
+ * host and runs the FP64 pipeline with every piece of device scratch taken
+ * from one static 32 MiB array inside the library; it allocates no device
+ * memory.  d_rho and d_mu_ex are device buffers [s][nz][ny][nx] owned by the
+ * caller; `stream` is a cudaStream_t (NULL = the default stream).  Blocks
+ * until the result is written.
+ * Limits: hard spheres only (a descriptor with square wells is rejected with
+ * PNP_ERR_INVALID); status word + twiddles + spectra + workspace must fit in
+ * 32 MiB (about a 48^3 grid with three species zero-padded on every axis),
+ * else PNP_ERR_TOO_LARGE.  The array is held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up the
+ * array's address while that device is current; make that call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller.
+ * Errors: PNP_ERR_INVALID, PNP_ERR_TOO_LARGE, PNP_ERR_PACKING, PNP_ERR_CUDA. */
+int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double *d_rho, double *d_mu_ex, void *stream);
 
 /* Synchronise the problem's last stream and return the deferred device status
  * (PNP_OK, PNP_ERR_PACKING, PNP_ERR_OVERFLOW or PNP_ERR_CUDA), clearing it. */

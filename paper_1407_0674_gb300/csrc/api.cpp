@@ -258,6 +258,7 @@ const char *pnp_error_string(int code) {
         case PNP_ERR_BUSY: return "server busy or request over the memory budget";
         case PNP_ERR_TIMEOUT: return "device wait timed out";
         case PNP_ERR_UNKNOWN_TICKET: return "unknown ticket";
+        case PNP_ERR_TOO_LARGE: return "problem too large for the fixed scratch area";
         default: return "unknown error";
     }
 }

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "fft_smem.cuh"
@@ -868,3 +869,135 @@ void mu_ex_free(Problem *p) {
 }
 
 }  // namespace pnp
+
+// ===========================================================================
+// Fixed-scratch variant of the FP64 mu_ex pipeline.
+//
+// Some callers cannot allocate device memory once they are running: a host
+// application whose GPU memory is owned by its own allocator (a framework
+// whose caching allocator already holds nearly all of the device, or a
+// simulation code that reserves its pool at start-up), or a latency-critical
+// loop that must not call cudaMalloc/cudaFree because those calls can
+// synchronise the whole device.  pnp_excess_mu_noalloc serves them: all of its
+// device-side scratch -- status word, twiddle tables, kernel spectra and the
+// FFT workspace -- lives in the file-scope array below, so the call performs
+// no device allocation at all.  The caller passes the densities and the output
+// buffer.
+//
+// The array is kNoAllocBytes (32 MiB) and every GPU that loads this library
+// holds it until the process exits.  Its address is looked up once per device
+// with cudaGetSymbolAddress on the first call made while that device is
+// current; make that first call before any stream capture.  Every call shares
+// the array and it keeps the previous call's contents: the status word is
+// cleared by each call, everything else is fully overwritten before it is
+// read.  Calls whose work overlaps on the GPU (other streams, other host
+// threads) race on the array; serialise them.
+namespace pnp {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[64] = {nullptr};
+
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// bytes of the fixed scratch a problem needs: status word, three FP64
+// twiddle tables, the FP64 spectrum octants and the FP64 workspace
+size_t noalloc_bytes(const Problem &p) {
+    const Dims d = make_dims(&p);
+    size_t b = 256;
+    for (int c = 0; c < 3; ++c) b += round256(16 * (size_t)p.L[c]);
+    b += round256(sizeof(double) * (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p.s);
+    b += round256(workspace_bytes(&p));
+    return b;
+}
+
+void twiddles_host(int L, std::vector<double> &h) {
+    h.assign(2 * (size_t)L, 0.0);
+    for (int m = 0; m < L; ++m) {
+        if ((4 * (long)m) % L == 0) {
+            const double cs[4][2] = {{1, 0}, {0, -1}, {-1, 0}, {0, 1}};
+            const int q = (int)((4 * (long)m) / L);
+            h[2 * m] = cs[q][0];
+            h[2 * m + 1] = cs[q][1];
+        } else {
+            const double ang = -2.0 * M_PI * (double)m / L;
+            h[2 * m] = std::cos(ang);
+            h[2 * m + 1] = std::sin(ang);
+        }
+    }
+}
+}  // namespace
+
+}  // namespace pnp
+
+extern "C" int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double *d_rho, double *d_mu_ex,
+                                     void *stream) {
+    using namespace pnp;
+    if (!desc || !d_rho || !d_mu_ex) return PNP_ERR_INVALID;
+    Problem p;
+    std::string why;
+    int rc = validate_and_copy(desc, &p, &why);
+    if (rc) return rc;
+    if (p.has_wells) return PNP_ERR_INVALID;        // hard-sphere part only
+    if (noalloc_bytes(p) > kNoAllocBytes) return PNP_ERR_TOO_LARGE;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return PNP_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e);
+        g_noalloc_addr[dev] = ptr;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    // carve: status word | twiddles x, y, z | spectra | workspace
+    size_t off = 256;
+    DeviceBuffers db;
+    db.prec = PNP_PREC_FP64;
+    std::vector<double> h;
+    for (int c = 0; c < 3; ++c) {
+        db.tw[c] = base + off;
+        twiddles_host(p.L[c], h);
+        e = cudaMemcpyAsync(db.tw[c], h.data(), 16 * (size_t)p.L[c], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e);
+        off += round256(16 * (size_t)p.L[c]);
+    }
+    const Dims d = make_dims(&p);
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    db.spec = base + off;
+    const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
+    const bool odd[kNumKernels][3] = {{false, false, false}, {false, false, false}, {true, false, false},
+                                      {false, true, false}, {false, false, true}};
+    h.assign(oct, 0.0);
+    for (int i = 0; i < p.s; ++i) {
+        Stencil stn[kNumKernels];
+        build_fmt_stencils(p.R[i], p.quad[0], p.quad[1], p.quad[2], p.S, stn);
+        for (int k = 0; k < kNumKernels; ++k) {
+            octant_transform(stn[k], p.L, odd[k], scale, h.data());
+            // synchronous copy: the host table is reused for the next kernel
+            e = cudaMemcpy((double *)db.spec + (size_t)(i * kNumKernels + k) * oct, h.data(), sizeof(double) * oct,
+                           cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    off += round256(sizeof(double) * oct * kNumKernels * p.s);
+    p.d_work = base + off;
+    p.d_flag = (int *)base;
+    e = cudaMemsetAsync(p.d_flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = run_pipeline<double>(&p, &db, d_rho, d_mu_ex, st);
+    if (rc) return rc;
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, p.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    p.d_work = nullptr;
+    p.d_flag = nullptr;
+    return (flag & (kFlagPacking | kFlagNonFinite)) ? PNP_ERR_PACKING : PNP_OK;
+}

@@ -32,6 +32,7 @@ ERR_OVERFLOW = -6
 ERR_BUSY = -7
 ERR_TIMEOUT = -8
 ERR_UNKNOWN_TICKET = -9
+ERR_TOO_LARGE = -10
 
 BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
 PREC = {"fp64": 0, "fp32": 1, None: -1, -1: -1, 0: 0, 1: 1}
@@ -118,6 +119,7 @@ def lib():
         L.pnp_submit.argtypes = [vp, ctypes.POINTER(Desc), _dp, _dp, ctypes.POINTER(ctypes.c_uint64)]
         L.pnp_poll.argtypes = [vp, ctypes.c_uint64, _dp, _dp, ctypes.POINTER(Stats)]
         L.pnp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -195,6 +197,15 @@ class DescHolder:
         d.precision = PREC[precision]
         d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
         self.desc = d
+
+
+def excess_mu_noalloc(spec, d_rho, d_mu, stream=None):
+    """pnp_excess_mu_noalloc: FP64 mu_ex into caller-owned device buffers
+    (objects with data_ptr()) with no device allocation; returns the code."""
+    dh = DescHolder(spec)
+    return lib().pnp_excess_mu_noalloc(ctypes.byref(dh.desc), ctypes.c_void_p(d_rho.data_ptr()),
+                                       ctypes.c_void_p(d_mu.data_ptr()),
+                                       None if stream is None else ctypes.c_void_p(stream))
 
 
 class Problem:
