@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "fft_smem.cuh"
@@ -42,7 +43,15 @@ struct SpeciesConst {
     double c0[8];      // 1 / (4 pi R^2)
     double c1[8];      // 1 / (4 pi R)
     double sh[8];      // mu_sh coefficient
+    float c0f[8], c1f[8];   // the same, pre-rounded for FP32 kernels
 };
+
+template <typename T> __device__ __forceinline__ T sc_c0(const SpeciesConst &sc, int i);
+template <> __device__ __forceinline__ double sc_c0<double>(const SpeciesConst &sc, int i) { return sc.c0[i]; }
+template <> __device__ __forceinline__ float sc_c0<float>(const SpeciesConst &sc, int i) { return sc.c0f[i]; }
+template <typename T> __device__ __forceinline__ T sc_c1(const SpeciesConst &sc, int i);
+template <> __device__ __forceinline__ double sc_c1<double>(const SpeciesConst &sc, int i) { return sc.c1[i]; }
+template <> __device__ __forceinline__ float sc_c1<float>(const SpeciesConst &sc, int i) { return sc.c1f[i]; }
 
 struct DeviceBuffers {
     int prec = 0;
@@ -68,6 +77,8 @@ static SpeciesConst make_sc(const Problem *p) {
         sc.c0[i] = 1.0 / (4.0 * M_PI * p->R[i] * p->R[i]);
         sc.c1[i] = 1.0 / (4.0 * M_PI * p->R[i]);
         sc.sh[i] = p->has_wells ? p->sh_coef[i] : 0.0;
+        sc.c0f[i] = (float)sc.c0[i];
+        sc.c1f[i] = (float)sc.c1[i];
     }
     return sc;
 }
@@ -107,6 +118,12 @@ __device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double ps
     for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a]);
     return ok;
 }
+
+}  // namespace pnp
+
+#include "mu_ex_reg.cuh"
+
+namespace pnp {
 
 // ---------------------------------------------------------------------------
 // 1: real lines (FP64 input) -> half spectra along x.  Two y-lines share one
@@ -576,6 +593,28 @@ static Work carve(const Problem *p, int prec) {
     return w;
 }
 
+// Padded lengths with a register-resident two-factor FFT (fft_reg.cuh);
+// every other length uses the shared-memory Stockham kernels.
+template <typename F> static bool with_shape(int L, F &&f) {
+    using std::integral_constant;
+    switch (L) {
+        case 32: f(integral_constant<int, 8>{}, integral_constant<int, 4>{}); return true;
+        case 40: f(integral_constant<int, 8>{}, integral_constant<int, 5>{}); return true;
+        case 64: f(integral_constant<int, 8>{}, integral_constant<int, 8>{}); return true;
+        case 128: f(integral_constant<int, 16>{}, integral_constant<int, 8>{}); return true;
+        case 256: f(integral_constant<int, 16>{}, integral_constant<int, 16>{}); return true;
+        default: return false;
+    }
+}
+
+template <auto K> static void ensure_smem() {
+    static const bool done = [] {
+        cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return true;
+    }();
+    (void)done;
+}
+
 template <typename T>
 static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
     using C = typename vec2<T>::type;
@@ -593,37 +632,116 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     const size_t N = p->npts();
     const int T256 = 256;
     StageTimer &tm = p->timer;
-    dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
+    const size_t cs = sizeof(C);
+    const long kBudget = 96 * 1024;
+    auto pow2_le = [](long v) { long r = 1; while (r * 2 <= v) r *= 2; return (int)r; };
+
+    // 1: x forward
     tm.begin(0, st);
-    k_xfwd<T><<<gx, T256, l.sm_x, st>>>(d_rho, N, A, d, p->ax[0], twx, l.P_x);
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int P = std::max(1, std::min(256 / G, d.npairs));
+            ensure_smem<k_xfwd_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz, s);
+            k_xfwd_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(d_rho, N, A, d, twx, P);
+        })) {
+        dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
+        k_xfwd<T><<<gx, T256, l.sm_x, st>>>(d_rho, N, A, d, p->ax[0], twx, l.P_x);
+    }
     tm.end(st);
-    dim3 gy((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, s);
-    tm.begin(1, st);
-    k_ypass<T, false><<<gy, T256, l.sm_y, st>>>(A, Bs, d, d.ny, d.ny, d.Ly, d.Ly, p->ax[1], twy, l.TX_y);
-    tm.end(st);
-    dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);
-    tm.begin(2, st);
-    k_zmac<T><<<gz, T256, l.sm_zmac, st>>>(Bs, B10, d, p->ax[2], twz, spec, sc, l.TX_z);
-    tm.end(st);
-    dim3 gy10((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, kNumWeighted);
-    tm.begin(3, st);
-    k_ypass<T, true><<<gy10, T256, l.sm_y, st>>>(B10, A, d, d.Ly, d.Ly, d.ny, d.ny, p->ax[1], twy, l.TX_y);
-    tm.end(st);
-    dim3 gf((d.npairs + l.P_fused - 1) / l.P_fused, d.nz);
+
+    // y passes: forward (rows ny -> Ly) or inverse (Ly -> ny) of F fields
+    auto ypass = [&](int stage, bool inv, const C *in, C *out, int F) {
+        tm.begin(stage, st);
+        const int rows_in = inv ? d.Ly : d.ny, rows_out = inv ? d.ny : d.Ly;
+        if (!with_shape(d.Ly, [&](auto a, auto b) {
+                constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                const int TX = pow2_le(std::min<long>(256 / G, 16));
+                dim3 g((d.Wx + TX - 1) / TX, d.nz, F);
+                const size_t sm = (size_t)TX * Shape<N1, N2>::EX * cs;
+                if (inv) {
+                    ensure_smem<k_ypass_r<T, true, N1, N2>>();
+                    k_ypass_r<T, true, N1, N2><<<g, TX * G, sm, st>>>(in, out, d, rows_in, rows_in, rows_out,
+                                                                     rows_out, twy, TX);
+                } else {
+                    ensure_smem<k_ypass_r<T, false, N1, N2>>();
+                    k_ypass_r<T, false, N1, N2><<<g, TX * G, sm, st>>>(in, out, d, rows_in, rows_in, rows_out,
+                                                                      rows_out, twy, TX);
+                }
+            })) {
+            dim3 g((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, F);
+            if (inv)
+                k_ypass<T, true><<<g, T256, l.sm_y, st>>>(in, out, d, rows_in, rows_in, rows_out, rows_out,
+                                                         p->ax[1], twy, l.TX_y);
+            else
+                k_ypass<T, false><<<g, T256, l.sm_y, st>>>(in, out, d, rows_in, rows_in, rows_out, rows_out,
+                                                          p->ax[1], twy, l.TX_y);
+        }
+        tm.end(st);
+    };
+
+    // z column kernels (MAC forward / back)
+    auto zpass = [&](int stage, bool back) {
+        tm.begin(stage, st);
+        if (!with_shape(d.Lz, [&](auto a, auto b) {
+                constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
+                const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(256 / G, 16), kBudget / per_col)));
+                dim3 g((d.Wx + TX - 1) / TX, d.Ly);
+                if (back) {
+                    ensure_smem<k_zback_r<T, N1, N2>>();
+                    k_zback_r<T, N1, N2><<<g, TX * G, TX * per_col, st>>>(B10, Bs, d, twz, spec, sc, TX);
+                } else {
+                    ensure_smem<k_zmac_r<T, N1, N2>>();
+                    k_zmac_r<T, N1, N2><<<g, TX * G, TX * per_col, st>>>(Bs, B10, d, twz, spec, sc, TX);
+                }
+            })) {
+            dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);
+            if (back)
+                k_zback<T><<<gz, T256, l.sm_zback, st>>>(B10, Bs, d, p->ax[2], twz, spec, sc, l.TX_z);
+            else
+                k_zmac<T><<<gz, T256, l.sm_zmac, st>>>(Bs, B10, d, p->ax[2], twz, spec, sc, l.TX_z);
+        }
+        tm.end(st);
+    };
+
+    ypass(1, false, A, Bs, s);
+    zpass(2, false);
+    ypass(3, true, B10, A, kNumWeighted);
+
+    // 5: x fused inverse -> dPhi/dn -> forward
     tm.begin(4, st);
-    k_xfused<T><<<gf, T256, l.sm_fused, st>>>(A, d, p->ax[0], twx, p->d_flag, l.P_fused);
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int NQ = std::min(N2, (d.nx + N1 - 1) / N1);
+            const long per_pair = ((long)kNumWeighted * NQ * N1 + Shape<N1, N2>::EX) * (long)cs;
+            const int P = (int)std::max<long>(1, std::min<long>(std::min<long>(256 / G, d.npairs), kBudget / per_pair));
+            ensure_smem<k_xfused_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz);
+            k_xfused_r<T, N1, N2><<<g, P * G, P * per_pair, st>>>(A, d, twx, p->d_flag, P, NQ);
+        })) {
+        dim3 gf((d.npairs + l.P_fused - 1) / l.P_fused, d.nz);
+        k_xfused<T><<<gf, T256, l.sm_fused, st>>>(A, d, p->ax[0], twx, p->d_flag, l.P_fused);
+    }
     tm.end(st);
-    tm.begin(5, st);
-    k_ypass<T, false><<<gy10, T256, l.sm_y, st>>>(A, B10, d, d.ny, d.ny, d.Ly, d.Ly, p->ax[1], twy, l.TX_y);
-    tm.end(st);
-    tm.begin(6, st);
-    k_zback<T><<<gz, T256, l.sm_zback, st>>>(B10, Bs, d, p->ax[2], twz, spec, sc, l.TX_z);
-    tm.end(st);
-    tm.begin(7, st);
-    k_ypass<T, true><<<gy, T256, l.sm_y, st>>>(Bs, A, d, d.Ly, d.Ly, d.ny, d.ny, p->ax[1], twy, l.TX_y);
-    tm.end(st);
+
+    ypass(5, false, A, B10, kNumWeighted);
+    zpass(6, true);
+    ypass(7, true, Bs, A, s);
+
+    // 9: x inverse + mu_sh
     tm.begin(8, st);
-    k_xinv<T><<<gx, T256, l.sm_x, st>>>(A, d_mu, N, d, p->ax[0], twx, p->has_wells ? p->d_U : nullptr, sc, l.P_x);
+    const double *U = p->has_wells ? p->d_U : nullptr;
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int P = std::max(1, std::min(256 / G, d.npairs));
+            ensure_smem<k_xinv_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz, s);
+            k_xinv_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(A, d_mu, N, d, twx, U, sc, P);
+        })) {
+        dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
+        k_xinv<T><<<gx, T256, l.sm_x, st>>>(A, d_mu, N, d, p->ax[0], twx, U, sc, l.P_x);
+    }
     tm.end(st);
     return cuda_status(cudaGetLastError());
 }

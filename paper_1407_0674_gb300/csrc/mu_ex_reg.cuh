@@ -1,0 +1,409 @@
+// mu_ex pipeline kernels on the register-resident two-factor FFT
+// (fft_reg.cuh).  Same passes, layouts and arithmetic as the shared-memory
+// Stockham kernels in mu_ex.cu; used for every axis whose padded length has a
+// two-factor shape (see fast_shape()).  Included by mu_ex.cu only.
+#pragma once
+
+#include "fft_reg.cuh"
+
+namespace pnp {
+
+// R2C of two real lines packed as one complex line: given Z = FFT(a + i b)
+// in natural order in `z`, write X = FFT(a), Y = FFT(b) for k < Wx.
+template <typename C>
+__device__ __forceinline__ void untangle_store(const C *z, int L, int Wx, int lane, int G, C *dst0, C *dst1) {
+    using T = decltype(z[0].x);
+    for (int k = lane; k < Wx; k += G) {
+        const C zk = z[k];
+        const C zm = z[(L - k) % L];
+        dst0[k] = C{(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
+        if (dst1) dst1[k] = C{(T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x)};
+    }
+}
+
+// Z_k = X_k + i Y_k for the half spectra X (line y0) and Y (line y0 + 1) of two
+// real lines; k > L/2 from Hermitian symmetry.
+template <typename C>
+__device__ __forceinline__ C pack_two(const C *__restrict__ x0, const C *__restrict__ x1, int k, int L) {
+    const bool up = k > L / 2;
+    const int kk = up ? L - k : k;
+    C X = x0[kk];
+    C Y = x1 ? x1[kk] : C{0, 0};
+    if (up) {
+        X.y = -X.y;
+        Y.y = -Y.y;
+    }
+    return C{X.x - Y.y, X.y + Y.x};
+}
+
+// ---------------------------------------------------------------------------
+// x forward (R2C, two real lines per complex FFT).  block P*G, grid (ceil(npairs/P), nz, F)
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_xfwd_r(const double *__restrict__ in, size_t in_fstride,
+                                                 typename vec2<T>::type *__restrict__ A, Dims d,
+                                                 const typename vec2<T>::type *__restrict__ tw, int P) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX, L = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = threadIdx.x / G, t = threadIdx.x % G;
+    C *ex = reinterpret_cast<C *>(smem_raw) + p * EX;
+    const int z = blockIdx.y, f = blockIdx.z, y0 = 2 * (blockIdx.x * P + p);
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    const double *src = in + f * in_fstride + (size_t)z * d.ny * d.nx;
+    if (t < N1) {
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int x = t + N1 * n2;
+            T re = 0, im = 0;
+            if (x < d.nx && y0 < d.ny) {
+                re = (T)src[(size_t)y0 * d.nx + x];
+                if (y0 + 1 < d.ny) im = (T)src[(size_t)(y0 + 1) * d.nx + x];
+            }
+            v[n2] = C{re, im};
+        }
+    }
+    fwd2<N1, N2>(v, lt, ex, t, 1);
+    if (t < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) ex[t + N2 * k1] = v[k1];
+    }
+    __syncthreads();
+    if (y0 < d.ny) {
+        C *dst = A + ((size_t)f * d.nz + z) * d.ny * d.Wx + (size_t)y0 * d.Wx;
+        untangle_store(ex, L, d.Wx, t, G, dst, y0 + 1 < d.ny ? dst + d.Wx : (C *)nullptr);
+    }
+}
+
+// x inverse (C2R) of F fields, write x < nx as FP64, optionally + coef * U
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__restrict__ A,
+                                                 double *__restrict__ out, size_t out_fstride, Dims d,
+                                                 const typename vec2<T>::type *__restrict__ tw,
+                                                 const double *__restrict__ U, SpeciesConst sc, int P) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX, L = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = threadIdx.x / G, t = threadIdx.x % G;
+    C *ex = reinterpret_cast<C *>(smem_raw) + p * EX;
+    const int z = blockIdx.y, f = blockIdx.z, y0 = 2 * (blockIdx.x * P + p);
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    const C *src = A + ((size_t)f * d.nz + z) * d.ny * d.Wx + (size_t)y0 * d.Wx;
+    if (t < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1)
+            v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
+                              : C{0, 0};
+    }
+    inv2<N1, N2>(v, lt, ex, t, 1);
+    if (t < N1 && y0 < d.ny) {
+        double *dst = out + f * out_fstride + (size_t)z * d.ny * d.nx;
+        const double coef = U ? sc.sh[f] : 0.0;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int x = t + N1 * n2;
+            if (x >= d.nx) continue;
+            double u0 = 0, u1 = 0;
+            if (U) {
+                u0 = coef * U[((size_t)z * d.ny + y0) * d.nx + x];
+                if (y0 + 1 < d.ny) u1 = coef * U[((size_t)z * d.ny + y0 + 1) * d.nx + x];
+            }
+            dst[(size_t)y0 * d.nx + x] = (double)v[n2].x + u0;
+            if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (double)v[n2].y + u1;
+        }
+    }
+}
+
+// x fused: C2R of the ten n_alpha, FP64 dPhi/dn inside the domain, R2C of the
+// ten Psi_alpha, in place in A.  Only the NQ = ceil(nx / N1) lane values that
+// can hold x < nx are kept (Psi is zero beyond nx).
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_xfused_r(typename vec2<T>::type *__restrict__ A, Dims d,
+                                                   const typename vec2<T>::type *__restrict__ tw,
+                                                   int *__restrict__ flag, int P, int NQ) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX, L = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = threadIdx.x / G, t = threadIdx.x % G;
+    C *slots = reinterpret_cast<C *>(smem_raw);                     // [10][NQ][P][N1]
+    C *ex = slots + (size_t)kNumWeighted * NQ * P * N1 + p * EX;
+    auto slot = [&](int a, int q) -> C & { return slots[((a * NQ + q) * P + p) * N1 + t]; };
+    const int z = blockIdx.y, y0 = 2 * (blockIdx.x * P + p);
+    const size_t fstride = (size_t)d.nz * d.ny * d.Wx;
+    C *base = A + (size_t)z * d.ny * d.Wx + (size_t)y0 * d.Wx;
+    const bool live = y0 < d.ny, two = y0 + 1 < d.ny;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    for (int a = 0; a < kNumWeighted; ++a) {
+        if (t < N2) {
+            const C *src = base + a * fstride;
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                v[k1] = live ? pack_two(src, two ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L) : C{0, 0};
+        }
+        inv2<N1, N2>(v, lt, ex, t, 1);
+        if (t < N1) {
+#pragma unroll
+            for (int q = 0; q < N2; ++q)
+                if (q < NQ) slot(a, q) = v[q];
+        }
+    }
+    bool bad = false;
+    if (t < N1) {
+        for (int q = 0; q < NQ; ++q) {
+            const int x = t + N1 * q;
+            for (int h = 0; h < 2; ++h) {
+                const int y = y0 + h;
+                double n[kNumWeighted], psi[kNumWeighted];
+#pragma unroll
+                for (int a = 0; a < kNumWeighted; ++a) {
+                    const C s = slot(a, q);
+                    n[a] = (double)(h ? s.y : s.x);
+                }
+                if (x < d.nx && y < d.ny) {
+                    if (!fmt_dphi(n, psi)) bad = true;
+                } else {
+#pragma unroll
+                    for (int a = 0; a < kNumWeighted; ++a) psi[a] = 0.0;
+                }
+#pragma unroll
+                for (int a = 0; a < kNumWeighted; ++a) {
+                    C &s = slot(a, q);
+                    if (h) s.y = (T)psi[a]; else s.x = (T)psi[a];
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(flag, kFlagPacking);
+    for (int a = 0; a < kNumWeighted; ++a) {
+        if (t < N1) {
+#pragma unroll
+            for (int q = 0; q < N2; ++q) v[q] = q < NQ ? slot(a, q) : C{0, 0};
+        }
+        fwd2<N1, N2>(v, lt, ex, t, 1);
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) ex[t + N2 * k1] = v[k1];
+        }
+        __syncthreads();
+        if (live) {
+            C *dst = base + a * fstride;
+            untangle_store(ex, L, d.Wx, t, G, dst, two ? dst + d.Wx : (C *)nullptr);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y pass over TX half-spectrum columns; block TX*G with lane-major thread
+// index (t * TX + c) so global accesses are contiguous over c.
+template <typename T, bool INV, int N1, int N2>
+__global__ void __launch_bounds__(256) k_ypass_r(const typename vec2<T>::type *__restrict__ in,
+                                                  typename vec2<T>::type *__restrict__ out, Dims d, int rows_in,
+                                                  int n_in, int rows_out, int n_out,
+                                                  const typename vec2<T>::type *__restrict__ tw, int TX) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x / TX, c = threadIdx.x % TX;
+    C *ex = reinterpret_cast<C *>(smem_raw) + c;
+    const int z = blockIdx.y, f = blockIdx.z, kx = blockIdx.x * TX + c;
+    const bool ok = kx < d.Wx;
+    const C *src = in + ((size_t)f * d.nz + z) * rows_in * d.Wx + kx;
+    C *dst = out + ((size_t)f * d.nz + z) * rows_out * d.Wx + kx;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    if (!INV) {
+        if (t < N1) {
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int j = t + N1 * n2;
+                v[n2] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
+            }
+        }
+        fwd2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N2 && ok) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                const int j = t + N2 * k1;
+                if (j < n_out) dst[(size_t)j * d.Wx] = v[k1];
+            }
+        }
+    } else {
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                const int j = t + N2 * k1;
+                v[k1] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
+            }
+        }
+        inv2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N1 && ok) {
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int j = t + N1 * n2;
+                if (j < n_out) dst[(size_t)j * d.Wx] = v[n2];
+            }
+        }
+    }
+}
+
+// spectral multiply for output alpha at (kx, ky, kz) from the s density
+// spectra r_i: conj(K_alpha,i) r_i summed over species
+template <typename T, typename C>
+__device__ __forceinline__ C mac_forward(int alpha, const T *__restrict__ spec, const Dims &d, const SpeciesConst &sc,
+                                         int kx, int ky, int kz, const C *r, int rstride) {
+    C acc = C{0, 0};
+    for (int i = 0; i < sc.s; ++i) {
+        const C x = r[i * rstride];
+        if (alpha < 4) {
+            T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
+            if (alpha == 0) g *= sc_c0<T>(sc, i);
+            if (alpha == 1) g *= sc_c1<T>(sc, i);
+            acc.x += g * x.x;
+            acc.y += g * x.y;
+        } else {
+            T sv = spec_at(spec, d, i, 2 + (alpha - 4) % 3, kx, ky, kz);
+            if (alpha < 7) sv *= sc_c1<T>(sc, i);
+            acc.x -= sv * x.y;
+            acc.y += sv * x.x;
+        }
+    }
+    return acc;
+}
+
+// z: forward FFT of the s density columns, the ten weighted-density spectra,
+// inverse FFT, rows z < nz.  block TX*G, grid (ceil(Wx/TX), Ly).
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_zmac_r(const typename vec2<T>::type *__restrict__ Bs,
+                                                 typename vec2<T>::type *__restrict__ B10, Dims d,
+                                                 const typename vec2<T>::type *__restrict__ tw,
+                                                 const T *__restrict__ spec, SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x / TX, c = threadIdx.x % TX;
+    C *slots = reinterpret_cast<C *>(smem_raw);     // [s][N1][G][TX]
+    C *ex = slots + (size_t)sc.s * N1 * G * TX + c;
+    const int rstride = N1 * G * TX;
+    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * TX + c]; };
+    const int ky = blockIdx.y, kx = blockIdx.x * TX + c;
+    const bool ok = kx < d.Wx;
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    for (int i = 0; i < sc.s; ++i) {
+        const C *src = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+        if (t < N1) {
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+            }
+        }
+        fwd2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = v[k1];
+        }
+    }
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1)
+                v[k1] = ok ? mac_forward(alpha, spec, d, sc, kx, ky, t + N2 * k1, &slot(0, k1), rstride) : C{0, 0};
+        }
+        inv2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N1 && ok) {
+            C *dst = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+            }
+        }
+    }
+}
+
+// z back: forward FFT of each Psi_alpha column, mu_i += K_alpha,i Psi_alpha,
+// inverse FFT of the s accumulators, rows z < nz.
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_zback_r(const typename vec2<T>::type *__restrict__ B10,
+                                                  typename vec2<T>::type *__restrict__ Bs, Dims d,
+                                                  const typename vec2<T>::type *__restrict__ tw,
+                                                  const T *__restrict__ spec, SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x / TX, c = threadIdx.x % TX;
+    C *slots = reinterpret_cast<C *>(smem_raw);     // [s][N1][G][TX]
+    C *ex = slots + (size_t)sc.s * N1 * G * TX + c;
+    const int rstride = N1 * G * TX;
+    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * TX + c]; };
+    const int ky = blockIdx.y, kx = blockIdx.x * TX + c;
+    const bool ok = kx < d.Wx;
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    if (t < N2)
+        for (int i = 0; i < sc.s; ++i)
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = C{0, 0};
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        const C *src = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+        if (t < N1) {
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+            }
+        }
+        fwd2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N2 && ok) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                const int kz = t + N2 * k1;
+                const C x = v[k1];
+                for (int i = 0; i < sc.s; ++i) {
+                    C &o = slot(i, k1);
+                    if (alpha < 4) {
+                        T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
+                        if (alpha == 0) g *= sc_c0<T>(sc, i);
+                        if (alpha == 1) g *= sc_c1<T>(sc, i);
+                        o.x += g * x.x;
+                        o.y += g * x.y;
+                    } else {
+                        T sv = spec_at(spec, d, i, 2 + (alpha - 4) % 3, kx, ky, kz);
+                        if (alpha < 7) sv *= sc_c1<T>(sc, i);
+                        o.x += sv * x.y;
+                        o.y -= sv * x.x;
+                    }
+                }
+            }
+        }
+    }
+    for (int i = 0; i < sc.s; ++i) {
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) v[k1] = slot(i, k1);
+        }
+        inv2<N1, N2>(v, lt, ex, t, TX);
+        if (t < N1 && ok) {
+            C *dst = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+            }
+        }
+    }
+}
+
+}  // namespace pnp

@@ -81,6 +81,39 @@ def test_explicit_odd_lengths(pnp):
     assert normwise(mu, ref) <= FP64_TOL
 
 
+REG_SHAPES = [
+    # (nx, ny, nz), padded lengths: every two-factor shape on every axis, odd ny
+    ((20, 10, 12), (32, 40, 64)),
+    ((16, 12, 14), (128, 256, 40)),
+    ((9, 11, 10), (256, 32, 128)),
+    ((28, 7, 36), (64, 128, 256)),
+]
+
+
+@pytest.mark.parametrize("shape,lens", REG_SHAPES)
+def test_register_fft_shapes(pnp, shape, lens):
+    spec, rho = mu_microbench(shape=shape)
+    spec.fft_len = lens
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == lens
+        mu = P.excess_mu(rho, precision="fp64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+
+
+def test_film_workload_full_size(pnp):
+    """The 32^3 film (periodic x, y at 32; z padded to 40) with wells."""
+    spec = film_gummel(32, 32, 32)
+    rho = film_rho(spec)
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (32, 32, 40)
+        mu = P.excess_mu(rho)
+    assert normwise(mu, ref) <= FP64_TOL
+
+
 def test_device_entry_matches_host_entry(pnp):
     import torch
     spec, rho = mu_microbench(16)
