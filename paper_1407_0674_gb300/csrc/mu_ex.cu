@@ -685,15 +685,16 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
         tm.begin(stage, st);
         if (!with_shape(d.Lz, [&](auto a, auto b) {
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                // paired columns (ky, Ly - ky): 2 TX columns per CTA
                 const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
-                const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(256 / G, 16), kBudget / per_col)));
-                dim3 g((d.Wx + TX - 1) / TX, d.Ly);
+                const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
+                dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
                 if (back) {
-                    ensure_smem<k_zback_r<T, N1, N2>>();
-                    k_zback_r<T, N1, N2><<<g, TX * G, TX * per_col, st>>>(B10, Bs, d, twz, spec, sc, TX);
+                    ensure_smem<k_zback_p<T, N1, N2>>();
+                    k_zback_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(B10, Bs, d, twz, spec, sc, TX);
                 } else {
-                    ensure_smem<k_zmac_r<T, N1, N2>>();
-                    k_zmac_r<T, N1, N2><<<g, TX * G, TX * per_col, st>>>(Bs, B10, d, twz, spec, sc, TX);
+                    ensure_smem<k_zmac_p<T, N1, N2>>();
+                    k_zmac_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(Bs, B10, d, twz, spec, sc, TX);
                 }
             })) {
             dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);

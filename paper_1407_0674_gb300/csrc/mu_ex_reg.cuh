@@ -407,3 +407,216 @@ __global__ void __launch_bounds__(256) k_zback_r(const typename vec2<T>::type *_
 }
 
 }  // namespace pnp
+
+namespace pnp {
+
+// ---------------------------------------------------------------------------
+// z kernels, paired-column form.  A CTA takes TX half-spectrum columns kx at
+// the two rows ky' and Ly - ky' (which read the same kernel-spectrum octant
+// entries), lanes (t, b, c) with c fastest.  The spectral products are grouped
+// by kernel type (shell, ball, vector x, y, z), so each lane loads the s
+// spectra of a type for its N1 frequencies in one batch.
+template <int N1, int N2> struct ZTile {
+    static constexpr int G = Shape<N1, N2>::G;
+};
+
+// column of lane (b, c) in tile (kx0, kyp): returns false if it does not exist
+__device__ __forceinline__ bool zcol(const Dims &d, int kyp, int b, int kx, int &ky) {
+    ky = b ? d.Ly - kyp : kyp;
+    if (b && (ky == kyp || ky >= d.Ly)) return false;   // self-paired row (0 or Ly/2)
+    return kx < d.Wx;
+}
+
+// spectrum values of `type` for species i0 .. i0 + kChunk - 1 (< s) at the
+// N1 frequencies kz = t + N2 k1 of a lane
+constexpr int kChunk = 3;
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void load_spec(T (&g)[kChunk][N1], const T *__restrict__ spec, const Dims &d, int s,
+                                          int i0, int type, int kx, int ky, int t, bool ok) {
+    const int fy = ky <= d.Ly / 2 ? ky : d.Ly - ky;
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    const bool flip_y = type == 3 && ky > d.Ly / 2;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        const int i = i0 + j;
+        const bool have = ok && i < s;
+        const T *base = spec + (size_t)((have ? i : 0) * kNumKernels + type) * oct + (size_t)fy * d.Ox + kx;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            const int kz = t + N2 * k1;
+            const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+            T v = have ? __ldg(&base[(size_t)fz * d.Oy * d.Ox]) : (T)0;
+            if (flip_y || (type == 4 && kz > d.Lz / 2)) v = -v;
+            g[j][k1] = v;
+        }
+    }
+}
+
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_zmac_p(const typename vec2<T>::type *__restrict__ Bs,
+                                                 typename vec2<T>::type *__restrict__ B10, Dims d,
+                                                 const typename vec2<T>::type *__restrict__ tw,
+                                                 const T *__restrict__ spec, SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = threadIdx.x % TX, b = (threadIdx.x / TX) & 1, t = threadIdx.x / (2 * TX);
+    const int lanes = 2 * TX;                        // interleaved columns in the tile
+    const int col = b * TX + c;
+    C *slots = reinterpret_cast<C *>(smem_raw);      // [s][N1][G][2 TX]
+    C *ex = slots + (size_t)sc.s * N1 * G * lanes + col;
+    const int rstride = N1 * G * lanes;
+    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * lanes + col]; };
+    const int kyp = blockIdx.y, kx = blockIdx.x * TX + c;
+    int ky;
+    const bool ok = zcol(d, kyp, b, kx, ky);
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    for (int i = 0; i < sc.s; ++i) {
+        const C *src = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+        if (t < N1) {
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+            }
+        }
+        fwd2<N1, N2>(v, lt, ex, t, lanes);
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = v[k1];
+        }
+    }
+    // output groups: shell {n0, n1, n2}, ball {n3}, vector x {n1x, n2x}, y, z;
+    // with s <= kChunk the group's spectra are loaded once
+    for (int type = 0; type < kNumKernels; ++type) {
+        T g[kChunk][N1];
+        const int nout = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        for (int o = 0; o < nout; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+            if (t < N2) {
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) v[k1] = C{0, 0};
+                for (int i0 = 0; i0 < sc.s; i0 += kChunk) {
+                    if (o == 0 || sc.s > kChunk) load_spec<T, N1, N2>(g, spec, d, sc.s, i0, type, kx, ky, t, ok);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) {
+                        const int i = i0 + j;
+                        if (i >= sc.s) break;
+                        const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                                : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+#pragma unroll
+                        for (int k1 = 0; k1 < N1; ++k1) {
+                            const T gg = cf * g[j][k1];
+                            const C x = slot(i, k1);
+                            if (type <= 1) {
+                                v[k1].x += gg * x.x;
+                                v[k1].y += gg * x.y;
+                            } else {             // conj(K) = +i S
+                                v[k1].x -= gg * x.y;
+                                v[k1].y += gg * x.x;
+                            }
+                        }
+                    }
+                }
+            }
+            inv2<N1, N2>(v, lt, ex, t, lanes);
+            if (t < N1 && ok) {
+                C *dst = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+                for (int n2 = 0; n2 < N2; ++n2) {
+                    const int zz = t + N1 * n2;
+                    if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int N1, int N2>
+__global__ void __launch_bounds__(256) k_zback_p(const typename vec2<T>::type *__restrict__ B10,
+                                                  typename vec2<T>::type *__restrict__ Bs, Dims d,
+                                                  const typename vec2<T>::type *__restrict__ tw,
+                                                  const T *__restrict__ spec, SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = threadIdx.x % TX, b = (threadIdx.x / TX) & 1, t = threadIdx.x / (2 * TX);
+    const int lanes = 2 * TX;
+    const int col = b * TX + c;
+    C *slots = reinterpret_cast<C *>(smem_raw);      // accumulators [s][N1][G][2 TX]
+    C *ex = slots + (size_t)sc.s * N1 * G * lanes + col;
+    const int rstride = N1 * G * lanes;
+    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * lanes + col]; };
+    const int kyp = blockIdx.y, kx = blockIdx.x * TX + c;
+    int ky;
+    const bool ok = zcol(d, kyp, b, kx, ky);
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    if (t < N2)
+        for (int i = 0; i < sc.s; ++i)
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = C{0, 0};
+    for (int type = 0; type < kNumKernels; ++type) {
+        T g[kChunk][N1];
+        const int nin = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        for (int o = 0; o < nin; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+            const C *src = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+            if (t < N1) {
+#pragma unroll
+                for (int n2 = 0; n2 < N2; ++n2) {
+                    const int zz = t + N1 * n2;
+                    v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+                }
+            }
+            fwd2<N1, N2>(v, lt, ex, t, lanes);
+            if (t < N2) {
+                for (int i0 = 0; i0 < sc.s; i0 += kChunk) {
+                    if (o == 0 || sc.s > kChunk) load_spec<T, N1, N2>(g, spec, d, sc.s, i0, type, kx, ky, t, ok);
+#pragma unroll
+                    for (int j = 0; j < kChunk; ++j) {
+                        const int i = i0 + j;
+                        if (i >= sc.s) break;
+                        const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                                : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+#pragma unroll
+                        for (int k1 = 0; k1 < N1; ++k1) {
+                            const T gg = cf * g[j][k1];
+                            const C x = v[k1];
+                            C &acc = slot(i, k1);
+                            if (type <= 1) {
+                                acc.x += gg * x.x;
+                                acc.y += gg * x.y;
+                            } else {             // K = -i S
+                                acc.x += gg * x.y;
+                                acc.y -= gg * x.x;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    for (int i = 0; i < sc.s; ++i) {
+        if (t < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) v[k1] = slot(i, k1);
+        }
+        inv2<N1, N2>(v, lt, ex, t, lanes);
+        if (t < N1 && ok) {
+            C *dst = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+            }
+        }
+    }
+}
+
+}  // namespace pnp
