@@ -48,6 +48,13 @@ def parse():
     ap.add_argument("--n", type=int, default=N_EDGE, help="grid edge (profiling runs use smaller cases)")
     ap.add_argument("--pad", type=int, default=PAD, help="padded FFT length")
     ap.add_argument("--variants", default="fp64,fp32", help="precisions to time, headline first")
+    ap.add_argument("--workload", default="mu_ex", choices=["mu_ex", "film", "batch", "serve"],
+                    help="mu_ex (headline), film (one 32^3 Gummel solve), batch (64 solves), serve (arrivals)")
+    ap.add_argument("--batch", type=int, default=64, help="solves in the batch workload")
+    ap.add_argument("--seq", type=int, default=8, help="solves timed one at a time as the sequential baseline")
+    ap.add_argument("--requests", type=int, default=40, help="served requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="request arrivals per second")
+    ap.add_argument("--max-edge", type=int, default=96, help="largest served grid edge")
     return ap.parse_args()
 
 
@@ -381,11 +388,138 @@ def run_gpu(args, world, rank, local):
     P.close()
 
 
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def run_solves(args, world, rank, local):
+    """Gummel workloads: film (one solve), batch (many solves through the
+    server against the same solves one at a time), serve (Poisson arrivals)."""
+    import numpy as np
+    import torch
+    from paper_1407_0674_gb300 import build as lb
+    from paper_1407_0674_gb300 import pnp
+    from workloads import batch_specs, film_gummel, serving_arrivals, serving_spec
+
+    torch.cuda.set_device(local)
+    lb.build()
+    if args.workload == "film":
+        spec = film_gummel(32, 32, 32)
+        with pnp.Problem(spec) as P:
+            P.gummel_solve()                       # builds the solve graph
+            t0 = time.perf_counter()
+            phi, rho, st = P.gummel_solve()
+            dt = time.perf_counter() - t0
+        line = {"metric": "PNP solves/s", "value": world / dt, "unit": "solves/s", "n_gpus": world, "steps": 1,
+                "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "Gummel solve of the 32^3 film (2 ions, R 2h, packing 0.2 each, wells 1 kT on "
+                                       "64 sites, bias 0.1 kT/e) to residual 1e-8"},
+                "iterations": st["iterations"], "linear_iterations": st["linear_iterations"],
+                "residual": st["residual"]}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    if args.workload == "batch":
+        specs = batch_specs(args.batch)
+        # sequential baseline: the plain FP64 form, one solve at a time
+        seq = []
+        seq_res = {}
+        for k, s in enumerate(specs[:args.seq]):
+            with pnp.Problem(s) as P:
+                t0 = time.perf_counter()
+                phi, rho, st = P.gummel_solve(raise_on_error=False)
+                seq.append(time.perf_counter() - t0)
+                seq_res[k] = (rho, st)
+        srv = pnp.Server(max_slots=64)
+        t0 = time.perf_counter()
+        tickets = []
+        for s in specs:
+            rc, t = srv.submit(s)
+            if rc != 0:
+                raise RuntimeError(f"submit {rc}")
+            tickets.append(t)
+        done = {}
+        while len(done) < len(tickets):
+            for k, t in enumerate(tickets):
+                if k in done:
+                    continue
+                rc, phi, rho, st = srv.poll(t)
+                if rc != pnp.PENDING:
+                    done[k] = (rc, rho, st, time.perf_counter() - t0)
+            time.sleep(0.002)
+        wall = time.perf_counter() - t0
+        srv.close()
+        errs = [float(np.abs(done[k][1] - seq_res[k][0]).max() / np.abs(seq_res[k][0]).max()) for k in seq_res]
+        ok = sum(1 for v in done.values() if v[0] in (0,))
+        lat = [v[3] for v in done.values()]
+        line = {"metric": "PNP solves/s", "value": world * len(specs) / wall, "unit": "solves/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{len(specs)} independent Gummel solves, grids from "
+                                       "{32^3,48^3,64^3,80x80x96,96^3}, T U(250,400) K, wells 0.3 eV/kT, packing "
+                                       "U(0.1,0.35), served concurrently (one CUDA graph per solve)"},
+                "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq),
+                                    "mean_s": float(np.mean(seq))},
+                "speedup_vs_sequential": (len(specs) / wall) / (len(seq) / sum(seq)),
+                "max_rel_err_vs_sequential": max(errs) if errs else None,
+                "converged": ok, "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+                "iterations_mean": float(np.mean([v[2]["iterations"] for v in done.values()]))}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    # serve
+    arr = serving_arrivals(args.requests, rate=args.rate, hi=args.max_edge)
+    specs = [serving_spec(n, bias, T) for (_, n, bias, T) in arr]
+    seq = []
+    for s in specs[:args.seq]:
+        with pnp.Problem(s) as P:
+            t0 = time.perf_counter()
+            P.gummel_solve(raise_on_error=False)
+            seq.append(time.perf_counter() - t0)
+    srv = pnp.Server(max_slots=64)
+    t0 = time.perf_counter()
+    pending = {}
+    lat = []
+    nxt = 0
+    statuses = []
+    while nxt < len(arr) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(arr) and arr[nxt][0] <= now:
+            rc, t = srv.submit(specs[nxt])
+            if rc == 0:
+                pending[t] = arr[nxt][0]
+            else:
+                statuses.append(rc)
+            nxt += 1
+        for t in list(pending):
+            rc, phi, rho, st = srv.poll(t)
+            if rc != pnp.PENDING:
+                lat.append(time.perf_counter() - t0 - pending.pop(t))
+                statuses.append(rc)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    srv.close()
+    line = {"metric": "PNP solves/s", "value": world * len(lat) / wall, "unit": "solves/s", "n_gpus": world,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{len(arr)} served Gummel solves, Poisson arrivals {args.rate}/s, cubic grids "
+                                   f"log-uniform 32..{args.max_edge}, bias U(0,1), T U(250,400) K, budget 150 GB"},
+            "latency_p50_ms": _pct(lat, 50) * 1e3, "latency_p99_ms": _pct(lat, 99) * 1e3,
+            "completed_ok": sum(1 for s in statuses if s == 0), "statuses": sorted(set(statuses)),
+            "sequential_fp64": {"solves": len(seq), "mean_s": float(np.mean(seq)) if seq else None}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload != "mu_ex":
+        run_solves(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

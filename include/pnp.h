@@ -60,9 +60,11 @@ enum { PNP_BC_PERIODIC = 0, PNP_BC_DIRICHLET = 1, PNP_BC_NOFLUX = 2 };
 enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1 };
 
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
- * rho <- l2 rho* + (1 - l2) rho, or the geometric form
- * rho <- rho (rho* / rho)^l2, equal to first order and positive for large steps. */
-enum { PNP_MIX_LINEAR = 0, PNP_MIX_GEOMETRIC = 1 };
+ * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
+ * (equal to first order, positive for large steps), or the geometric form
+ * with its step in ln rho limited to +-0.2 per iteration (deep square wells
+ * cannot push the packing fraction past 1 in one step; same fixed point). */
+enum { PNP_MIX_LINEAR = 0, PNP_MIX_GEOMETRIC = 1, PNP_MIX_GEOMETRIC_LIMITED = 2 };
 
 typedef struct {
     int nx, ny, nz;                /* grid points per axis */
@@ -90,7 +92,8 @@ typedef struct {
     int sw_half;                   /* 1: mu_sh keeps the factor 1/2 of Sec 2.3.2 */
     int fft_len[3];                /* padded FFT length per axis, 0 = smallest legal */
     int precision;                 /* PNP_PREC_FP64 / FP32: default for the calls below */
-    double lin_tol;                /* relative residual of the linear solves, 0 -> 1e-12 */
+    double lin_tol;                /* relative residual ||r|| / ||b|| of the linear solves; 0 -> adaptive:
+                                      min(1e-6, max(1e-12, 0.01 x previous Gummel residual)) */
     unsigned flags;                /* reserved, 0 */
 } pnp_problem_desc;
 

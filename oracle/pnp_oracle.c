@@ -215,7 +215,8 @@ typedef struct {
     int sw_half;               /* 1: the 1/2 of Sec 2.3.2 kept; 0: dropped */
     double lin_tol;            /* PCG relative residual target */
     int lin_max_iter;
-    int rho_mix;               /* 0: linear relaxation (Sec 3.2), 1: geometric */
+    int rho_mix;               /* 0: linear relaxation (Sec 3.2), 1: geometric,
+                                  2: geometric with |step in ln rho| <= 0.2 */
 } oracle_problem;
 
 static grid_t cdft_grid(const oracle_problem *p)
@@ -852,7 +853,9 @@ void oracle_np_flux(const oracle_problem *p, int i, const double *phi, const dou
  *   rho* = rhobar exp(-(q phi^n + mu_ex)); rho^n = l2 rho* + (1-l2) rho^{n-1}
  *   (rho_mix 0, as printed) or rho^n = rho^{n-1} (rho* / rho^{n-1})^l2
  *   (rho_mix 1: the same update to first order, kept positive and bounded for
- *   the large first steps of a dense fluid next to a hard wall);
+ *   the large first steps of a dense fluid next to a hard wall), or that step
+ *   in ln rho limited to +-0.2 per iteration (rho_mix 2: deep square wells
+ *   cannot push the packing fraction past 1 in one step; same fixed point);
  *   stop when max(|dphi|_inf, max_i |drho_i|_inf / rho_b,i) < tol.
  * Initial state (when phi0/rho0 are NULL): phi linear in z between the
  * Dirichlet values, rho = rho_b.  Returns 0 converged, 1 not converged,
@@ -901,9 +904,14 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
             double drho = 0.0;
             for (long k = 0; k < N; ++k) {
                 double rs = rb[k] * exp(-(p->q[i] * phi[k] + mui[k]));
-                double v = p->rho_mix == 1
-                               ? rho[i * N + k] * exp(p->lambda_rho * log(rs / rho[i * N + k]))
-                               : p->lambda_rho * rs + (1.0 - p->lambda_rho) * rho[i * N + k];
+                double v;
+                if (p->rho_mix == 0) {
+                    v = p->lambda_rho * rs + (1.0 - p->lambda_rho) * rho[i * N + k];
+                } else {
+                    double step = p->lambda_rho * log(rs / rho[i * N + k]);
+                    if (p->rho_mix == 2) step = step > 0.2 ? 0.2 : (step < -0.2 ? -0.2 : step);
+                    v = rho[i * N + k] * exp(step);
+                }
                 double d = fabs(v - rho[i * N + k]) / p->rho_b[i];
                 if (d > drho) drho = d;
                 rho_new[i * N + k] = v;

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -16,6 +17,28 @@ int cuda_status(cudaError_t e) {
     return PNP_ERR_CUDA;
 }
 
+cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st) {
+    static std::once_flag pool_once[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64)
+        std::call_once(pool_once[dev], [dev] {
+            // keep freed blocks in the pool instead of returning them at each sync
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+        });
+    cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+void dfree(void *ptr, cudaStream_t st) {
+    if (ptr) cudaFreeAsync(ptr, st);
+}
+
 void destroy_problem_internal(Problem *p) {
     if (!p) return;
     int cur = -1;
@@ -24,9 +47,9 @@ void destroy_problem_internal(Problem *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     gummel_free(p);
     mu_ex_free(p);
-    cudaFree(p->d_flag);
-    cudaFree(p->d_io);
-    cudaFree(p->d_sh_coef);
+    dfree(p->d_flag, p->stream);
+    dfree(p->d_io, p->stream);
+    dfree(p->d_sh_coef, p->stream);
     if (p->stream) cudaStreamDestroy(p->stream);
     if (cur >= 0 && cur != p->device) cudaSetDevice(cur);
     delete p;
@@ -42,8 +65,8 @@ int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::st
     }
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_flag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(p->d_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = dmalloc((void **)&p->d_flag, sizeof(int), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream);
     if (e != cudaSuccess) {
         rc = cuda_status(e);
         destroy_problem_internal(p);
@@ -51,6 +74,7 @@ int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::st
     }
     p->last_stream = p->stream;
     rc = mu_ex_setup(p);
+    if (rc == PNP_OK) rc = cuda_status(cudaStreamSynchronize(p->stream));
     if (rc) {
         destroy_problem_internal(p);
         return rc;
@@ -145,7 +169,8 @@ int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precisio
     for (size_t k = 0; k < n; ++k)
         if (!(rho[k] >= 0.0) || !std::isfinite(rho[k])) return PNP_ERR_INVALID;
     if (!p->d_io) {
-        if (cudaMalloc(&p->d_io, sizeof(double) * (2 * n + p->npts())) != cudaSuccess) return PNP_ERR_NOMEM;
+        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + p->npts()), p->stream) != cudaSuccess)
+            return PNP_ERR_NOMEM;
         p->device_bytes += sizeof(double) * (2 * n + p->npts());
     }
     cudaStream_t st = p->stream;
@@ -196,7 +221,7 @@ int pnp_gummel_solve(pnp_problem *h, const double *phi0, const double *rho0, dou
         for (size_t k = 0; k < N; ++k)
             if (!std::isfinite(phi0[k])) return PNP_ERR_INVALID;
     if (!p->d_io) {
-        if (cudaMalloc(&p->d_io, sizeof(double) * (2 * n + N)) != cudaSuccess) return PNP_ERR_NOMEM;
+        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
         p->device_bytes += sizeof(double) * (2 * n + N);
     }
     cudaStream_t st = p->stream;

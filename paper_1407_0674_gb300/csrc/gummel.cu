@@ -43,20 +43,39 @@ struct Level {
 
 constexpr int kRedBlocks = 512;
 constexpr int kCoarseSweeps = 40;
+constexpr double kCoarseScale = 1.8;
+constexpr double kMixStepLimit = 0.2;     // |step in ln rho| of PNP_MIX_GEOMETRIC_LIMITED
+
+// device-side record of a solve (written by the loop-control kernels)
+struct DevStats {
+    int status;            // PNP_OK, PNP_ERR_NOT_CONVERGED, PNP_ERR_PACKING, PNP_ERR_OVERFLOW
+    int iters;             // Gummel iterations done
+    int pcg_it;            // iterations of the current linear solve
+    int pad;
+    double residual;       // last Gummel residual
+    long long lin;         // linear iterations over the solve
+    double lin_tol;        // current tolerance of the linear solves (adaptive mode)
+};
 
 struct GummelState {
     std::vector<Level> lv;
     double *mu = nullptr, *rho_new = nullptr;
+    double *phi = nullptr, *rho = nullptr;    // solve state the graph works on
+    DevStats *stats = nullptr;
+    int *keep_q = nullptr;                    // valences and fixed charge used by the graph
+    double *keep_rhof = nullptr;
+    cudaStream_t cap[2] = {nullptr, nullptr}; // capture streams of the loop bodies
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     double *rhs = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr;
     double *partial = nullptr;     // kRedBlocks
     double *scal = nullptr;        // device scalars
     unsigned long long *dmax = nullptr;
-    double *h_pinned = nullptr;    // host mirror of a few scalars
     size_t bytes = 0;
     bool poisson_ready = false;
 };
 
-enum { S_RZ = 0, S_PAP, S_RR, S_ALPHA, S_BETA, S_RZNEW, S_BB, S_COUNT };
+enum { S_RZ = 0, S_PAP, S_RR, S_ALPHA, S_BETA, S_RZNEW, S_BB, S_TGT, S_COUNT };
 
 __device__ __forceinline__ size_t pidx(int i, int j, int k, int nx, int ny) {
     return ((size_t)k * ny + j) * nx + i;
@@ -167,12 +186,14 @@ __global__ void k_restrict(const double *__restrict__ rf, int nx, int ny, int fx
     }
 }
 
+// x_fine += scale * x_coarse (piecewise constant); scale > 1 compensates the
+// weak correction of piecewise-constant interpolation
 __global__ void k_prolong_add(double *__restrict__ xf, int nx, int ny, int nz, int fx, int fy, int fz, int cnx,
-                              int cny, const double *__restrict__ xc) {
+                              int cny, const double *__restrict__ xc, double scale) {
     const size_t n = (size_t)nx * ny * nz;
     GRID_LOOP(p, n) {
         const int i = p % nx, j = (p / nx) % ny, k = p / ((size_t)nx * ny);
-        xf[p] += xc[pidx(i / fx, j / fy, k / fz, cnx, cny)];
+        xf[p] += scale * xc[pidx(i / fx, j / fy, k / fz, cnx, cny)];
     }
 }
 
@@ -349,7 +370,14 @@ __global__ void k_np_finish(size_t n, double q, double l2, int mix, double inv_r
     GRID_LOOP(p, n) {
         const double rs = rbar[p] * exp(-(q * phi[p] + mu[p]));
         const double old = rho[p];
-        const double v = mix == PNP_MIX_GEOMETRIC ? old * exp(l2 * log(rs / old)) : l2 * rs + (1.0 - l2) * old;
+        double v;
+        if (mix == PNP_MIX_LINEAR) {
+            v = l2 * rs + (1.0 - l2) * old;
+        } else {
+            double step = l2 * log(rs / old);
+            if (mix == PNP_MIX_GEOMETRIC_LIMITED) step = fmin(fmax(step, -kMixStepLimit), kMixStepLimit);
+            v = old * exp(step);
+        }
         if (!isfinite(v) || !(v > 0)) bad = true;
         m = fmax(m, fabs(v - old) * inv_rb);
         rho[p] = v;
@@ -367,30 +395,241 @@ __global__ void k_init_phi(PhysConst c, double *__restrict__ phi) {
     }
 }
 
+
+// first red sweep from x = 0: red points b/diag, black points 0 (replaces a
+// fill and a sweep)
+__global__ void k_sweep_zero(Op A, double *__restrict__ x, const double *__restrict__ b) {
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+        x[p] = ((i + j + k) & 1) ? 0.0 : b[p] / op_diag(A, i, j, k, p);
+    }
+}
+
+// coarse right-hand side = sum of the fine residuals b - A x over each aggregate
+__global__ void k_residual_restrict(Op F, const double *__restrict__ x, const double *__restrict__ b, int fx, int fy,
+                                    int fz, int cnx, int cny, int cnz, double *__restrict__ bc) {
+    const size_t n = (size_t)cnx * cny * cnz;
+    GRID_LOOP(q, n) {
+        const int I = q % cnx, J = (q / cnx) % cny, K = q / ((size_t)cnx * cny);
+        double s = 0;
+        for (int c = 0; c < fz; ++c)
+            for (int bb = 0; bb < fy; ++bb)
+                for (int a = 0; a < fx; ++a) {
+                    const int i = I * fx + a, j = J * fy + bb, k = K * fz + c;
+                    const size_t p = pidx(i, j, k, F.nx, F.ny);
+                    s += b[p] - (op_diag(F, i, j, k, p) * x[p] - op_nbr(F, x, i, j, k, p));
+                }
+        bc[q] = s;
+    }
+}
+
+// coarsest level in shared memory: x = 0, then kCoarseSweeps symmetric
+// red-black sweeps; n <= kCoarseMax
+constexpr int kCoarseMax = 1024;
+__global__ void k_coarse_smem(Op A, double *__restrict__ x_out, const double *__restrict__ b_in) {
+    extern __shared__ double csm[];
+    const int n = A.nx * A.ny * A.nz;
+    double *x = csm, *b = csm + n, *dg = csm + 2 * n, *cx = csm + 3 * n, *cy = csm + 4 * n, *cz = csm + 5 * n,
+           *cl = csm + 6 * n;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        x[p] = 0.0;
+        b[p] = b_in[p];
+        cx[p] = A.cx[p];
+        cy[p] = A.cy[p];
+        cz[p] = A.cz[p];
+        cl[p] = A.czlo[p];
+    }
+    __syncthreads();
+    const Op S{A.nx, A.ny, A.nz, cx, cy, cz, cl};
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+        dg[p] = op_diag(S, i, j, k, p);
+    }
+    __syncthreads();
+    const int order[4] = {0, 1, 1, 0};
+    for (int s = 0; s < kCoarseSweeps; ++s)
+        for (int c = 0; c < 4; ++c) {
+            for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+                if (((i + j + k) & 1) != order[c]) continue;
+                x[p] = (b[p] + op_nbr(S, x, i, j, k, p)) / dg[p];
+            }
+            __syncthreads();
+        }
+    for (int p = threadIdx.x; p < n; p += blockDim.x) x_out[p] = x[p];
+}
+
+// y = A x and the block partial sums of x . y
+__global__ void k_apply_dot(Op A, const double *__restrict__ x, double *__restrict__ y, double *__restrict__ partial) {
+    __shared__ double sh[256];
+    const size_t n = (size_t)A.nx * A.ny * A.nz;
+    double acc = 0;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / ((size_t)A.nx * A.ny);
+        const double v = op_diag(A, i, j, k, p) * x[p] - op_nbr(A, x, i, j, k, p);
+        y[p] = v;
+        acc += x[p] * v;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// x += alpha p; r -= alpha Ap; block partial sums of r . r
+__global__ void k_update_xr_dot(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                const double *__restrict__ Ap, const double *__restrict__ scal, size_t n,
+                                double *__restrict__ partial) {
+    __shared__ double sh[256];
+    const double a = scal[S_ALPHA];
+    double acc = 0;
+    GRID_LOOP(k, n) {
+        x[k] += a * p[k];
+        const double v = r[k] - a * Ap[k];
+        r[k] = v;
+        acc += v * v;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// fixed-order sum of nb block partials into scal[slot], then an optional
+// scalar step: 1 alpha = rz / pAp, 2 beta = rz_new / rz
+__device__ __forceinline__ double block_sum_partials(const double *__restrict__ partial, int nb) {
+    __shared__ double sh[kRedBlocks];
+    for (int t = threadIdx.x; t < kRedBlocks; t += blockDim.x) sh[t] = t < nb ? partial[t] : 0.0;
+    __syncthreads();
+    for (int w = kRedBlocks / 2; w > 0; w >>= 1) {
+        for (int t = threadIdx.x; t < w; t += blockDim.x) sh[t] += sh[t + w];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__global__ void k_final(const double *__restrict__ partial, int nb, double *__restrict__ scal, int slot, int step) {
+    const double v = block_sum_partials(partial, nb);
+    if (threadIdx.x == 0) {
+        scal[slot] = v;
+        if (step == 1) scal[S_ALPHA] = scal[S_RZ] / v;
+        if (step == 2) {
+            scal[S_BETA] = v / scal[S_RZ];
+            scal[S_RZ] = v;
+        }
+    }
+}
+
+// sum of r . r, then the loop decision of the CG iteration
+__global__ void k_final_check(const double *__restrict__ partial, int nb, double *__restrict__ scal, int maxit,
+                              DevStats *st, int *flag, cudaGraphConditionalHandle h) {
+    const double rr = block_sum_partials(partial, nb);
+    if (threadIdx.x == 0) {
+        scal[S_RR] = rr;
+        const int it = ++st->pcg_it;
+        st->lin += 1;
+        const bool finite = isfinite(rr);
+        if (!finite) atomicOr(flag, kFlagOverflow);
+        cudaGraphSetConditional(h, (finite && rr > scal[S_TGT] && it < maxit) ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// loop control on the device (conditional graph nodes)
+
+// start of a linear solve: target = tol^2 ||b||^2; enter the loop unless the
+// warm start already meets it
+__global__ void k_pcg_init(double *scal, double tol, DevStats *st, int *flag, cudaGraphConditionalHandle h) {
+    if (!(tol > 0)) tol = st->lin_tol;      // adaptive: set by the Gummel loop
+    double bb = scal[S_BB];
+    if (!(bb > 0)) bb = 1.0;
+    const double tgt = tol * tol * bb;
+    const double rr = scal[S_RR];
+    scal[S_TGT] = tgt;
+    st->pcg_it = 0;
+    const bool finite = isfinite(rr);
+    if (!finite) atomicOr(flag, kFlagOverflow);
+    cudaGraphSetConditional(h, (finite && rr > tgt) ? 1u : 0u);
+}
+
+// end of a CG iteration: continue while ||r||^2 > target and below maxit
+__global__ void k_pcg_check(const double *scal, int maxit, DevStats *st, int *flag, cudaGraphConditionalHandle h) {
+    const double rr = scal[S_RR];
+    const int it = ++st->pcg_it;
+    st->lin += 1;
+    const bool finite = isfinite(rr);
+    if (!finite) atomicOr(flag, kFlagOverflow);
+    cudaGraphSetConditional(h, (finite && rr > scal[S_TGT] && it < maxit) ? 1u : 0u);
+}
+
+// end of a Gummel iteration: residual, status, continue or stop
+__global__ void k_gummel_check(const unsigned long long *dmax, const int *flag, double tol, int max_iter,
+                               DevStats *st, cudaGraphConditionalHandle h) {
+    const unsigned long long bits = *dmax;
+    const double res = __longlong_as_double((long long)bits);
+    const int it = ++st->iters;
+    st->residual = res;
+    const int f = *flag;
+    // inexact inner solves: tolerance follows the outer residual (forcing term)
+    st->lin_tol = fmin(1e-6, fmax(1e-12, 0.01 * res));
+    unsigned cont = 0;
+    if (f & kFlagPacking) st->status = PNP_ERR_PACKING;
+    else if (f & (kFlagOverflow | kFlagNonFinite)) st->status = PNP_ERR_OVERFLOW;
+    else if (res < tol) st->status = PNP_OK;
+    else if (it >= max_iter) st->status = PNP_ERR_NOT_CONVERGED;
+    else cont = 1;
+    cudaGraphSetConditional(h, cont);
+}
+
+__global__ void k_stats_reset(DevStats *st) {
+    st->lin_tol = 1e-6;
+    st->status = PNP_ERR_NOT_CONVERGED;
+    st->iters = 0;
+    st->pcg_it = 0;
+    st->residual = 0;
+    st->lin = 0;
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 static int grid_for(size_t n) { return (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16); }
 
 static Op op_of(const Level &L) { return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo}; }
 
-static void vcycle(GummelState *g, int l, cudaStream_t st) {
+// one V(1,1) cycle for level l: x = M b (x, b default to the level's vectors)
+static void vcycle(GummelState *g, int l, cudaStream_t st, double *x = nullptr, const double *b = nullptr) {
     Level &L = g->lv[l];
+    if (!x) x = L.x;
+    if (!b) b = L.b;
     const Op A = op_of(L);
     const int G = grid_for(L.n);
     if (l + 1 == (int)g->lv.size()) {
-        k_coarse_solve<<<1, 512, 0, st>>>(A, L.x, L.b);
+        if (L.n <= (size_t)kCoarseMax)
+            k_coarse_smem<<<1, 256, 7 * L.n * sizeof(double), st>>>(A, x, b);
+        else
+            k_coarse_solve<<<1, 512, 0, st>>>(A, x, b);
         return;
     }
     Level &C = g->lv[l + 1];
-    k_fill<<<G, 256, 0, st>>>(L.x, 0.0, L.n);
-    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 0);
-    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 1);
-    k_residual<<<G, 256, 0, st>>>(A, L.x, L.b, L.r);
-    k_restrict<<<grid_for(C.n), 256, 0, st>>>(L.r, L.nx, L.ny, L.fx, L.fy, L.fz, C.nx, C.ny, C.nz, C.b);
+    // V(2,2): red, black, red, black before; black, red, black, red after
+    k_sweep_zero<<<G, 256, 0, st>>>(A, x, b);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 1);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 0);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 1);
+    k_residual_restrict<<<grid_for(C.n), 256, 0, st>>>(A, x, b, L.fx, L.fy, L.fz, C.nx, C.ny, C.nz, C.b);
     vcycle(g, l + 1, st);
-    k_prolong_add<<<G, 256, 0, st>>>(L.x, L.nx, L.ny, L.nz, L.fx, L.fy, L.fz, C.nx, C.ny, C.x);
-    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 1);
-    k_color_sweep<<<G, 256, 0, st>>>(A, L.x, L.b, 0);
+    k_prolong_add<<<G, 256, 0, st>>>(x, L.nx, L.ny, L.nz, L.fx, L.fy, L.fz, C.nx, C.ny, C.x, kCoarseScale);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 1);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 0);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 1);
+    k_color_sweep<<<G, 256, 0, st>>>(A, x, b, 0);
 }
 
 static void coarsen_all(GummelState *g, cudaStream_t st) {
@@ -406,53 +645,86 @@ static void dot(GummelState *g, const double *a, const double *b, size_t n, int 
     k_dot_final<<<1, 256, 0, st>>>(g->partial, g->scal, slot);
 }
 
-// MG-preconditioned CG on level 0's operator; x holds the initial guess.
-// Stops when ||r||_2 <= tol ||b||_2.  Returns iterations or a negative code.
-static int pcg(GummelState *g, double *x, const double *b, double tol, int maxit, cudaStream_t st) {
+// Append a conditional WHILE node to the capture on `st`; later captured work
+// depends on it.  Returns its body graph and handle (default value `dflt`).
+static cudaError_t add_while(cudaStream_t st, unsigned dflt, cudaGraphConditionalHandle *h, cudaGraph_t *body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphConditionalHandleCreate(h, cg, dflt, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = *h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, cg, deps, ed, nd, &prm);
+    if (e != cudaSuccess) return e;
+    *body = prm.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// MG-preconditioned CG on level 0's operator, recorded into the capture on
+// `st` with the iteration loop as a conditional WHILE node whose body is
+// captured on `sb`.  x holds the initial guess; stops at ||r||_2 <= tol ||b||_2
+// or maxit iterations.  All reductions have a fixed shape.
+static cudaError_t pcg_capture(GummelState *g, double *x, const double *b, double tol, int maxit, int *flag,
+                               cudaStream_t st, cudaStream_t sb) {
     Level &L0 = g->lv[0];
     const Op A = op_of(L0);
     const size_t n = L0.n;
     const int G = grid_for(n);
+    const int NB = std::min(G, kRedBlocks);
     double *r = g->r, *z = g->z, *p = g->pv, *Ap = g->Ap;
     dot(g, b, b, n, S_BB, st);
     k_residual<<<G, 256, 0, st>>>(A, x, b, r);
     dot(g, r, r, n, S_RR, st);
-    cudaMemcpyAsync(g->h_pinned, g->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_status(e);
-    double bb = g->h_pinned[S_BB], rr = g->h_pinned[S_RR];
-    if (!(bb > 0)) bb = 1.0;
-    const double target = tol * tol * bb;
-    if (!std::isfinite(rr)) return PNP_ERR_OVERFLOW;
-    if (rr <= target) return 0;
-    // z = M r
-    k_copy<<<G, 256, 0, st>>>(L0.b, r, n);
-    vcycle(g, 0, st);
-    k_copy<<<G, 256, 0, st>>>(z, L0.x, n);
+    vcycle(g, 0, st, z, r);
     k_copy<<<G, 256, 0, st>>>(p, z, n);
     dot(g, r, z, n, S_RZ, st);
-    int it = 0;
-    while (it < maxit) {
-        k_apply<<<G, 256, 0, st>>>(A, p, Ap);
-        dot(g, p, Ap, n, S_PAP, st);
-        k_scalars_alpha<<<1, 1, 0, st>>>(g->scal);
-        k_update_xr<<<G, 256, 0, st>>>(x, r, p, Ap, g->scal, n);
-        ++it;
-        dot(g, r, r, n, S_RR, st);
-        cudaMemcpyAsync(g->h_pinned + S_RR, g->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, st);
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_status(e);
-        rr = g->h_pinned[S_RR];
-        if (!std::isfinite(rr)) return PNP_ERR_OVERFLOW;
-        if (rr <= target) break;
-        k_copy<<<G, 256, 0, st>>>(L0.b, r, n);
-        vcycle(g, 0, st);
-        k_copy<<<G, 256, 0, st>>>(z, L0.x, n);
-        dot(g, r, z, n, S_RZNEW, st);
-        k_scalars_beta<<<1, 1, 0, st>>>(g->scal);
-        k_update_p<<<G, 256, 0, st>>>(p, z, g->scal, n);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    k_pcg_init<<<1, 1, 0, st>>>(g->scal, tol, g->stats, flag, h);
+    cudaGraph_t body = nullptr;
+    {
+        const cudaGraphNode_t *deps = nullptr;
+        const cudaGraphEdgeData *ed = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd);
+        if (e != cudaSuccess) return e;
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = h;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, cg, deps, ed, nd, &prm);
+        if (e != cudaSuccess) return e;
+        body = prm.conditional.phGraph_out[0];
+        e = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) return e;
     }
-    return it;
+    e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    k_apply_dot<<<NB, 256, 0, sb>>>(A, p, Ap, g->partial);
+    k_final<<<1, 256, 0, sb>>>(g->partial, NB, g->scal, S_PAP, 1);
+    k_update_xr_dot<<<NB, 256, 0, sb>>>(x, r, p, Ap, g->scal, n, g->partial);
+    k_final_check<<<1, 256, 0, sb>>>(g->partial, NB, g->scal, maxit, g->stats, flag, h);
+    vcycle(g, 0, sb, z, r);
+    k_dot_partial<<<NB, 256, 0, sb>>>(r, z, n, g->partial);
+    k_final<<<1, 256, 0, sb>>>(g->partial, NB, g->scal, S_RZNEW, 2);
+    k_update_p<<<G, 256, 0, sb>>>(p, z, g->scal, n);
+    return cudaStreamEndCapture(sb, &body);
 }
 
 static void set_operator(GummelState *g, bool poisson) {
@@ -471,7 +743,7 @@ int gummel_setup(Problem *p) {
     GummelState *g = new GummelState();
     p->gs = g;
     auto alloc = [&](double **ptr, size_t n) {
-        if (cudaMalloc(ptr, sizeof(double) * std::max<size_t>(n, 1)) != cudaSuccess) return false;
+        if (dmalloc((void **)ptr, sizeof(double) * std::max<size_t>(n, 1), p->stream) != cudaSuccess) return false;
         g->bytes += sizeof(double) * std::max<size_t>(n, 1);
         return true;
     };
@@ -484,7 +756,7 @@ int gummel_setup(Problem *p) {
         L.fx = (nx % 2 == 0 && nx >= 4) ? 2 : 1;
         L.fy = (ny % 2 == 0 && ny >= 4) ? 2 : 1;
         L.fz = (nz % 2 == 0 && nz >= 4) ? 2 : 1;
-        bool last = L.n <= 64 || (L.fx == 1 && L.fy == 1 && L.fz == 1) || g->lv.size() >= 16;
+        bool last = L.n <= 8 || (L.fx == 1 && L.fy == 1 && L.fz == 1) || g->lv.size() >= 16;
         if (last) L.fx = L.fy = L.fz = 1;
         g->lv.push_back(L);
         if (last) break;
@@ -499,16 +771,20 @@ int gummel_setup(Problem *p) {
              alloc(&L.pcx, L.n) && alloc(&L.pcy, L.n) && alloc(&L.pcz, L.n) && alloc(&L.pczlo, L.n) &&
              alloc(&L.x, L.n) && alloc(&L.b, L.n) && alloc(&L.r, L.n);
     }
-    ok = ok && alloc(&g->mu, N * p->s) && alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
+    ok = ok && alloc(&g->mu, N * p->s) && alloc(&g->phi, N) && alloc(&g->rho, N * p->s) &&
+         alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
          alloc(&g->z, N) && alloc(&g->pv, N) && alloc(&g->Ap, N) && alloc(&g->partial, kRedBlocks) &&
          alloc(&g->scal, S_COUNT);
     if (ok) {
-        if (cudaMalloc(&g->dmax, sizeof(unsigned long long)) != cudaSuccess) ok = false;
-        if (ok && cudaMallocHost(&g->h_pinned, sizeof(double) * 16) != cudaSuccess) ok = false;
+        if (dmalloc((void **)&g->dmax, sizeof(unsigned long long), p->stream) != cudaSuccess) ok = false;
+        if (ok && dmalloc((void **)&g->stats, sizeof(DevStats), p->stream) != cudaSuccess) ok = false;
+        for (int k = 0; k < 2 && ok; ++k)
+            if (cudaStreamCreateWithFlags(&g->cap[k], cudaStreamNonBlocking) != cudaSuccess) ok = false;
     }
     if (!ok) return PNP_ERR_NOMEM;
     p->device_bytes += g->bytes;
     p->mg_levels = (int)g->lv.size();
+    cudaFuncSetAttribute(k_coarse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
     // Poisson operator on every level (into the p* arrays)
     PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
     set_operator(g, true);
@@ -522,75 +798,59 @@ void gummel_free(Problem *p) {
     GummelState *g = p->gs;
     if (!g) return;
     for (auto &L : g->lv) {
-        for (double *a : {L.cx, L.cy, L.cz, L.czlo, L.pcx, L.pcy, L.pcz, L.pczlo, L.x, L.b, L.r}) cudaFree(a);
+        for (double *a : {L.cx, L.cy, L.cz, L.czlo, L.pcx, L.pcy, L.pcz, L.pczlo, L.x, L.b, L.r}) dfree(a, p->stream);
     }
-    for (double *a : {g->mu, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal}) cudaFree(a);
-    cudaFree(g->dmax);
-    cudaFreeHost(g->h_pinned);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (int k = 0; k < 2; ++k)
+        if (g->cap[k]) cudaStreamDestroy(g->cap[k]);
+    for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal})
+        dfree(a, p->stream);
+    dfree(g->dmax, p->stream);
+    dfree(g->stats, p->stream);
+    dfree(g->keep_q, p->stream);
+    dfree(g->keep_rhof, p->stream);
     delete g;
     p->gs = nullptr;
 }
 
-int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho, pnp_stats *stats,
-               cudaStream_t st) {
-    if (p->bc[2] != PNP_BC_DIRICHLET || p->bc[0] == PNP_BC_DIRICHLET || p->bc[1] == PNP_BC_DIRICHLET)
-        return PNP_ERR_INVALID;
-    int rc = gummel_setup(p);
-    if (rc) return rc;
+// Record one whole Gummel solve into g->graph: an outer WHILE node over
+// Gummel iterations whose body holds mu_ex, the Poisson solve, the phi
+// relaxation, per species the Slotboom coefficients, the NP solve and the
+// density update, and k_gummel_check, which ends the loop on convergence,
+// a status error or max_iter.  Works on g->phi and g->rho.
+static int build_graph(Problem *p, int *d_q, double *d_rhof) {
     GummelState *g = p->gs;
     const size_t N = p->npts();
     const int s = p->s;
     const int G = grid_for(N);
     PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
-    // device copies of the per-species integers and the fixed charge
-    int *d_q = nullptr;
-    double *d_rhof = nullptr;
-    cudaError_t e = cudaMalloc(&d_q, sizeof(int) * s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_q, p->q.data(), sizeof(int) * s, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !p->rho_f.empty()) {
-        e = cudaMalloc(&d_rhof, sizeof(double) * N);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_rhof, p->rho_f.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st);
-    }
-    if (e != cudaSuccess) {
-        cudaFree(d_q);
-        cudaFree(d_rhof);
-        return cuda_status(e);
-    }
-    // initial state
-    if (d_phi0) {
-        if (d_phi0 != d_phi) k_copy<<<G, 256, 0, st>>>(d_phi, d_phi0, N);
-    } else {
-        k_init_phi<<<G, 256, 0, st>>>(c, d_phi);
-    }
-    if (d_rho0) {
-        if (d_rho0 != d_rho) k_copy<<<G, 256, 0, st>>>(d_rho, d_rho0, N * s);
-    } else {
-        for (int i = 0; i < s; ++i) k_fill<<<G, 256, 0, st>>>(d_rho + i * N, p->rho_b[i], N);
-    }
-    cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
-    long long lin = 0;
-    int status = PNP_ERR_NOT_CONVERGED, it = 0;
-    double res = 0;
     const int maxlin = 2000;
-    for (it = 1; it <= p->max_iter; ++it) {
+    cudaStream_t st = p->stream, sb = g->cap[0], sc = g->cap[1];
+    const bool timer = p->timer.enabled;
+    p->timer.enabled = false;
+    cudaGraph_t top = nullptr;
+    cudaError_t e = cudaGraphCreate(&top, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    cudaGraphConditionalHandle hg;
+    cudaGraph_t body = nullptr;
+    int rc = PNP_OK;
+    if (e == cudaSuccess) e = add_while(st, 1, &hg, &body);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
         // 1. mu_ex from rho^{n-1}
-        rc = mu_ex_enqueue(p, p->precision, d_rho, g->mu, st);
-        if (rc) { status = rc; break; }
+        rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
+        cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
         // 2. Poisson for phi*, starting from phi
-        cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), st);
         set_operator(g, true);
-        k_poisson_rhs<<<G, 256, 0, st>>>(c, d_rho, s, d_q, d_rhof, g->rhs);
-        k_copy<<<G, 256, 0, st>>>(g->x, d_phi, N);
-        int li = pcg(g, g->x, g->rhs, p->lin_tol, maxlin, st);
+        k_poisson_rhs<<<G, 256, 0, sb>>>(c, g->rho, s, d_q, d_rhof, g->rhs);
+        k_copy<<<G, 256, 0, sb>>>(g->x, g->phi, N);
+        e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
         set_operator(g, true);
-        if (li < 0) { status = li; break; }
-        lin += li;
         // 3. relax phi
-        k_relax_phi<<<G, 256, 0, st>>>(d_phi, g->x, p->lambda_phi, N, g->dmax);
+        k_relax_phi<<<G, 256, 0, sb>>>(g->phi, g->x, p->lambda_phi, N, g->dmax);
         // 4. Nernst-Planck per species
-        bool fail = false;
-        for (int i = 0; i < s && !fail; ++i) {
+        for (int i = 0; i < s && e == cudaSuccess; ++i) {
             NpConst nc;
             nc.D = p->D[i];
             nc.q = p->q[i];
@@ -599,49 +859,119 @@ int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d
             nc.rlo = p->rho_b[i] * std::exp(p->q[i] * p->phi_lo + p->mu_bulk[i]);
             nc.rhi = p->rho_b[i] * std::exp(p->q[i] * p->phi_hi + p->mu_bulk[i]);
             Level &L0 = g->lv[0];
-            k_np_setup<<<G, 256, 0, st>>>(c, nc, d_phi, g->mu + i * N, d_rho + i * N, L0.cx, L0.cy, L0.cz, L0.czlo,
-                                          g->rhs, g->x, p->d_flag);
-            coarsen_all(g, st);
-            li = pcg(g, g->x, g->rhs, p->lin_tol, maxlin, st);
-            if (li < 0) { status = li; fail = true; break; }
-            lin += li;
-            k_np_finish<<<G, 256, 0, st>>>(N, (double)p->q[i], p->lambda_rho, p->rho_mix, 1.0 / p->rho_b[i], d_phi,
-                                           g->mu + i * N, g->x, d_rho + i * N, g->dmax, p->d_flag);
+            k_np_setup<<<G, 256, 0, sb>>>(c, nc, g->phi, g->mu + i * N, g->rho + i * N, L0.cx, L0.cy, L0.cz,
+                                          L0.czlo, g->rhs, g->x, p->d_flag);
+            coarsen_all(g, sb);
+            e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
+            k_np_finish<<<G, 256, 0, sb>>>(N, (double)p->q[i], p->lambda_rho, p->rho_mix, 1.0 / p->rho_b[i], g->phi,
+                                           g->mu + i * N, g->x, g->rho + i * N, g->dmax, p->d_flag);
         }
-        if (fail) break;
-        // 5. residual and status
-        unsigned long long hm = 0;
-        int hf = 0;
-        cudaMemcpyAsync(&hm, g->dmax, sizeof(hm), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(&hf, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) { status = cuda_status(e); break; }
-        double m;
-        std::memcpy(&m, &hm, sizeof(m));
-        res = m;
-        if (hf & kFlagPacking) { status = PNP_ERR_PACKING; break; }
-        if (hf & kFlagOverflow) { status = PNP_ERR_OVERFLOW; break; }
-        if (res < p->tol) { status = PNP_OK; break; }
+        // 5. residual, status, continue?
+        k_gummel_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->tol, p->max_iter, g->stats, hg);
+        cudaError_t e2 = cudaStreamEndCapture(sb, &body);
+        if (e == cudaSuccess) e = e2;
     }
-    if (it > p->max_iter) it = p->max_iter;
-    cudaStreamSynchronize(st);
-    if (status != PNP_OK && status != PNP_ERR_NOT_CONVERGED) {
-        // a packing error in mu_ex poisons everything after it: report it first
-        int hf = 0;
-        if (cudaMemcpy(&hf, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && (hf & kFlagPacking))
-            status = PNP_ERR_PACKING;
+    cudaError_t e3 = cudaStreamEndCapture(st, &top);
+    if (e == cudaSuccess) e = e3;
+    p->timer.enabled = timer;
+    if (e == cudaSuccess && rc == PNP_OK) e = cudaGraphInstantiate(&g->exec, top, 0);
+    if (e != cudaSuccess || rc != PNP_OK) {
+        cudaGetLastError();
+        if (top) cudaGraphDestroy(top);
+        return rc != PNP_OK ? rc : cuda_status(e);
+    }
+    g->graph = top;
+    return PNP_OK;
+}
+
+// Enqueue a whole solve on `st` (initial state, the solve graph, stats into
+// g->stats) without waiting.  Builds the graph on first use.
+int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaStream_t st) {
+    if (p->bc[2] != PNP_BC_DIRICHLET || p->bc[0] == PNP_BC_DIRICHLET || p->bc[1] == PNP_BC_DIRICHLET)
+        return PNP_ERR_INVALID;
+    int rc = gummel_setup(p);
+    if (rc) return rc;
+    rc = mu_ex_prepare(p, p->precision);
+    if (rc) return rc;
+    GummelState *g = p->gs;
+    const size_t N = p->npts();
+    const int s = p->s;
+    const int G = grid_for(N);
+    if (!g->exec) {
+        // per-species integers and the fixed charge live as long as the graph
+        int *d_q = nullptr;
+        double *d_rhof = nullptr;
+        cudaError_t e = dmalloc((void **)&d_q, sizeof(int) * s, p->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(d_q, p->q.data(), sizeof(int) * s, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !p->rho_f.empty()) {
+            e = dmalloc((void **)&d_rhof, sizeof(double) * N, p->stream);
+            if (e == cudaSuccess) e = cudaMemcpy(d_rhof, p->rho_f.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            dfree(d_q, p->stream);
+            dfree(d_rhof, p->stream);
+            return cuda_status(e);
+        }
+        g->keep_q = d_q;
+        g->keep_rhof = d_rhof;
+        rc = build_graph(p, d_q, d_rhof);
+        if (rc) return rc;
+    }
+    PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
+    if (d_phi0) k_copy<<<G, 256, 0, st>>>(g->phi, d_phi0, N);
+    else k_init_phi<<<G, 256, 0, st>>>(c, g->phi);
+    if (d_rho0) {
+        k_copy<<<G, 256, 0, st>>>(g->rho, d_rho0, N * s);
+    } else {
+        for (int i = 0; i < s; ++i) k_fill<<<G, 256, 0, st>>>(g->rho + i * N, p->rho_b[i], N);
     }
     cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
-    cudaStreamSynchronize(st);
-    cudaFree(d_q);
-    cudaFree(d_rhof);
+    k_stats_reset<<<1, 1, 0, st>>>(g->stats);
+    return cuda_status(cudaGraphLaunch(g->exec, st));
+}
+
+// Enqueue copies of the solve's state and record to caller buffers (device
+// or pinned host, any direction the runtime infers).
+int gummel_fetch(Problem *p, double *phi, double *rho, void *dev_stats_copy, cudaStream_t st) {
+    GummelState *g = p->gs;
+    const size_t N = p->npts();
+    cudaError_t e = cudaSuccess;
+    if (phi) e = cudaMemcpyAsync(phi, g->phi, sizeof(double) * N, cudaMemcpyDefault, st);
+    if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, g->rho, sizeof(double) * N * p->s, cudaMemcpyDefault, st);
+    if (dev_stats_copy && e == cudaSuccess)
+        e = cudaMemcpyAsync(dev_stats_copy, g->stats, sizeof(DevStats), cudaMemcpyDefault, st);
+    return cuda_status(e);
+}
+
+size_t gummel_stats_bytes() { return sizeof(DevStats); }
+
+void gummel_decode_stats(const void *raw, pnp_stats *out) {
+    const DevStats *hs = (const DevStats *)raw;
+    out->iterations = hs->iters;
+    out->residual = hs->residual;
+    out->linear_iterations = hs->lin;
+    out->status = hs->status;
+}
+
+int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho, pnp_stats *stats,
+               cudaStream_t st) {
+    int rc = gummel_launch(p, d_phi0, d_rho0, st);
+    if (rc) return rc;
+    DevStats hs;
+    rc = gummel_fetch(p, d_phi, d_rho, &hs, st);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    pnp_stats local{};
+    gummel_decode_stats(&hs, &local);
     if (stats) {
-        stats->iterations = it;
-        stats->residual = res;
-        stats->linear_iterations = lin;
-        stats->status = status;
+        stats->iterations = local.iterations;
+        stats->residual = local.residual;
+        stats->linear_iterations = local.linear_iterations;
+        stats->status = local.status;
     }
-    return status;
+    return local.status;
 }
 
 }  // namespace pnp

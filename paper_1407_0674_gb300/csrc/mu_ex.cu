@@ -766,7 +766,7 @@ static int upload_twiddles(const Problem *p, DeviceBuffers *db, int prec) {
             }
         }
         size_t bytes = (prec == PNP_PREC_FP64 ? 16 : 8) * (size_t)L;
-        cudaError_t e = cudaMalloc(&db->tw[c], bytes);
+        cudaError_t e = dmalloc(&db->tw[c], bytes, p->stream);
         if (e != cudaSuccess) return PNP_ERR_NOMEM;
         db->bytes += bytes;
         if (prec == PNP_PREC_FP64) {
@@ -780,10 +780,10 @@ static int upload_twiddles(const Problem *p, DeviceBuffers *db, int prec) {
     return PNP_OK;
 }
 
-static void free_buffers(DeviceBuffers *db) {
+static void free_buffers(DeviceBuffers *db, cudaStream_t st) {
     if (!db) return;
-    for (int c = 0; c < 3; ++c) cudaFree(db->tw[c]);
-    cudaFree(db->spec);
+    for (int c = 0; c < 3; ++c) dfree(db->tw[c], st);
+    dfree(db->spec, st);
     delete db;
 }
 
@@ -797,7 +797,7 @@ static int build_fp64(Problem *p) {
     const Dims d = make_dims(p);
     const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
     const size_t bytes = sizeof(double) * oct * kNumKernels * p->s;
-    if (cudaMalloc(&db->spec, bytes) != cudaSuccess) return PNP_ERR_NOMEM;
+    if (dmalloc(&db->spec, bytes, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     db->bytes += bytes;
     const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
     const bool odd[kNumKernels][3] = {{false, false, false}, {false, false, false}, {true, false, false},
@@ -829,7 +829,7 @@ int mu_ex_prepare(Problem *p, int prec) {
     if (rc) return rc;
     const Dims d = make_dims(p);
     const size_t n = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p->s;
-    if (cudaMalloc(&db->spec, sizeof(float) * n) != cudaSuccess) return PNP_ERR_NOMEM;
+    if (dmalloc(&db->spec, sizeof(float) * n, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     db->bytes += sizeof(float) * n;
     k_to_float<<<1024, 256, 0, p->stream>>>((const double *)p->buf[0]->spec, (float *)db->spec, n);
     cudaError_t e = cudaStreamSynchronize(p->stream);
@@ -841,7 +841,7 @@ int mu_ex_prepare(Problem *p, int prec) {
 // Workspace, FP64 spectra and the square-well field U = K_sw (x) rho_s.
 int mu_ex_setup(Problem *p) {
     p->work_bytes = workspace_bytes(p);
-    if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return PNP_ERR_NOMEM;
+    if (dmalloc(&p->d_work, p->work_bytes, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     p->device_bytes += p->work_bytes;
     int rc = build_fp64(p);
     if (rc) return rc;
@@ -851,16 +851,16 @@ int mu_ex_setup(Problem *p) {
     const size_t N = p->npts();
     p->sh_coef.assign(p->s, 0.0);
     for (int i = 0; i < p->s; ++i) p->sh_coef[i] = (p->sw_half ? 0.5 : 1.0) * (-p->depth[i]);
-    if (cudaMalloc(&p->d_U, sizeof(double) * N) != cudaSuccess) return PNP_ERR_NOMEM;
+    if (dmalloc((void **)&p->d_U, sizeof(double) * N, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     p->device_bytes += sizeof(double) * N;
     // site density into the FP64 staging area of the workspace end
     double *d_sites = nullptr, *d_rs = nullptr, *d_spec = nullptr;
-    cudaError_t e = cudaMalloc(&d_sites, sizeof(double) * std::max<size_t>(3, p->sites.size()));
-    if (e == cudaSuccess) e = cudaMalloc(&d_rs, sizeof(double) * N);
+    cudaError_t e = dmalloc((void **)&d_sites, sizeof(double) * std::max<size_t>(3, p->sites.size()), p->stream);
+    if (e == cudaSuccess) e = dmalloc((void **)&d_rs, sizeof(double) * N, p->stream);
     const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
-    if (e == cudaSuccess) e = cudaMalloc(&d_spec, sizeof(double) * oct);
+    if (e == cudaSuccess) e = dmalloc((void **)&d_spec, sizeof(double) * oct, p->stream);
     if (e != cudaSuccess) {
-        cudaFree(d_sites); cudaFree(d_rs); cudaFree(d_spec);
+        dfree(d_sites, p->stream); dfree(d_rs, p->stream); dfree(d_spec, p->stream);
         return PNP_ERR_NOMEM;
     }
     e = cudaMemcpy(d_sites, p->sites.data(), sizeof(double) * p->sites.size(), cudaMemcpyHostToDevice);
@@ -899,9 +899,9 @@ int mu_ex_setup(Problem *p) {
                                                        nullptr, one, l.P_x);
         e = cudaStreamSynchronize(p->stream);
     }
-    cudaFree(d_sites);
-    cudaFree(d_rs);
-    cudaFree(d_spec);
+    dfree(d_sites, p->stream);
+    dfree(d_rs, p->stream);
+    dfree(d_spec, p->stream);
     if (rc) return rc;
     return cuda_status(e);
 }
@@ -978,11 +978,11 @@ void StageTimer::release() {
 void mu_ex_free(Problem *p) {
     p->timer.release();
     for (int k = 0; k < 2; ++k) {
-        free_buffers(p->buf[k]);
+        free_buffers(p->buf[k], p->stream);
         p->buf[k] = nullptr;
     }
-    cudaFree(p->d_work);
-    cudaFree(p->d_U);
+    dfree(p->d_work, p->stream);
+    dfree(p->d_U, p->stream);
     p->d_work = nullptr;
     p->d_U = nullptr;
 }
@@ -1120,3 +1120,23 @@ extern "C" int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double 
     p.d_flag = nullptr;
     return (flag & (kFlagPacking | kFlagNonFinite)) ? PNP_ERR_PACKING : PNP_OK;
 }
+
+namespace pnp {
+
+// Device memory a problem will hold once its Gummel state exists: FFT
+// workspace, spectra (FP64, plus FP32 when that is the problem's precision),
+// square-well field, staging buffers and the multigrid hierarchy.
+size_t estimate_device_bytes(const Problem &p) {
+    const Dims d = make_dims(&p);
+    const size_t N = p.npts();
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p.s;
+    size_t b = workspace_bytes(&p) + oct * sizeof(double);
+    if (p.precision == PNP_PREC_FP32) b += oct * sizeof(float);
+    if (p.has_wells) b += N * sizeof(double);
+    b += sizeof(double) * (2 * N * p.s + N);                 // host-call staging
+    b += sizeof(double) * N * 11 * 8 / 7;                    // multigrid levels
+    b += sizeof(double) * N * (2 * (size_t)p.s + 7);         // solve state and CG vectors
+    return b + b / 16 + (1 << 20);
+}
+
+}  // namespace pnp

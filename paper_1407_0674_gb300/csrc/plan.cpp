@@ -297,7 +297,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     if (d->temperature_K <= 0 || d->eps_r <= 0 || d->h_nm <= 0) return bad("temperature, eps_r, h_nm must be > 0");
     if (!(d->lambda_phi > 0 && d->lambda_phi <= 1) || !(d->lambda_rho > 0 && d->lambda_rho <= 1))
         return bad("relaxation parameters must be in (0, 1]");
-    if (d->rho_mix != PNP_MIX_LINEAR && d->rho_mix != PNP_MIX_GEOMETRIC) return bad("bad rho_mix");
+    if (d->rho_mix < PNP_MIX_LINEAR || d->rho_mix > PNP_MIX_GEOMETRIC_LIMITED) return bad("bad rho_mix");
     if (!(d->tol > 0) || d->max_iter < 1) return bad("tol must be > 0 and max_iter >= 1");
     if (d->precision != PNP_PREC_FP64 && d->precision != PNP_PREC_FP32) return bad("bad precision");
     if (d->lin_tol < 0 || d->lin_tol >= 1) return bad("lin_tol must be in [0, 1)");
@@ -359,7 +359,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->wquad[0] = d->well_nmu; p->wquad[1] = d->well_ntheta; p->wquad[2] = d->well_nr;
     p->sw_half = d->sw_half ? 1 : 0;
     p->precision = d->precision;
-    p->lin_tol = d->lin_tol > 0 ? d->lin_tol : 1e-12;
+    p->lin_tol = d->lin_tol;      // 0: adaptive inner tolerance
     bulk_mu_rosenfeld(*p, p->mu_bulk);
     double n3 = 0;
     for (int i = 0; i < p->s; ++i) n3 += p->rho_b[i] * 4.0 * M_PI * std::pow(p->R[i], 3) / 3.0;

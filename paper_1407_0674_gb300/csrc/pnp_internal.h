@@ -72,7 +72,7 @@ struct Problem {
     int quad[3] = {0, 0, 0}, wquad[3] = {0, 0, 0};
     int sw_half = 1;
     int precision = 0;
-    double lin_tol = 1e-12;
+    double lin_tol = 0.0;             // 0: adaptive inner tolerance
     bool has_wells = false;
 
     // ---- plan ----
@@ -123,9 +123,19 @@ int gummel_setup(Problem *p);
 int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho,
                pnp_stats *stats, cudaStream_t st);
 void gummel_free(Problem *p);
+int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaStream_t st);
+int gummel_fetch(Problem *p, double *phi, double *rho, void *dev_stats_copy, cudaStream_t st);
+size_t gummel_stats_bytes();
+void gummel_decode_stats(const void *raw, pnp_stats *out);
+size_t estimate_device_bytes(const Problem &p);   // problem + Gummel state, from the plan
 
 // api.cpp helpers
 int cuda_status(cudaError_t e);
+// Device allocations of a problem are stream-ordered (cudaMallocAsync on the
+// problem's stream, completed before return; cudaFreeAsync), so freeing one
+// problem never waits for work of the others.
+cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st);
+void dfree(void *ptr, cudaStream_t st);
 int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why);
 void destroy_problem_internal(Problem *p);
 

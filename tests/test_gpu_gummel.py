@@ -67,6 +67,17 @@ def test_dense_film_trajectory_matches_oracle(pnp):
     compare(spec, pnp)
 
 
+def test_deep_wells_step_limited_trajectory(pnp):
+    """Batch-workload physics at 12^3: wells 12 kT deep, packing 0.3, step-
+    limited geometric relaxation; six iterations match the oracle (the step
+    limit is active in the first ones)."""
+    from workloads import batch_specs
+    spec = batch_specs(1, grids=[(12, 12, 12)])[0]
+    spec.depth = (12.0, 0.0)
+    spec.tol, spec.max_iter, spec.lin_tol = 1e-30, 6, 1e-13
+    compare(spec, pnp)
+
+
 def test_converged_state_matches_oracle(pnp):
     spec = dilute(0.0, 0.5)
     phi, rho, st, ref = compare(spec, pnp)

@@ -58,6 +58,13 @@ def test_geometric_relaxation_same_fixed_point(zero_bias):
     np.testing.assert_allclose(r2["phi"], r["phi"], atol=1e-9)
 
 
+def test_step_limited_relaxation_same_fixed_point(zero_bias):
+    spec, r = zero_bias
+    r2 = oracle.gummel(film(0.2, 0.2, mix=2))
+    assert r2["status"] == 0
+    np.testing.assert_allclose(r2["rho"], r["rho"], rtol=1e-8)
+
+
 def test_biased_flux_is_conserved():
     spec = film(0.0, 0.6)
     r = oracle.gummel(spec)

@@ -46,7 +46,7 @@ class ProblemSpec:
     phi_hi: float = 0.0                      # Dirichlet potential at the z = top side (kT/e)
     lambda_phi: float = 0.3
     lambda_rho: float = 0.3
-    rho_mix: int = 0                         # 0 linear density relaxation, 1 geometric
+    rho_mix: int = 0                         # 0 linear, 1 geometric, 2 geometric step-limited
     tol: float = 1e-8
     max_iter: int = 500
     quad_nmu: int = 0                        # FMT quadrature counts (0 = default rule)
@@ -155,11 +155,13 @@ def film3(nx: int = 128, ny: int = 128, nz: int = 256, nsites: Optional[int] = N
 # temperatures U(250, 400) K with well depth 0.3 eV / kT, total packing
 # fraction U(0.1, 0.35) split equally over the two ions, fixed-charge seeds
 # 100..163, sites at one per 512 cells (seed = fixed-charge seed + 1000).
+# Wells 9-14 kT deep on a fluid at packing up to 0.35 need the step-limited
+# geometric density relaxation.
 BATCH_GRIDS = [(32, 32, 32), (48, 48, 48), (64, 64, 64), (80, 80, 96), (96, 96, 96)]
 KB_EV_PER_K = 8.617333262e-5
 
 
-def batch_specs(count: int = 64, seed: int = 4, grids=None, max_iter: int = 500,
+def batch_specs(count: int = 64, seed: int = 4, grids=None, max_iter: int = 2000,
                 tol: float = 1e-8) -> List[ProblemSpec]:
     rng = np.random.default_rng(seed)
     grids = BATCH_GRIDS if grids is None else grids
@@ -177,7 +179,7 @@ def batch_specs(count: int = 64, seed: int = 4, grids=None, max_iter: int = 500,
         out.append(ProblemSpec(nx=nx, ny=ny, nz=nz, bc=("P", "P", "D"), R=(R, R), q=(1, -1),
                                rho_b=(rb, rb), depth=(depth, 0.0), well_inner=4.0, well_outer=5.0,
                                sites=sites, rho_f=rho_f, temperature_K=T, phi_lo=0.0, phi_hi=0.1,
-                               lambda_phi=0.3, lambda_rho=0.05, rho_mix=1, tol=tol, max_iter=max_iter))
+                               lambda_phi=0.3, lambda_rho=0.05, rho_mix=2, tol=tol, max_iter=max_iter))
     return out
 
 
@@ -196,21 +198,26 @@ def _smooth_sizes(lo: int, hi: int) -> List[int]:
 # --------------------------------------------------------------------------
 # Served requests: Poisson arrivals at `rate` per second (seed 5), cubic
 # grids with log-uniform edge in [32, 256] rounded to a 2^a 3^b 5^c size,
-# bias U(0, 1) kT/e, temperature U(250, 400) K.
-def serving_requests(count: int = 600, rate: float = 20.0, seed: int = 5, lo: int = 32,
-                     hi: int = 256, max_iter: int = 500, tol: float = 1e-8):
+# bias U(0, 1) kT/e, temperature U(250, 400) K (well depth 0.3 eV / kT).
+def serving_arrivals(count: int = 600, rate: float = 20.0, seed: int = 5, lo: int = 32, hi: int = 256):
+    """[(arrival time s, edge n, bias, temperature)]; build each problem with serving_spec."""
     rng = np.random.default_rng(seed)
     sizes = np.array(_smooth_sizes(lo, hi))
     t = 0.0
-    reqs = []
-    for j in range(count):
+    out = []
+    for _ in range(count):
         t += float(rng.exponential(1.0 / rate))
         edge = math.exp(rng.uniform(math.log(lo), math.log(hi)))
         n = int(sizes[np.argmin(np.abs(sizes - edge))])
         bias = float(rng.uniform(0.0, 1.0))
         T = float(rng.uniform(250.0, 400.0))
-        spec = film_gummel(n, n, n, tol=tol, max_iter=max_iter, phi_hi=bias)
-        spec.temperature_K = T
-        spec.depth = (0.3 / (KB_EV_PER_K * T), 0.0)
-        reqs.append((t, spec))
-    return reqs
+        out.append((t, n, bias, T))
+    return out
+
+
+def serving_spec(n: int, bias: float, T: float, max_iter: int = 2000, tol: float = 1e-8) -> ProblemSpec:
+    spec = film_gummel(n, n, n, tol=tol, max_iter=max_iter, phi_hi=bias)
+    spec.temperature_K = T
+    spec.depth = (0.3 / (KB_EV_PER_K * T), 0.0)
+    spec.rho_mix = 2
+    return spec
