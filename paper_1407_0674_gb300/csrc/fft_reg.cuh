@@ -147,7 +147,7 @@ template <int N1, int N2, typename C> struct LaneTw {
     __device__ __forceinline__ void load(const C *__restrict__ tw, int t) {
         constexpr int L = N1 * N2;
 #pragma unroll
-        for (int j = 0; j < Shape<N1, N2>::G; ++j) w[j] = __ldg(&tw[(t * j) % L]);
+        for (int j = 0; j < Shape<N1, N2>::G; ++j) w[j] = ldgc(&tw[(t * j) % L]);
     }
 };
 

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ddouble.cuh"
 #include "pnp_internal.h"
 
 namespace pnp {
@@ -18,6 +19,19 @@ namespace pnp {
 template <typename T> struct vec2;
 template <> struct vec2<double> { using type = double2; };
 template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<dd> { using type = dd2; };
+
+// read-only cached loads of scalars and complex values of every precision
+template <typename T> __device__ __forceinline__ T ldgt(const T *p) { return __ldg(p); }
+template <> __device__ __forceinline__ dd ldgt<dd>(const dd *p) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return dd(v.x, v.y);
+}
+template <typename C> __device__ __forceinline__ C ldgc(const C *p) { return __ldg(p); }
+template <> __device__ __forceinline__ dd2 ldgc<dd2>(const dd2 *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return dd2{dd(v.x, v.y), dd(v.z, v.w)};
+}
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
@@ -83,7 +97,7 @@ __device__ __forceinline__ void fft_stage(const C *__restrict__ a, C *__restrict
         for (int r = 0; r < R; ++r) {
             C x = a[(j + r * LR) * NL + l];
             if (r > 0 && k > 0) {
-                C w = __ldg(&tw[k * r * step]);
+                C w = ldgc(&tw[k * r * step]);
                 if (INV) w.y = -w.y;
                 x = cmul(x, w);
             }

@@ -1,0 +1,691 @@
+// Kernels and launch logic of the mu_ex pipeline, shared by the per-precision
+// translation units (mu_ex_fp64.cu, mu_ex_fp32.cu, mu_ex_df64.cu) and mu_ex.cu.
+//
+// Excess chemical potential mu_ex = mu_hs + mu_sh by zero-padded FFT
+// convolution (Sec 3.4) of the quadrature stencils of Sec 3.5.
+//
+// Pipeline for s species on an nx x ny x nz grid padded to Lx x Ly x Lz
+// (Wx = Lx/2 + 1 half-spectrum columns).  Passes only touch the lines that can
+// be non-zero (input inside the domain) or that are needed (output inside the
+// domain), so a zero-extended axis costs about half a full transform:
+//   1 x-fwd   : rho_i real lines -> R2C (two lines per complex FFT)   [s][nz][ny][Wx]
+//   2 y-fwd   : ny -> Ly                                              [s][nz][Ly][Wx]
+//   3 z-mac   : per (ky,kx) column: FFT_z(rho_i), n_alpha = sum_i conj(K_alpha,i) rho_i,
+//               inverse FFT_z, keep z < nz                            [10][nz][Ly][Wx]
+//   4 y-inv   : Ly -> ny                                              [10][nz][ny][Wx]
+//   5 x-fused : C2R of the ten n_alpha, Rosenfeld dPhi/dn_alpha in FP64 masked to
+//               the domain (Sec 2.3.1), R2C of the ten Psi_alpha      [10][nz][ny][Wx]
+//   6 y-fwd   : ny -> Ly                                              [10][nz][Ly][Wx]
+//   7 z-back  : FFT_z(Psi_alpha), mu_i = sum_alpha K_alpha,i Psi_alpha, inverse, z < nz
+//   8 y-inv   : Ly -> ny                                              [s][nz][ny][Wx]
+//   9 x-inv   : C2R, + mu_sh,i, write rho-shaped output
+// The kernel spectra are stored as one real octant per kernel (the stencils
+// are even or odd in each axis) with 1/(Lx Ly Lz) folded in.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+#include <vector>
+
+#include "fft_smem.cuh"
+#include "pnp_internal.h"
+
+namespace pnp {
+
+struct Dims {
+    int nx, ny, nz;
+    int Lx, Ly, Lz;
+    int Wx;            // Lx / 2 + 1
+    int Ox, Oy, Oz;    // octant extents
+    int npairs;        // (ny + 1) / 2
+};
+
+struct SpeciesConst {
+    int s;
+    double c0[8];      // 1 / (4 pi R^2)
+    double c1[8];      // 1 / (4 pi R)
+    double sh[8];      // mu_sh coefficient
+    float c0f[8], c1f[8];   // the same, pre-rounded for FP32 kernels
+    float c0h[8], c0l[8], c1h[8], c1l[8];   // and split for double-float kernels
+};
+
+template <typename T> __device__ __forceinline__ T sc_c0(const SpeciesConst &sc, int i);
+template <> __device__ __forceinline__ double sc_c0<double>(const SpeciesConst &sc, int i) { return sc.c0[i]; }
+template <> __device__ __forceinline__ float sc_c0<float>(const SpeciesConst &sc, int i) { return sc.c0f[i]; }
+template <> __device__ __forceinline__ dd sc_c0<dd>(const SpeciesConst &sc, int i) { return dd(sc.c0h[i], sc.c0l[i]); }
+template <typename T> __device__ __forceinline__ T sc_c1(const SpeciesConst &sc, int i);
+template <> __device__ __forceinline__ double sc_c1<double>(const SpeciesConst &sc, int i) { return sc.c1[i]; }
+template <> __device__ __forceinline__ float sc_c1<float>(const SpeciesConst &sc, int i) { return sc.c1f[i]; }
+template <> __device__ __forceinline__ dd sc_c1<dd>(const SpeciesConst &sc, int i) { return dd(sc.c1h[i], sc.c1l[i]); }
+
+struct DeviceBuffers {
+    int prec = 0;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    void *spec = nullptr;      // [s][5][Oz][Oy][Ox]
+    size_t bytes = 0;
+};
+
+static Dims make_dims(const Problem *p) {
+    Dims d;
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    d.Lx = p->L[0]; d.Ly = p->L[1]; d.Lz = p->L[2];
+    d.Wx = d.Lx / 2 + 1;
+    d.Ox = d.Lx / 2 + 1; d.Oy = d.Ly / 2 + 1; d.Oz = d.Lz / 2 + 1;
+    d.npairs = (d.ny + 1) / 2;
+    return d;
+}
+
+static SpeciesConst make_sc(const Problem *p) {
+    SpeciesConst sc{};
+    sc.s = p->s;
+    for (int i = 0; i < p->s; ++i) {
+        sc.c0[i] = 1.0 / (4.0 * M_PI * p->R[i] * p->R[i]);
+        sc.c1[i] = 1.0 / (4.0 * M_PI * p->R[i]);
+        sc.sh[i] = p->has_wells ? p->sh_coef[i] : 0.0;
+        sc.c0f[i] = (float)sc.c0[i];
+        sc.c1f[i] = (float)sc.c1[i];
+        const dd a(sc.c0[i]), b(sc.c1[i]);
+        sc.c0h[i] = a.hi; sc.c0l[i] = a.lo;
+        sc.c1h[i] = b.hi; sc.c1l[i] = b.lo;
+    }
+    return sc;
+}
+
+// ---------------------------------------------------------------------------
+// spectrum lookup: kernel `type` (0 shell, 1 ball, 2..4 vector x,y,z) of
+// species i at half-spectrum index (kx, ky, kz); vector kernels carry the
+// sign of their odd axis.
+template <typename T>
+__device__ __forceinline__ T spec_at(const T *__restrict__ sp, const Dims &d, int i, int type, int kx, int ky,
+                                     int kz) {
+    const int fy = ky <= d.Ly / 2 ? ky : d.Ly - ky;
+    const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    T v = ldgt(&sp[(size_t)(i * kNumKernels + type) * oct + ((size_t)fz * d.Oy + fy) * d.Ox + kx]);
+    if (type == 3 && ky > d.Ly / 2) v = -v;
+    if (type == 4 && kz > d.Lz / 2) v = -v;
+    return v;
+}
+
+// Rosenfeld FMT derivatives of Sec 2.3.1, FP64.
+__device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double psi[kNumWeighted]) {
+    const double n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
+    const double g = 1.0 / (1.0 - n3);
+    const double g2 = g * g;
+    const double v1v2 = n[4] * n[7] + n[5] * n[8] + n[6] * n[9];
+    const double v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
+    psi[0] = -log1p(-n3);
+    psi[1] = n2 * g;
+    psi[2] = n1 * g + (n2 * n2 - v2v2) * g2 * (1.0 / (8.0 * M_PI));
+    psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * g2 * g * (1.0 / (12.0 * M_PI));
+    for (int c = 0; c < 3; ++c) {
+        psi[4 + c] = -n[7 + c] * g;
+        psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * g2 * (1.0 / (4.0 * M_PI));
+    }
+    bool ok = n3 < 1.0;
+    for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a]);
+    return ok;
+}
+
+}  // namespace pnp
+
+#include "mu_ex_reg.cuh"
+
+namespace pnp {
+
+// ---------------------------------------------------------------------------
+// 1: real lines (FP64 input) -> half spectra along x.  Two y-lines share one
+// complex FFT.  grid (ceil(npairs/P), nz, F).
+template <typename T>
+__global__ void k_xfwd(const double *__restrict__ in, size_t in_fstride, typename vec2<T>::type *__restrict__ A,
+                       Dims d, FftAxis ax, const typename vec2<T>::type *__restrict__ tw, int P) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *a = reinterpret_cast<C *>(smem_raw);
+    C *b = a + (size_t)P * d.Lx;
+    const int z = blockIdx.y, f = blockIdx.z;
+    const int pair0 = blockIdx.x * P;
+    const double *src = in + f * in_fstride + (size_t)z * d.ny * d.nx;
+    for (int idx = threadIdx.x; idx < P * d.Lx; idx += blockDim.x) {
+        const int p = idx / d.Lx, x = idx % d.Lx;
+        const int y0 = 2 * (pair0 + p);
+        T re = 0, im = 0;
+        if (x < d.nx && y0 < d.ny) {
+            re = (T)src[(size_t)y0 * d.nx + x];
+            if (y0 + 1 < d.ny) im = (T)src[(size_t)(y0 + 1) * d.nx + x];
+        }
+        a[x * P + p] = C{re, im};
+    }
+    __syncthreads();
+    C *r = fft_lines<false>(a, b, P, ax, tw);
+    C *dst = A + ((size_t)f * d.nz + z) * d.ny * d.Wx;
+    for (int idx = threadIdx.x; idx < P * d.Wx; idx += blockDim.x) {
+        const int p = idx / d.Wx, k = idx % d.Wx;
+        const int y0 = 2 * (pair0 + p);
+        if (y0 >= d.ny) continue;
+        C zk = r[k * P + p];
+        C zm = r[((d.Lx - k) % d.Lx) * P + p];
+        // X = (Z_k + conj Z_{L-k}) / 2,  Y = (Z_k - conj Z_{L-k}) / (2i)
+        C X = C{(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
+        C Y = C{(T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x)};
+        dst[(size_t)y0 * d.Wx + k] = X;
+        if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.Wx + k] = Y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2/4/6/8: complex FFT along y of TX half-spectrum columns.  Input rows
+// j < n_in of an array with rows_in rows per plane (others are zero); output
+// rows j < n_out of an array with rows_out rows per plane.  grid (ceil(Wx/TX), nz, F).
+template <typename T, bool INV>
+__global__ void k_ypass(const typename vec2<T>::type *__restrict__ in, typename vec2<T>::type *__restrict__ out,
+                        Dims d, int rows_in, int n_in, int rows_out, int n_out, FftAxis ax,
+                        const typename vec2<T>::type *__restrict__ tw, int TX) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *a = reinterpret_cast<C *>(smem_raw);
+    C *b = a + (size_t)TX * d.Ly;
+    const int z = blockIdx.y, f = blockIdx.z, kx0 = blockIdx.x * TX;
+    const C *src = in + ((size_t)f * d.nz + z) * rows_in * d.Wx;
+    for (int idx = threadIdx.x; idx < TX * d.Ly; idx += blockDim.x) {
+        const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+        C v = C{0, 0};
+        if (j < n_in && kx < d.Wx) v = src[(size_t)j * d.Wx + kx];
+        a[j * TX + c] = v;
+    }
+    __syncthreads();
+    C *r = fft_lines<INV>(a, b, TX, ax, tw);
+    C *dst = out + ((size_t)f * d.nz + z) * rows_out * d.Wx;
+    for (int idx = threadIdx.x; idx < TX * n_out; idx += blockDim.x) {
+        const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+        if (kx < d.Wx) dst[(size_t)j * d.Wx + kx] = r[j * TX + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3: per (ky, kx-tile) column: forward z-FFT of the s density columns, the
+// weighted-density spectra n_alpha = sum_i conj(K_alpha,i) rho_i, inverse
+// z-FFT, rows z < nz.  grid (ceil(Wx/TX), Ly).
+template <typename T>
+__global__ void k_zmac(const typename vec2<T>::type *__restrict__ Bs, typename vec2<T>::type *__restrict__ B10,
+                       Dims d, FftAxis ax, const typename vec2<T>::type *__restrict__ tw, const T *__restrict__ spec,
+                       SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int col = TX * d.Lz;
+    C *rho = reinterpret_cast<C *>(smem_raw);   // s columns
+    C *work = rho + (size_t)sc.s * col;
+    C *scr = work + col;
+    const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    for (int i = 0; i < sc.s; ++i) {
+        const C *src = Bs + (size_t)i * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
+        C *dst = rho + (size_t)i * col;
+        for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+            const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+            C v = C{0, 0};
+            if (j < d.nz && kx < d.Wx) v = src[(size_t)j * d.Ly * d.Wx + kx];
+            dst[idx] = v;
+        }
+        __syncthreads();
+        fft_lines_inplace<false>(dst, scr, TX, ax, tw);
+    }
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+            const int kz = idx / TX, c = idx % TX, kx = kx0 + c;
+            C acc = C{0, 0};
+            if (kx < d.Wx) {
+                for (int i = 0; i < sc.s; ++i) {
+                    const C r = rho[(size_t)i * col + idx];
+                    if (alpha < 4) {
+                        T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
+                        if (alpha == 0) g *= sc_c0<T>(sc, i);
+                        if (alpha == 1) g *= sc_c1<T>(sc, i);
+                        acc.x += g * r.x;
+                        acc.y += g * r.y;
+                    } else {
+                        const int comp = (alpha - 4) % 3;
+                        T sv = spec_at(spec, d, i, 2 + comp, kx, ky, kz);
+                        if (alpha < 7) sv *= sc_c1<T>(sc, i);
+                        // conj(K) = +i S:  (i S)(a + ib) = (-S b, S a)
+                        acc.x -= sv * r.y;
+                        acc.y += sv * r.x;
+                    }
+                }
+            }
+            work[idx] = acc;
+        }
+        __syncthreads();
+        C *r = fft_lines<true>(work, scr, TX, ax, tw);
+        C *dst = B10 + (size_t)alpha * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
+        for (int idx = threadIdx.x; idx < TX * d.nz; idx += blockDim.x) {
+            const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+            if (kx < d.Wx) dst[(size_t)j * d.Ly * d.Wx + kx] = r[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5: for P pairs of y-lines in plane z: inverse x-FFT of the ten n_alpha,
+// dPhi/dn_alpha (FP64) inside the domain (zero outside), forward x-FFT of the
+// ten Psi_alpha, in place in A.  grid (ceil(npairs/P), nz).
+template <typename T>
+__global__ void k_xfused(typename vec2<T>::type *__restrict__ A, Dims d, FftAxis ax,
+                         const typename vec2<T>::type *__restrict__ tw, int *__restrict__ flag, int P) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int line = P * d.Lx;
+    C *fld = reinterpret_cast<C *>(smem_raw);   // 10 fields
+    C *scr = fld + (size_t)kNumWeighted * line;
+    const int z = blockIdx.y, pair0 = blockIdx.x * P;
+    const size_t fstride = (size_t)d.nz * d.ny * d.Wx;
+    C *base = A + (size_t)z * d.ny * d.Wx;
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        C *buf = fld + (size_t)alpha * line;
+        const C *src = base + alpha * fstride;
+        for (int idx = threadIdx.x; idx < line; idx += blockDim.x) {
+            const int p = idx / d.Lx, k = idx % d.Lx;
+            const int y0 = 2 * (pair0 + p);
+            C Z = C{0, 0};
+            if (y0 < d.ny) {
+                const bool up = k > d.Lx / 2;
+                const int kk = up ? d.Lx - k : k;
+                C X = src[(size_t)y0 * d.Wx + kk];
+                C Y = (y0 + 1 < d.ny) ? src[(size_t)(y0 + 1) * d.Wx + kk] : C{0, 0};
+                if (up) { X.y = -X.y; Y.y = -Y.y; }
+                Z = C{X.x - Y.y, X.y + Y.x};     // X + iY
+            }
+            buf[k * P + p] = Z;
+        }
+        __syncthreads();
+        fft_lines_inplace<true>(buf, scr, P, ax, tw);
+    }
+    // pointwise derivatives; line y0 in .x, line y0+1 in .y
+    int bad = 0;
+    for (int idx = threadIdx.x; idx < line; idx += blockDim.x) {
+        const int p = idx / d.Lx, x = idx % d.Lx;
+        const int y0 = 2 * (pair0 + p);
+        for (int h = 0; h < 2; ++h) {
+            const int y = y0 + h;
+            double n[kNumWeighted], psi[kNumWeighted];
+            const bool inside = x < d.nx && y < d.ny;
+            for (int a = 0; a < kNumWeighted; ++a) {
+                C v = fld[(size_t)a * line + x * P + p];
+                n[a] = (double)(h ? v.y : v.x);
+            }
+            if (inside) {
+                if (!fmt_dphi(n, psi)) bad = 1;
+            } else {
+                for (int a = 0; a < kNumWeighted; ++a) psi[a] = 0.0;
+            }
+            for (int a = 0; a < kNumWeighted; ++a) {
+                C &v = fld[(size_t)a * line + x * P + p];
+                if (h) v.y = (T)psi[a]; else v.x = (T)psi[a];
+            }
+        }
+    }
+    if (bad) atomicOr(flag, kFlagPacking);
+    __syncthreads();
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        C *buf = fld + (size_t)alpha * line;
+        C *r = fft_lines<false>(buf, scr, P, ax, tw);
+        C *dst = base + alpha * fstride;
+        for (int idx = threadIdx.x; idx < P * d.Wx; idx += blockDim.x) {
+            const int p = idx / d.Wx, k = idx % d.Wx;
+            const int y0 = 2 * (pair0 + p);
+            if (y0 >= d.ny) continue;
+            C zk = r[k * P + p];
+            C zm = r[((d.Lx - k) % d.Lx) * P + p];
+            C X = C{(T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y)};
+            C Y = C{(T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x)};
+            dst[(size_t)y0 * d.Wx + k] = X;
+            if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.Wx + k] = Y;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 7: per column: forward z-FFT of each Psi_alpha, accumulate
+// mu_i = sum_alpha K_alpha,i Psi_alpha, inverse z-FFT, rows z < nz.
+template <typename T>
+__global__ void k_zback(const typename vec2<T>::type *__restrict__ B10, typename vec2<T>::type *__restrict__ Bs,
+                        Dims d, FftAxis ax, const typename vec2<T>::type *__restrict__ tw, const T *__restrict__ spec,
+                        SpeciesConst sc, int TX) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int col = TX * d.Lz;
+    C *acc = reinterpret_cast<C *>(smem_raw);   // s accumulators
+    C *work = acc + (size_t)sc.s * col;
+    C *scr = work + col;
+    const int ky = blockIdx.y, kx0 = blockIdx.x * TX;
+    for (int idx = threadIdx.x; idx < sc.s * col; idx += blockDim.x) acc[idx] = C{0, 0};
+    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
+        const C *src = B10 + (size_t)alpha * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
+        for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+            const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+            C v = C{0, 0};
+            if (j < d.nz && kx < d.Wx) v = src[(size_t)j * d.Ly * d.Wx + kx];
+            work[idx] = v;
+        }
+        __syncthreads();
+        C *r = fft_lines<false>(work, scr, TX, ax, tw);
+        for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+            const int kz = idx / TX, c = idx % TX, kx = kx0 + c;
+            if (kx >= d.Wx) continue;
+            const C v = r[idx];
+            for (int i = 0; i < sc.s; ++i) {
+                C &o = acc[(size_t)i * col + idx];
+                if (alpha < 4) {
+                    T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
+                    if (alpha == 0) g *= sc_c0<T>(sc, i);
+                    if (alpha == 1) g *= sc_c1<T>(sc, i);
+                    o.x += g * v.x;
+                    o.y += g * v.y;
+                } else {
+                    const int comp = (alpha - 4) % 3;
+                    T sv = spec_at(spec, d, i, 2 + comp, kx, ky, kz);
+                    if (alpha < 7) sv *= sc_c1<T>(sc, i);
+                    // K = -i S:  (-i S)(a + ib) = (S b, -S a)
+                    o.x += sv * v.y;
+                    o.y -= sv * v.x;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < sc.s; ++i) {
+        C *r = fft_lines<true>(acc + (size_t)i * col, work, TX, ax, tw);
+        C *dst = Bs + (size_t)i * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
+        for (int idx = threadIdx.x; idx < TX * d.nz; idx += blockDim.x) {
+            const int j = idx / TX, c = idx % TX, kx = kx0 + c;
+            if (kx < d.Wx) dst[(size_t)j * d.Ly * d.Wx + kx] = r[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 9: inverse x-FFT of F half-spectrum fields, write real values x < nx as
+// FP64, optionally adding coef_f * U.  grid (ceil(npairs/P), nz, F).
+template <typename T>
+__global__ void k_xinv(const typename vec2<T>::type *__restrict__ A, double *__restrict__ out, size_t out_fstride,
+                       Dims d, FftAxis ax, const typename vec2<T>::type *__restrict__ tw,
+                       const double *__restrict__ U, SpeciesConst sc, int P) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *a = reinterpret_cast<C *>(smem_raw);
+    C *b = a + (size_t)P * d.Lx;
+    const int z = blockIdx.y, f = blockIdx.z, pair0 = blockIdx.x * P;
+    const C *src = A + ((size_t)f * d.nz + z) * d.ny * d.Wx;
+    for (int idx = threadIdx.x; idx < P * d.Lx; idx += blockDim.x) {
+        const int p = idx / d.Lx, k = idx % d.Lx;
+        const int y0 = 2 * (pair0 + p);
+        C Z = C{0, 0};
+        if (y0 < d.ny) {
+            const bool up = k > d.Lx / 2;
+            const int kk = up ? d.Lx - k : k;
+            C X = src[(size_t)y0 * d.Wx + kk];
+            C Y = (y0 + 1 < d.ny) ? src[(size_t)(y0 + 1) * d.Wx + kk] : C{0, 0};
+            if (up) { X.y = -X.y; Y.y = -Y.y; }
+            Z = C{X.x - Y.y, X.y + Y.x};
+        }
+        a[k * P + p] = Z;
+    }
+    __syncthreads();
+    C *r = fft_lines<true>(a, b, P, ax, tw);
+    double *dst = out + f * out_fstride + (size_t)z * d.ny * d.nx;
+    const double coef = U ? sc.sh[f] : 0.0;
+    for (int idx = threadIdx.x; idx < P * d.nx; idx += blockDim.x) {
+        const int p = idx / d.nx, x = idx % d.nx;
+        const int y0 = 2 * (pair0 + p);
+        if (y0 >= d.ny) continue;
+        C v = r[x * P + p];
+        double u0 = 0, u1 = 0;
+        if (U) {
+            u0 = coef * U[((size_t)z * d.ny + y0) * d.nx + x];
+            if (y0 + 1 < d.ny) u1 = coef * U[((size_t)z * d.ny + y0 + 1) * d.nx + x];
+        }
+        dst[(size_t)y0 * d.nx + x] = (double)v.x + u0;
+        if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (double)v.y + u1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static int pick_pow2(long limit, int cap) {
+    int v = 1;
+    while (v * 2 <= cap && v * 2 <= limit) v *= 2;
+    return v;
+}
+
+struct Launch {
+    int P_x, P_fused, TX_y, TX_z;
+    size_t sm_x, sm_fused, sm_y, sm_zmac, sm_zback, sm_zconv;
+};
+
+static Launch launch_shape(const Problem *p, int prec) {
+    const Dims d = make_dims(p);
+    const size_t cs = prec == PNP_PREC_FP32 ? 8 : 16;
+    const long budget = 96 * 1024;
+    Launch l;
+    l.P_x = pick_pow2(std::min<long>(48 * 1024 / (2 * cs * d.Lx), d.npairs), 16);
+    l.P_fused = pick_pow2(std::min<long>(budget / ((kNumWeighted + 1) * cs * d.Lx), d.npairs), 8);
+    l.TX_y = pick_pow2(std::min<long>(48 * 1024 / (2 * cs * d.Ly), d.Wx), 16);
+    l.TX_z = pick_pow2(std::min<long>(budget / ((p->s + 2) * cs * d.Lz), d.Wx), 16);
+    l.sm_x = 2 * cs * l.P_x * d.Lx;
+    l.sm_fused = (kNumWeighted + 1) * cs * l.P_fused * d.Lx;
+    l.sm_y = 2 * cs * l.TX_y * d.Ly;
+    l.sm_zmac = (p->s + 2) * cs * l.TX_z * d.Lz;
+    l.sm_zback = (p->s + 2) * cs * l.TX_z * d.Lz;
+    l.sm_zconv = 2 * 16 * l.TX_z * d.Lz;
+    return l;
+}
+
+template <typename T> static int set_smem_attrs() {
+    static bool done = false;
+    if (done) return PNP_OK;
+    const int big = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_ypass<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_ypass<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_zmac<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_xfused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_zback<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    e = e ? e : cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return cuda_status(e);
+    done = true;
+    return PNP_OK;
+}
+
+static size_t workspace_bytes(const Problem *p) {
+    const Dims d = make_dims(p);
+    const size_t wx = d.Wx, cs = 16;
+    size_t A = (size_t)kNumWeighted * d.nz * d.ny * wx;
+    size_t B10 = (size_t)kNumWeighted * d.nz * d.Ly * wx;
+    size_t Bs = (size_t)p->s * d.nz * d.Ly * wx;
+    return cs * (A + B10 + Bs) + 3 * 256;
+}
+
+struct Work {
+    void *A, *B10, *Bs;
+};
+
+static Work carve(const Problem *p, int prec) {
+    const Dims d = make_dims(p);
+    const size_t cs = prec == PNP_PREC_FP32 ? 8 : 16;
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    char *base = (char *)p->d_work;
+    size_t A = cs * kNumWeighted * d.nz * d.ny * d.Wx;
+    size_t B10 = cs * kNumWeighted * d.nz * d.Ly * d.Wx;
+    Work w;
+    w.A = base;
+    w.B10 = base + up(A);
+    w.Bs = base + up(A) + up(B10);
+    return w;
+}
+
+// Padded lengths with a register-resident two-factor FFT (fft_reg.cuh);
+// every other length uses the shared-memory Stockham kernels.
+template <typename F> static bool with_shape(int L, F &&f) {
+    using std::integral_constant;
+    switch (L) {
+        case 32: f(integral_constant<int, 8>{}, integral_constant<int, 4>{}); return true;
+        case 40: f(integral_constant<int, 8>{}, integral_constant<int, 5>{}); return true;
+        case 64: f(integral_constant<int, 8>{}, integral_constant<int, 8>{}); return true;
+        case 128: f(integral_constant<int, 16>{}, integral_constant<int, 8>{}); return true;
+        case 256: f(integral_constant<int, 16>{}, integral_constant<int, 16>{}); return true;
+        default: return false;
+    }
+}
+
+template <auto K> static void ensure_smem() {
+    static const bool done = [] {
+        cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return true;
+    }();
+    (void)done;
+}
+
+template <typename T>
+static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
+    using C = typename vec2<T>::type;
+    const int prec = std::is_same<T, float>::value ? PNP_PREC_FP32
+                     : (std::is_same<T, dd>::value ? PNP_PREC_DF64 : PNP_PREC_FP64);
+    int rc = set_smem_attrs<T>();
+    if (rc) return rc;
+    const Dims d = make_dims(p);
+    const Launch l = launch_shape(p, prec);
+    const SpeciesConst sc = make_sc(p);
+    Work w = carve(p, prec);
+    C *A = (C *)w.A, *B10 = (C *)w.B10, *Bs = (C *)w.Bs;
+    const C *twx = (const C *)db->tw[0], *twy = (const C *)db->tw[1], *twz = (const C *)db->tw[2];
+    const T *spec = (const T *)db->spec;
+    const int s = p->s;
+    const size_t N = p->npts();
+    const int T256 = 256;
+    StageTimer &tm = p->timer;
+    const size_t cs = sizeof(C);
+    const long kBudget = 96 * 1024;
+    auto pow2_le = [](long v) { long r = 1; while (r * 2 <= v) r *= 2; return (int)r; };
+
+    // 1: x forward
+    tm.begin(0, st);
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int P = std::max(1, std::min(256 / G, d.npairs));
+            ensure_smem<k_xfwd_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz, s);
+            k_xfwd_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(d_rho, N, A, d, twx, P);
+        })) {
+        dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
+        k_xfwd<T><<<gx, T256, l.sm_x, st>>>(d_rho, N, A, d, p->ax[0], twx, l.P_x);
+    }
+    tm.end(st);
+
+    // y passes: forward (rows ny -> Ly) or inverse (Ly -> ny) of F fields
+    auto ypass = [&](int stage, bool inv, const C *in, C *out, int F) {
+        tm.begin(stage, st);
+        const int rows_in = inv ? d.Ly : d.ny, rows_out = inv ? d.ny : d.Ly;
+        if (!with_shape(d.Ly, [&](auto a, auto b) {
+                constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                const int TX = pow2_le(std::min<long>(256 / G, 16));
+                dim3 g((d.Wx + TX - 1) / TX, d.nz, F);
+                const size_t sm = (size_t)TX * Shape<N1, N2>::EX * cs;
+                if (inv) {
+                    ensure_smem<k_ypass_r<T, true, N1, N2>>();
+                    k_ypass_r<T, true, N1, N2><<<g, TX * G, sm, st>>>(in, out, d, rows_in, rows_in, rows_out,
+                                                                     rows_out, twy, TX);
+                } else {
+                    ensure_smem<k_ypass_r<T, false, N1, N2>>();
+                    k_ypass_r<T, false, N1, N2><<<g, TX * G, sm, st>>>(in, out, d, rows_in, rows_in, rows_out,
+                                                                      rows_out, twy, TX);
+                }
+            })) {
+            dim3 g((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, F);
+            if (inv)
+                k_ypass<T, true><<<g, T256, l.sm_y, st>>>(in, out, d, rows_in, rows_in, rows_out, rows_out,
+                                                         p->ax[1], twy, l.TX_y);
+            else
+                k_ypass<T, false><<<g, T256, l.sm_y, st>>>(in, out, d, rows_in, rows_in, rows_out, rows_out,
+                                                          p->ax[1], twy, l.TX_y);
+        }
+        tm.end(st);
+    };
+
+    // z column kernels (MAC forward / back)
+    auto zpass = [&](int stage, bool back) {
+        tm.begin(stage, st);
+        if (!with_shape(d.Lz, [&](auto a, auto b) {
+                constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                // paired columns (ky, Ly - ky): 2 TX columns per CTA
+                const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
+                const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
+                dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
+                if (back) {
+                    ensure_smem<k_zback_p<T, N1, N2>>();
+                    k_zback_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(B10, Bs, d, twz, spec, sc, TX);
+                } else {
+                    ensure_smem<k_zmac_p<T, N1, N2>>();
+                    k_zmac_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(Bs, B10, d, twz, spec, sc, TX);
+                }
+            })) {
+            dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);
+            if (back)
+                k_zback<T><<<gz, T256, l.sm_zback, st>>>(B10, Bs, d, p->ax[2], twz, spec, sc, l.TX_z);
+            else
+                k_zmac<T><<<gz, T256, l.sm_zmac, st>>>(Bs, B10, d, p->ax[2], twz, spec, sc, l.TX_z);
+        }
+        tm.end(st);
+    };
+
+    ypass(1, false, A, Bs, s);
+    zpass(2, false);
+    ypass(3, true, B10, A, kNumWeighted);
+
+    // 5: x fused inverse -> dPhi/dn -> forward
+    tm.begin(4, st);
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int NQ = std::min(N2, (d.nx + N1 - 1) / N1);
+            const long per_pair = ((long)kNumWeighted * NQ * N1 + Shape<N1, N2>::EX) * (long)cs;
+            const int P = (int)std::max<long>(1, std::min<long>(std::min<long>(256 / G, d.npairs), kBudget / per_pair));
+            ensure_smem<k_xfused_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz);
+            k_xfused_r<T, N1, N2><<<g, P * G, P * per_pair, st>>>(A, d, twx, p->d_flag, P, NQ);
+        })) {
+        dim3 gf((d.npairs + l.P_fused - 1) / l.P_fused, d.nz);
+        k_xfused<T><<<gf, T256, l.sm_fused, st>>>(A, d, p->ax[0], twx, p->d_flag, l.P_fused);
+    }
+    tm.end(st);
+
+    ypass(5, false, A, B10, kNumWeighted);
+    zpass(6, true);
+    ypass(7, true, Bs, A, s);
+
+    // 9: x inverse + mu_sh
+    tm.begin(8, st);
+    const double *U = p->has_wells ? p->d_U : nullptr;
+    if (!with_shape(d.Lx, [&](auto a, auto b) {
+            constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+            const int P = std::max(1, std::min(256 / G, d.npairs));
+            ensure_smem<k_xinv_r<T, N1, N2>>();
+            dim3 g((d.npairs + P - 1) / P, d.nz, s);
+            k_xinv_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(A, d_mu, N, d, twx, U, sc, P);
+        })) {
+        dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
+        k_xinv<T><<<gx, T256, l.sm_x, st>>>(A, d_mu, N, d, p->ax[0], twx, U, sc, l.P_x);
+    }
+    tm.end(st);
+    return cuda_status(cudaGetLastError());
+}
+
+// one instantiation of run_pipeline per precision, each in its own file
+int run_pipeline_fp64(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
+int run_pipeline_fp32(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
+int run_pipeline_df64(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
+
+}  // namespace pnp

@@ -1,0 +1,9 @@
+// mu_ex pipeline instantiated in double FFT arithmetic (compiled on its own so
+// the precisions build in parallel).
+#include "mu_ex_core.cuh"
+
+namespace pnp {
+int run_pipeline_fp64(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
+    return run_pipeline<double>(p, db, d_rho, d_mu, st);
+}
+}  // namespace pnp

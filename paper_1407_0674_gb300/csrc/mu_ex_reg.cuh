@@ -445,7 +445,7 @@ __device__ __forceinline__ void load_spec(T (&g)[kChunk][N1], const T *__restric
         for (int k1 = 0; k1 < N1; ++k1) {
             const int kz = t + N2 * k1;
             const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
-            T v = have ? __ldg(&base[(size_t)fz * d.Oy * d.Ox]) : (T)0;
+            T v = have ? ldgt(&base[(size_t)fz * d.Oy * d.Ox]) : (T)0;
             if (flip_y || (type == 4 && kz > d.Lz / 2)) v = -v;
             g[j][k1] = v;
         }

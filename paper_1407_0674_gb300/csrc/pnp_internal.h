@@ -89,7 +89,7 @@ struct Problem {
     double *d_U = nullptr;            // square-well field sum_m K_sw[m] rho_s(r+m)
     std::vector<double> sh_coef;      // mu_sh,i = sh_coef[i] * U
     double *d_sh_coef = nullptr;
-    DeviceBuffers *buf[2] = {nullptr, nullptr};   // FP64, FP32
+    DeviceBuffers *buf[3] = {nullptr, nullptr, nullptr};   // FP64, FP32, double-float
     void *d_work = nullptr;           // shared FFT workspace
     size_t work_bytes = 0;
     double *d_io = nullptr;           // staging for host-pointer calls (s+1 fields)

@@ -59,6 +59,17 @@ def test_trajectory_matches_oracle(pnp, mix):
     assert st["status"] == pnp.ERR_NOT_CONVERGED
 
 
+def test_df64_trajectory_matches_oracle(pnp):
+    spec = dilute(0.0, 0.5, tol=1e-30, max_iter=6)
+    ref = oracle.gummel(spec)
+    with pnp.Problem(spec, precision="df64") as P:
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+    assert st["iterations"] == ref["iters"]
+    assert rel(phi, ref["phi"], 1.0) <= TOL
+    for i in range(spec.s):
+        assert rel(rho[i], ref["rho"][i]) <= TOL
+
+
 def test_dense_film_trajectory_matches_oracle(pnp):
     """The film workload's physics (R 2h, packing 0.2 per ion, wells, geometric
     relaxation 0.05) on a 12^3 grid, five iterations."""

@@ -60,6 +60,16 @@ def test_mu_ex_fp64_matches_oracle(pnp, case):
     np.testing.assert_array_equal(mu, mu2)          # deterministic
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mu_ex_df64_matches_oracle(pnp, case):
+    """Double-float FFT arithmetic (FP32 pairs) meets the FP64 bar."""
+    spec, rho = CASES[case]()
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="df64")
+    assert normwise(mu, ref) <= FP64_TOL
+
+
 @pytest.mark.parametrize("case", ["three_species_16", "film_wells_16"])
 def test_mu_ex_fp32_bound(pnp, case):
     spec, rho = CASES[case]()
@@ -99,8 +109,10 @@ def test_register_fft_shapes(pnp, shape, lens):
         assert P.info()["fft_len"] == lens
         mu = P.excess_mu(rho, precision="fp64")
         mu32 = P.excess_mu(rho, precision="fp32")
+        mudd = P.excess_mu(rho, precision="df64")
     assert normwise(mu, ref) <= FP64_TOL
     assert normwise(mu32, ref) <= FP32_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
 
 
 def test_film_workload_full_size(pnp):
@@ -140,10 +152,14 @@ def test_full_size_sampled(pnp):
     with pnp.Problem(spec) as P:
         mu = P.excess_mu(rho, precision="fp64").reshape(3, -1)
         mu32 = P.excess_mu(rho, precision="fp32").reshape(3, -1)
+        mudd = P.excess_mu(rho, precision="df64").reshape(3, -1)
     for i in range(3):
         scale = np.abs(mu[i]).max()
         assert np.abs(mu[i, flat] - ref[i]).max() / scale <= FP64_TOL
         assert np.abs(mu32[i, flat] - ref[i]).max() / scale <= FP32_TOL
+        assert np.abs(mudd[i, flat] - ref[i]).max() / scale <= FP64_TOL
+    # whole-field agreement of the two FP64-accuracy paths
+    assert np.abs(mudd - mu).max() / np.abs(mu).max() <= FP64_TOL
 
 
 def test_packing_error_reported(pnp):
