@@ -129,6 +129,22 @@ __device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double ps
     return ok;
 }
 
+// Rosenfeld dPhi/dn (FP64) in place on ten real fields [10][N] of type V:
+// n_alpha in, Psi_alpha out.
+template <typename V>
+__global__ void k_dphi_fields(V *__restrict__ f, size_t N, int *__restrict__ flag) {
+    bool bad = false;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        double n[kNumWeighted], psi[kNumWeighted];
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) n[a] = (double)f[a * N + p];
+        if (!fmt_dphi(n, psi)) bad = true;
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) f[a * N + p] = (V)psi[a];
+    }
+    if (bad) atomicOr(flag, kFlagPacking);
+}
+
 }  // namespace pnp
 
 #include "mu_ex_reg.cuh"
@@ -550,6 +566,9 @@ template <auto K> static void ensure_smem() {
     (void)done;
 }
 
+// split derivative stage (see stage 5 of run_pipeline)
+constexpr bool kSplitDerivatives = true;
+
 template <typename T>
 static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
     using C = typename vec2<T>::type;
@@ -646,16 +665,32 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     zpass(2, false);
     ypass(3, true, B10, A, kNumWeighted);
 
-    // 5: x fused inverse -> dPhi/dn -> forward
+    // 5: x inverse -> dPhi/dn -> forward.  Split form (real n fields through
+    // the idle y-spectra buffer, a pointwise FP64 kernel at full occupancy) or
+    // one fused kernel; both use the register FFT where the length allows.
     tm.begin(4, st);
+    using V = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    V *nf = reinterpret_cast<V *>(B10);     // [10][nz][ny][nx], B10 is free here
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
-            const int NQ = std::min(N2, (d.nx + N1 - 1) / N1);
-            const long per_pair = ((long)kNumWeighted * NQ * N1 + Shape<N1, N2>::EX) * (long)cs;
-            const int P = (int)std::max<long>(1, std::min<long>(std::min<long>(256 / G, d.npairs), kBudget / per_pair));
-            ensure_smem<k_xfused_r<T, N1, N2>>();
-            dim3 g((d.npairs + P - 1) / P, d.nz);
-            k_xfused_r<T, N1, N2><<<g, P * G, P * per_pair, st>>>(A, d, twx, p->d_flag, P, NQ);
+            if (kSplitDerivatives) {
+                const int P = std::max(1, std::min(256 / G, d.npairs));
+                const size_t sm = P * Shape<N1, N2>::EX * cs;
+                dim3 g((d.npairs + P - 1) / P, d.nz, kNumWeighted);
+                ensure_smem<k_xinv_raw_r<T, N1, N2, V>>();
+                k_xinv_raw_r<T, N1, N2, V><<<g, P * G, sm, st>>>(A, nf, d, twx, P);
+                k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag);
+                ensure_smem<k_xfwd_r<T, N1, N2, V>>();
+                k_xfwd_r<T, N1, N2, V><<<g, P * G, sm, st>>>(nf, N, A, d, twx, P);
+            } else {
+                const int NQ = std::min(N2, (d.nx + N1 - 1) / N1);
+                const long per_pair = ((long)kNumWeighted * NQ * N1 + Shape<N1, N2>::EX) * (long)cs;
+                const int P =
+                    (int)std::max<long>(1, std::min<long>(std::min<long>(256 / G, d.npairs), kBudget / per_pair));
+                ensure_smem<k_xfused_r<T, N1, N2>>();
+                dim3 g((d.npairs + P - 1) / P, d.nz);
+                k_xfused_r<T, N1, N2><<<g, P * G, P * per_pair, st>>>(A, d, twx, p->d_flag, P, NQ);
+            }
         })) {
         dim3 gf((d.npairs + l.P_fused - 1) / l.P_fused, d.nz);
         k_xfused<T><<<gf, T256, l.sm_fused, st>>>(A, d, p->ax[0], twx, p->d_flag, l.P_fused);

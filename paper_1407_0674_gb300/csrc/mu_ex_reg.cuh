@@ -38,8 +38,8 @@ __device__ __forceinline__ C pack_two(const C *__restrict__ x0, const C *__restr
 
 // ---------------------------------------------------------------------------
 // x forward (R2C, two real lines per complex FFT).  block P*G, grid (ceil(npairs/P), nz, F)
-template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_xfwd_r(const double *__restrict__ in, size_t in_fstride,
+template <typename T, int N1, int N2, typename InT = double>
+__global__ void __launch_bounds__(256) k_xfwd_r(const InT *__restrict__ in, size_t in_fstride,
                                                  typename vec2<T>::type *__restrict__ A, Dims d,
                                                  const typename vec2<T>::type *__restrict__ tw, int P) {
     using C = typename vec2<T>::type;
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_xfwd_r(const double *__restrict__ in, s
     LaneTw<N1, N2, C> lt;
     lt.load(tw, t);
     C v[G];
-    const double *src = in + f * in_fstride + (size_t)z * d.ny * d.nx;
+    const InT *src = in + f * in_fstride + (size_t)z * d.ny * d.nx;
     if (t < N1) {
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) {
@@ -113,6 +113,41 @@ __global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__
             }
             dst[(size_t)y0 * d.nx + x] = (double)v[n2].x + u0;
             if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (double)v[n2].y + u1;
+        }
+    }
+}
+
+// x inverse (C2R) of F fields into real arrays of type OutT (x < nx), for the
+// split form of the derivative stage
+template <typename T, int N1, int N2, typename OutT>
+__global__ void __launch_bounds__(256) k_xinv_raw_r(const typename vec2<T>::type *__restrict__ A,
+                                                     OutT *__restrict__ out, Dims d,
+                                                     const typename vec2<T>::type *__restrict__ tw, int P) {
+    using C = typename vec2<T>::type;
+    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX, L = N1 * N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = threadIdx.x / G, t = threadIdx.x % G;
+    C *ex = reinterpret_cast<C *>(smem_raw) + p * EX;
+    const int z = blockIdx.y, f = blockIdx.z, y0 = 2 * (blockIdx.x * P + p);
+    LaneTw<N1, N2, C> lt;
+    lt.load(tw, t);
+    C v[G];
+    const C *src = A + ((size_t)f * d.nz + z) * d.ny * d.Wx + (size_t)y0 * d.Wx;
+    if (t < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1)
+            v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
+                              : C{0, 0};
+    }
+    inv2<N1, N2>(v, lt, ex, t, 1);
+    if (t < N1 && y0 < d.ny) {
+        OutT *dst = out + ((size_t)f * d.nz + z) * d.ny * d.nx;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int x = t + N1 * n2;
+            if (x >= d.nx) continue;
+            dst[(size_t)y0 * d.nx + x] = (OutT)v[n2].x;
+            if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (OutT)v[n2].y;
         }
     }
 }
