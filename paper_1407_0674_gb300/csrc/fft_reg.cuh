@@ -149,19 +149,38 @@ template <int N1, int N2, typename C> struct LaneTw {
 #pragma unroll
         for (int j = 0; j < Shape<N1, N2>::G; ++j) w[j] = ldgc(&tw[(t * j) % L]);
     }
+    __device__ __forceinline__ C operator[](int j) const { return w[j]; }
+};
+
+// The same values in a shared-memory table [j][lane] (one per CTA), for
+// kernels whose register budget is better spent elsewhere.
+template <int N1, int N2, typename C> struct SmemTw {
+    const C *tab;
+    int t;
+    static constexpr int G = Shape<N1, N2>::G;
+    static constexpr int WORDS = G * G;
+    // every thread of the block calls fill; a __syncthreads must follow
+    static __device__ __forceinline__ void fill(C *tab, const C *__restrict__ tw) {
+        constexpr int L = N1 * N2;
+        for (int k = threadIdx.x; k < G * G; k += blockDim.x) {
+            const int j = k / G, lane = k % G;
+            tab[k] = ldgc(&tw[(lane * j) % L]);
+        }
+    }
+    __device__ __forceinline__ C operator[](int j) const { return tab[j * G + t]; }
 };
 
 // forward: lane t < N1 gives x[t + N1 n2] in v[n2] (n2 < N2); on return lane
 // t < N2 holds X[t + N2 k1] in v[k1] (k1 < N1).  ex = this line's exchange
 // buffer, element a at ex[a * xs] (xs = number of interleaved lines).
 // Contains two __syncthreads (every thread of the block must call).
-template <int N1, int N2, typename C>
-__device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const LaneTw<N1, N2, C> &tw, C *ex, int t, int xs) {
+template <int N1, int N2, typename C, typename TW>
+__device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs) {
     constexpr int S = N2 + 1;
     if (t < N1) {
         rdftR<N2, false>(v);
 #pragma unroll
-        for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw.w[k2]);
+        for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[k2]);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) ex[(t * S + k2) * xs] = v[k2];
     }
@@ -176,13 +195,13 @@ __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const LaneTw<N1, 
 
 // inverse (unnormalised): lane t < N2 gives X[t + N2 k1] in v[k1]; on return
 // lane t < N1 holds x[t + N1 n2] in v[n2].
-template <int N1, int N2, typename C>
-__device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const LaneTw<N1, N2, C> &tw, C *ex, int t, int xs) {
+template <int N1, int N2, typename C, typename TW>
+__device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs) {
     constexpr int S = N2 + 1;
     if (t < N2) {
         rdftR<N1, true>(v);
 #pragma unroll
-        for (int n1 = 1; n1 < N1; ++n1) v[n1] = cmul(v[n1], cconj(tw.w[n1]));
+        for (int n1 = 1; n1 < N1; ++n1) v[n1] = cmul(v[n1], cconj(tw[n1]));
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) ex[(n1 * S + t) * xs] = v[n1];
     }

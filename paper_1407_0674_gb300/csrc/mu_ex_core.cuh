@@ -644,12 +644,13 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
                 const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
                 dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
+                const size_t sm = 2 * TX * per_col + (size_t)G * G * cs;   // + twiddle table
                 if (back) {
                     ensure_smem<k_zback_p<T, N1, N2>>();
-                    k_zback_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(B10, Bs, d, twz, spec, sc, TX);
+                    k_zback_p<T, N1, N2><<<g, 2 * TX * G, sm, st>>>(B10, Bs, d, twz, spec, sc, TX);
                 } else {
                     ensure_smem<k_zmac_p<T, N1, N2>>();
-                    k_zmac_p<T, N1, N2><<<g, 2 * TX * G, 2 * TX * per_col, st>>>(Bs, B10, d, twz, spec, sc, TX);
+                    k_zmac_p<T, N1, N2><<<g, 2 * TX * G, sm, st>>>(Bs, B10, d, twz, spec, sc, TX);
                 }
             })) {
             dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);

@@ -4,6 +4,8 @@
 // two-factor shape (see fast_shape()).  Included by mu_ex.cu only.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_reg.cuh"
 
 namespace pnp {
@@ -506,8 +508,19 @@ __global__ void __launch_bounds__(256) k_zmac_p(const typename vec2<T>::type *__
     int ky;
     const bool ok = zcol(d, kyp, b, kx, ky);
     const size_t plane = (size_t)d.Ly * d.Wx;
-    LaneTw<N1, N2, C> lt;
-    lt.load(tw, t);
+    // 64-bit types: lane twiddles from a shared table (frees 2 G registers);
+    // FP32 keeps them in registers
+    C *twtab = slots + (size_t)sc.s * N1 * G * lanes + (size_t)Shape<N1, N2>::EX * lanes;
+    using TwT = typename std::conditional<std::is_same<T, float>::value, LaneTw<N1, N2, C>, SmemTw<N1, N2, C>>::type;
+    TwT lt;
+    if constexpr (std::is_same<T, float>::value) {
+        lt.load(tw, t);
+    } else {
+        SmemTw<N1, N2, C>::fill(twtab, tw);
+        __syncthreads();
+        lt.tab = twtab;
+        lt.t = t;
+    }
     C v[G];
     for (int i = 0; i < sc.s; ++i) {
         const C *src = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
@@ -589,8 +602,19 @@ __global__ void __launch_bounds__(256) k_zback_p(const typename vec2<T>::type *_
     int ky;
     const bool ok = zcol(d, kyp, b, kx, ky);
     const size_t plane = (size_t)d.Ly * d.Wx;
-    LaneTw<N1, N2, C> lt;
-    lt.load(tw, t);
+    // 64-bit types: lane twiddles from a shared table (frees 2 G registers);
+    // FP32 keeps them in registers
+    C *twtab = slots + (size_t)sc.s * N1 * G * lanes + (size_t)Shape<N1, N2>::EX * lanes;
+    using TwT = typename std::conditional<std::is_same<T, float>::value, LaneTw<N1, N2, C>, SmemTw<N1, N2, C>>::type;
+    TwT lt;
+    if constexpr (std::is_same<T, float>::value) {
+        lt.load(tw, t);
+    } else {
+        SmemTw<N1, N2, C>::fill(twtab, tw);
+        __syncthreads();
+        lt.tab = twtab;
+        lt.t = t;
+    }
     C v[G];
     if (t < N2)
         for (int i = 0; i < sc.s; ++i)
