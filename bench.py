@@ -205,8 +205,8 @@ def stage_flops(name, dims, s):
 # the 128^3 workload by the rows it moves; set to None whenever the kernel
 # changes after the capture.
 PROFILED_TRAFFIC = {
-    ("fp64", "z_back"): None,
-    ("fp32", "z_back"): None,
+    ("fp64", "z_back"): 1.1299e9,     # k_zback_p_fp64_120_pad256.md
+    ("fp32", "z_back"): 5.559e8,      # k_zback_p_fp32_120_pad256.md
 }
 
 DTYPE = {"fp64": "f64",

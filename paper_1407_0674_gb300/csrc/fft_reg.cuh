@@ -1,5 +1,5 @@
 // Register-resident two-factor FFT of length L = N1 * N2 (N1, N2 in
-// {2, 3, 4, 5, 8, 16}, compile time).
+// {2, 3, 4, 5, 6, 8, 16}, compile time).
 //
 // One line is handled by a group of G = max(N1, N2) threads; lane t of the
 // group keeps its values in registers.  Forward transform of natural-order
@@ -97,6 +97,24 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft8(C *v) {
     (void)sizeof(T);
 }
 
+// 6 = 2 x 3 (Good-Thomas would need no twiddles; the plain split keeps the
+// same shape as radix 16): n = n1 + 2 n2, k = k2 + 3 k1
+template <bool INV, typename C> __device__ __forceinline__ void rdft6(C *v) {
+    C a0[3] = {v[0], v[2], v[4]};
+    C a1[3] = {v[1], v[3], v[5]};
+    rdft3<INV>(a0);
+    rdft3<INV>(a1);
+    const double sg = INV ? 1.0 : -1.0;
+    // W6^k2 for the odd half: 1, (1/2, -+sqrt3/2), (-1/2, -+sqrt3/2)
+    a1[1] = mulc(a1[1], 0.5, sg * kS3);
+    a1[2] = mulc(a1[2], -0.5, sg * kS3);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+        v[k2] = cadd(a0[k2], a1[k2]);
+        v[k2 + 3] = csub(a0[k2], a1[k2]);
+    }
+}
+
 // 16 = 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1
 template <bool INV, typename C> __device__ __forceinline__ void rdft16(C *v) {
     C a[4][4];
@@ -131,6 +149,7 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void rdftR(C *
     else if constexpr (R == 3) rdft3<INV>(v);
     else if constexpr (R == 4) rdft4<INV>(v);
     else if constexpr (R == 5) rdft5<INV>(v);
+    else if constexpr (R == 6) rdft6<INV>(v);
     else if constexpr (R == 8) rdft8<INV>(v);
     else if constexpr (R == 16) rdft16<INV>(v);
 }

@@ -549,9 +549,15 @@ static Work carve(const Problem *p, int prec) {
 template <typename F> static bool with_shape(int L, F &&f) {
     using std::integral_constant;
     switch (L) {
+        case 16: f(integral_constant<int, 4>{}, integral_constant<int, 4>{}); return true;
+        case 20: f(integral_constant<int, 5>{}, integral_constant<int, 4>{}); return true;
+        case 24: f(integral_constant<int, 8>{}, integral_constant<int, 3>{}); return true;
         case 32: f(integral_constant<int, 8>{}, integral_constant<int, 4>{}); return true;
         case 40: f(integral_constant<int, 8>{}, integral_constant<int, 5>{}); return true;
+        case 48: f(integral_constant<int, 16>{}, integral_constant<int, 3>{}); return true;
         case 64: f(integral_constant<int, 8>{}, integral_constant<int, 8>{}); return true;
+        case 80: f(integral_constant<int, 16>{}, integral_constant<int, 5>{}); return true;
+        case 96: f(integral_constant<int, 16>{}, integral_constant<int, 6>{}); return true;
         case 128: f(integral_constant<int, 16>{}, integral_constant<int, 8>{}); return true;
         case 256: f(integral_constant<int, 16>{}, integral_constant<int, 16>{}); return true;
         default: return false;

@@ -388,7 +388,14 @@ int plan_lengths(Problem *p, const int fft_len[3]) {
                 L = fft_len[c];
                 if (L < minL || !smooth235(L) || (even && L % 2)) return PNP_ERR_INVALID;
             } else {
+                // smallest legal length, or a register-FFT length when one is
+                // within 30% of it
                 L = next_smooth(minL, even);
+                for (int f : {16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 256})
+                    if (f >= minL && f <= L + (3 * L) / 10 && f >= L) {
+                        L = f;
+                        break;
+                    }
             }
         }
         if (L > 4096) return PNP_ERR_INVALID;

@@ -97,6 +97,11 @@ REG_SHAPES = [
     ((16, 12, 14), (128, 256, 40)),
     ((9, 11, 10), (256, 32, 128)),
     ((28, 7, 36), (64, 128, 256)),
+    ((12, 16, 90), (16, 20, 96)),
+    ((16, 76, 12), (20, 80, 16)),
+    ((90, 12, 10), (96, 16, 20)),
+    ((44, 9, 40), (48, 24, 48)),
+    ((76, 20, 9), (80, 24, 16)),
 ]
 
 
@@ -112,6 +117,20 @@ def test_register_fft_shapes(pnp, shape, lens):
         mudd = P.excess_mu(rho, precision="df64")
     assert normwise(mu, ref) <= FP64_TOL
     assert normwise(mu32, ref) <= FP32_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+
+
+def test_default_lengths_prefer_register_shapes(pnp):
+    """Minimal lengths 90, 24, 9 (S = 4): x moves up to the register length 96
+    (within 30%), y is one already, z stays at 9 (16 is too far) and runs the
+    shared-memory FFT."""
+    spec, rho = mu_microbench(shape=(86, 20, 5))
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (96, 24, 9)
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+    assert normwise(mu, ref) <= FP64_TOL
     assert normwise(mudd, ref) <= FP64_TOL
 
 
