@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=24, help="edge of the reference-arm sample box")
     ap.add_argument("--n", type=int, default=N_EDGE, help="grid edge (profiling runs use smaller cases)")
     ap.add_argument("--pad", type=int, default=PAD, help="padded FFT length")
-    ap.add_argument("--variants", default="fp64,df64,fp32", help="precisions to time, headline first")
+    ap.add_argument("--variants", default="fp64,df64,fp32,tf32split", help="precisions to time, headline first")
     ap.add_argument("--workload", default="mu_ex", choices=["mu_ex", "film", "batch", "serve"],
                     help="mu_ex (headline), film (one 32^3 Gummel solve), batch (64 solves), serve (arrivals)")
     ap.add_argument("--batch", type=int, default=64, help="solves in the batch workload")
@@ -211,8 +211,9 @@ PROFILED_TRAFFIC = {
 
 DTYPE = {"fp64": "f64",
          "df64": "df64 (FFT values as FP32 pairs, ~48-bit; FP64 derivatives)",
-         "fp32": "f32 FFT / f64 derivatives"}
-VARIANT_NAME = {"fp64": "fp64", "df64": "df64_fft", "fp32": "fp32_fft"}
+         "fp32": "f32 FFT / f64 derivatives",
+         "tf32split": "f32 FFT with the y-axis radix-16 DFT stages as 3xTF32 tensor-core products / f64 derivatives"}
+VARIANT_NAME = {"fp64": "fp64", "df64": "df64_fft", "fp32": "fp32_fft", "tf32split": "tf32split_fft"}
 
 # FP64 peak of the part, from its unit counts and clock: 152 SMs x 2 FP64 FMA
 # per clock x 2 flops x 2.07 GHz (an FMA-chain probe measured 1.195 TFLOP/s).
@@ -314,6 +315,21 @@ def run_gpu(args, world, rank, local):
         ms_step = reduce_max(world, sum(ms) / len(ms))
         results[prec] = {"ms": ms_step, "stages": st}
 
+    # each variant's error against the FP64 path (itself within 1e-10 of the
+    # oracle in the parity tests): max over species of ||mu - mu64|| / ||mu64||
+    errs = {}
+    if rank == 0:
+        P.excess_mu_device(d_rho, d_mu, precision="fp64", stream=sh)
+        torch.cuda.synchronize()
+        mu64 = d_mu.cpu().numpy().reshape(SPECIES, -1)
+        for prec in variants:
+            if prec == "fp64":
+                continue
+            P.excess_mu_device(d_rho, d_mu, precision=prec, stream=sh)
+            torch.cuda.synchronize()
+            m = d_mu.cpu().numpy().reshape(SPECIES, -1)
+            errs[prec] = max(float(abs(m[i] - mu64[i]).max() / abs(mu64[i]).max()) for i in range(SPECIES))
+
     # end to end through the host-pointer entry point, pinned host buffers
     h_rho = torch.from_numpy(rho).pin_memory().numpy()
     h_mu = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
@@ -337,7 +353,7 @@ def run_gpu(args, world, rank, local):
 
     def roof(prec):
         st = results[prec]["stages"]
-        cs = 8 if prec == "fp32" else 16
+        cs = 8 if prec in ("fp32", "tf32split") else 16
         name = max(st, key=lambda k: st[k][0])
         tot, n = st[name]
         avg = tot / max(n, 1)
@@ -399,7 +415,7 @@ def run_gpu(args, world, rank, local):
             "clocks": clocks,
             "variants": {VARIANT_NAME[p]: {
                 "value": vals[p], "unit": "Gpoints/s", "ms_per_step": results[p]["ms"],
-                "dtype": DTYPE[p], "roofline": roof(p)}
+                "dtype": DTYPE[p], "roofline": roof(p), "max_rel_err_vs_fp64": errs.get(p)}
                 for p in variants[1:]},
             "stages_ms": {p: {k: v[0] / max(v[1], 1) for k, v in results[p]["stages"].items()}
                           for p in results},

@@ -59,8 +59,12 @@ enum { PNP_BC_PERIODIC = 0, PNP_BC_DIRICHLET = 1, PNP_BC_NOFLUX = 2 };
  * its norms and the linear solves are FP64 in every variant.  PNP_PREC_DF64
  * carries each FFT value as an unevaluated sum of two FP32 numbers (about 48
  * significant bits) and runs the transforms on the FP32 pipes, which GB300
- * executes ~58x faster than FP64; it meets the FP64 accuracy bar of mu_ex. */
-enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF64 = 2 };
+ * executes ~58x faster than FP64; it meets the FP64 accuracy bar of mu_ex.
+ * PNP_PREC_TF32SPLIT is the FP32 variant with the y-axis transforms of length
+ * 256 run as two radix-16 DFT stages on the tensor cores, each product split
+ * into three TF32 products (hi*hi + lo*hi + hi*lo) accumulated in FP32; other
+ * y lengths use the FP32 path. */
+enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF64 = 2, PNP_PREC_TF32SPLIT = 3 };
 
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
@@ -94,7 +98,7 @@ typedef struct {
     int well_nmu, well_ntheta, well_nr;   /* square-well quadrature counts, 0 = default */
     int sw_half;                   /* 1: mu_sh keeps the factor 1/2 of Sec 2.3.2 */
     int fft_len[3];                /* padded FFT length per axis, 0 = smallest legal */
-    int precision;                 /* PNP_PREC_FP64 / FP32 / DF64: default for the calls below */
+    int precision;                 /* PNP_PREC_FP64 / FP32 / DF64 / TF32SPLIT: default for the calls below */
     double lin_tol;                /* relative residual ||r|| / ||b|| of the linear solves; 0 -> adaptive:
                                       min(1e-6, max(1e-12, 0.01 x previous Gummel residual)) */
     unsigned flags;                /* reserved, 0 */

@@ -100,7 +100,8 @@ static int read_flag(Problem *p, cudaStream_t st) {
 
 static int resolve_prec(const Problem *p, int prec) {
     if (prec == PNP_PREC_DEFAULT) return p->precision;
-    if (prec == PNP_PREC_FP64 || prec == PNP_PREC_FP32 || prec == PNP_PREC_DF64) return prec;
+    if (prec == PNP_PREC_FP64 || prec == PNP_PREC_FP32 || prec == PNP_PREC_DF64 || prec == PNP_PREC_TF32SPLIT)
+        return prec;
     return -100;
 }
 

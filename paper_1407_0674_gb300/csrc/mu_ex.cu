@@ -127,6 +127,7 @@ static void free_buffers(DeviceBuffers *db, cudaStream_t st) {
     if (!db) return;
     for (int c = 0; c < 3; ++c) dfree(db->tw[c], st);
     dfree(db->spec, st);
+    dfree(db->tc_b, st);
     delete db;
 }
 
@@ -162,6 +163,23 @@ static int build_fp64(Problem *p) {
 
 int mu_ex_prepare(Problem *p, int prec) {
     if (prec == PNP_PREC_FP64) return p->buf[0] ? PNP_OK : build_fp64(p);
+    if (prec == PNP_PREC_TF32SPLIT) {
+        // the FP32 buffers plus the split DFT matrices of the tensor-core y pass
+        int rc = mu_ex_prepare(p, PNP_PREC_FP32);
+        if (rc) return rc;
+        DeviceBuffers *db = p->buf[1];
+        if (db->tc_b) return PNP_OK;
+        std::vector<float> m(4 * 32 * 32);
+        ypass_tc_matrices(m.data());
+        const size_t bytes = m.size() * sizeof(float);
+        if (dmalloc((void **)&db->tc_b, bytes, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
+        cudaError_t e = cudaMemcpyAsync(db->tc_b, m.data(), bytes, cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        db->bytes += bytes;
+        p->device_bytes += bytes;
+        return PNP_OK;
+    }
     const int slot = prec == PNP_PREC_FP32 ? 1 : 2;
     if (p->buf[slot]) return PNP_OK;
     int rc = mu_ex_prepare(p, PNP_PREC_FP64);
@@ -261,7 +279,7 @@ int mu_ex_enqueue(Problem *p, int prec, const double *d_rho, double *d_mu, cudaS
     if (rc) return rc;
     if (prec == PNP_PREC_FP64) return run_pipeline_fp64(p, p->buf[0], d_rho, d_mu, st);
     if (prec == PNP_PREC_DF64) return run_pipeline_df64(p, p->buf[2], d_rho, d_mu, st);
-    return run_pipeline_fp32(p, p->buf[1], d_rho, d_mu, st);
+    return run_pipeline_fp32(p, p->buf[1], d_rho, d_mu, st, prec == PNP_PREC_TF32SPLIT);
 }
 
 // ---------------------------------------------------------------------------
@@ -482,7 +500,7 @@ size_t estimate_device_bytes(const Problem &p) {
     const size_t N = p.npts();
     const size_t oct = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p.s;
     size_t b = workspace_bytes(&p) + oct * sizeof(double);
-    if (p.precision == PNP_PREC_FP32) b += oct * sizeof(float);
+    if (p.precision == PNP_PREC_FP32 || p.precision == PNP_PREC_TF32SPLIT) b += oct * sizeof(float);
     if (p.precision == PNP_PREC_DF64) b += oct * sizeof(dd);
     if (p.has_wells) b += N * sizeof(double);
     b += sizeof(double) * (2 * N * p.s + N);                 // host-call staging

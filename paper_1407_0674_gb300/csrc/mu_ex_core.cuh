@@ -64,6 +64,7 @@ struct DeviceBuffers {
     int prec = 0;
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *spec = nullptr;      // [s][5][Oz][Oy][Ox]
+    float *tc_b = nullptr;     // split 16-point DFT matrices of the tensor-core y pass
     size_t bytes = 0;
 };
 
@@ -546,6 +547,12 @@ static Work carve(const Problem *p, int prec) {
 
 // Padded lengths with a register-resident two-factor FFT (fft_reg.cuh);
 // every other length uses the shared-memory Stockham kernels.
+// tensor-core (3xTF32) y pass of the FP32 pipeline, in its own unit
+bool ypass_tc_supported(const Dims &d);
+void ypass_tc_matrices(float *out);
+int launch_ypass_tc(bool inv, const float2 *in, float2 *out, const Dims &d, int rows_in, int n_in, int rows_out,
+                    int n_out, int F, const float2 *tw, const float *bmat, int *flag, cudaStream_t st);
+
 template <typename F> static bool with_shape(int L, F &&f) {
     using std::integral_constant;
     switch (L) {
@@ -576,7 +583,8 @@ template <auto K> static void ensure_smem() {
 constexpr bool kSplitDerivatives = true;
 
 template <typename T>
-static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
+static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st,
+                        bool tc = false) {
     using C = typename vec2<T>::type;
     const int prec = std::is_same<T, float>::value ? PNP_PREC_FP32
                      : (std::is_same<T, dd>::value ? PNP_PREC_DF64 : PNP_PREC_FP64);
@@ -615,6 +623,14 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     auto ypass = [&](int stage, bool inv, const C *in, C *out, int F) {
         tm.begin(stage, st);
         const int rows_in = inv ? d.Ly : d.ny, rows_out = inv ? d.ny : d.Ly;
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc && db->tc_b && ypass_tc_supported(d)) {
+                launch_ypass_tc(inv, in, out, d, rows_in, rows_in, rows_out, rows_out, F, twy, db->tc_b, p->d_flag,
+                                st);
+                tm.end(st);
+                return;
+            }
+        }
         if (!with_shape(d.Ly, [&](auto a, auto b) {
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
                 const int TX = pow2_le(std::min<long>(256 / G, 16));
@@ -727,7 +743,8 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
 
 // one instantiation of run_pipeline per precision, each in its own file
 int run_pipeline_fp64(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
-int run_pipeline_fp32(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
+int run_pipeline_fp32(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st,
+                      bool tc = false);
 int run_pipeline_df64(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st);
 
 }  // namespace pnp

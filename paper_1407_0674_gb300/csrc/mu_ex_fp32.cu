@@ -3,7 +3,7 @@
 #include "mu_ex_core.cuh"
 
 namespace pnp {
-int run_pipeline_fp32(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st) {
-    return run_pipeline<float>(p, db, d_rho, d_mu, st);
+int run_pipeline_fp32(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st, bool tc) {
+    return run_pipeline<float>(p, db, d_rho, d_mu, st, tc);
 }
 }  // namespace pnp

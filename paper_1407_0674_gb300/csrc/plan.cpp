@@ -299,7 +299,8 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
         return bad("relaxation parameters must be in (0, 1]");
     if (d->rho_mix < PNP_MIX_LINEAR || d->rho_mix > PNP_MIX_GEOMETRIC_LIMITED) return bad("bad rho_mix");
     if (!(d->tol > 0) || d->max_iter < 1) return bad("tol must be > 0 and max_iter >= 1");
-    if (d->precision != PNP_PREC_FP64 && d->precision != PNP_PREC_FP32 && d->precision != PNP_PREC_DF64)
+    if (d->precision != PNP_PREC_FP64 && d->precision != PNP_PREC_FP32 && d->precision != PNP_PREC_DF64 &&
+        d->precision != PNP_PREC_TF32SPLIT)
         return bad("bad precision");
     if (d->lin_tol < 0 || d->lin_tol >= 1) return bad("lin_tol must be in [0, 1)");
     if (d->nsites < 0 || (d->nsites > 0 && !d->site_xyz)) return bad("sites missing");

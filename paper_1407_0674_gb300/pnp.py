@@ -35,7 +35,7 @@ ERR_UNKNOWN_TICKET = -9
 ERR_TOO_LARGE = -10
 
 BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
-PREC = {"fp64": 0, "fp32": 1, "df64": 2, None: -1, -1: -1, 0: 0, 1: 1, 2: 2}
+PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)

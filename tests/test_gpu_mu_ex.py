@@ -2,7 +2,9 @@
 
 Bar: FP64 normwise relative error ||mu - mu_ref||_inf / ||mu_ref||_inf <= 1e-10
 per species; FP32 FFT variant <= 2e-5 (FP32 transforms of O(10) fields with
-~2^-24 rounding per butterfly level, a few 1e-7 expected, bound with margin).
+~2^-24 rounding per butterfly level, a few 1e-7 expected, bound with margin);
+the 3xTF32 tensor-core y-pass variant <= 5e-5 (its DFT products carry about
+21 significant bits, ~2^-21 per radix-16 stage, the rest is the FP32 path).
 Cases span several FFT tiles, ragged and odd padded lengths (radix 3 and 5),
 periodic and zero-extended axes, square wells, and the full 128^3 / 256^3
 workload on sampled points.
@@ -17,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
 FP32_TOL = 2e-5
+TF32SPLIT_TOL = 5e-5
 
 
 @pytest.fixture(scope="module")
@@ -80,6 +83,37 @@ def test_mu_ex_fp32_bound(pnp, case):
     assert err <= FP32_TOL, err
 
 
+@pytest.mark.parametrize("case", ["three_species_16", "film_wells_16"])
+def test_mu_ex_tf32split_bound(pnp, case):
+    """Ly = 16 here: the tensor-core y pass needs Ly = 256, so this checks that
+    the variant falls back to the FP32 y pass on other lengths."""
+    spec, rho = CASES[case]()
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="tf32split")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= TF32SPLIT_TOL
+    np.testing.assert_array_equal(mu, mu32)
+
+
+@pytest.mark.parametrize("shape", [(16, 128, 12), (24, 97, 9), (9, 250, 10)])
+def test_tensor_core_y_pass(pnp, shape):
+    """Ly padded to 256 (ny up to 250, ragged, several 8-column tiles and a
+    partial one): the tensor-core y pass against the oracle, and against the
+    FP32 path it replaces."""
+    spec, rho = mu_microbench(shape=shape)
+    spec.fft_len = (32, 256, 32)
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        mutc = P.excess_mu(rho, precision="tf32split")
+        assert P.status() == 0
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mutc, ref) <= TF32SPLIT_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+    assert normwise(mutc, mu32) <= TF32SPLIT_TOL
+    assert not np.array_equal(mutc, mu32)       # the tensor-core path ran
+
+
 def test_explicit_odd_lengths(pnp):
     """Padded lengths with radix-3 and radix-5 stages (x even, y/z odd)."""
     spec, rho = mu_microbench(shape=(12, 10, 11))
@@ -115,9 +149,11 @@ def test_register_fft_shapes(pnp, shape, lens):
         mu = P.excess_mu(rho, precision="fp64")
         mu32 = P.excess_mu(rho, precision="fp32")
         mudd = P.excess_mu(rho, precision="df64")
+        mutc = P.excess_mu(rho, precision="tf32split")
     assert normwise(mu, ref) <= FP64_TOL
     assert normwise(mu32, ref) <= FP32_TOL
     assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mutc, ref) <= TF32SPLIT_TOL
 
 
 def test_default_lengths_prefer_register_shapes(pnp):
@@ -172,11 +208,15 @@ def test_full_size_sampled(pnp):
         mu = P.excess_mu(rho, precision="fp64").reshape(3, -1)
         mu32 = P.excess_mu(rho, precision="fp32").reshape(3, -1)
         mudd = P.excess_mu(rho, precision="df64").reshape(3, -1)
+        mutc = P.excess_mu(rho, precision="tf32split").reshape(3, -1)
     for i in range(3):
         scale = np.abs(mu[i]).max()
         assert np.abs(mu[i, flat] - ref[i]).max() / scale <= FP64_TOL
         assert np.abs(mu32[i, flat] - ref[i]).max() / scale <= FP32_TOL
         assert np.abs(mudd[i, flat] - ref[i]).max() / scale <= FP64_TOL
+        assert np.abs(mutc[i, flat] - ref[i]).max() / scale <= TF32SPLIT_TOL
+    # whole field of the tensor-core variant against the FP64 path
+    assert normwise(mutc, mu) <= TF32SPLIT_TOL
     # whole-field agreement of the two FP64-accuracy paths
     assert np.abs(mudd - mu).max() / np.abs(mu).max() <= FP64_TOL
 
