@@ -316,10 +316,25 @@ int launch_ypass_tc(bool inv, const float2 *in, float2 *out, const Dims &d, int 
         for (int k = 0; k < 2; ++k) {
             auto fn = k ? tcy::k_ypass_tc<true> : tcy::k_ypass_tc<false>;
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tcy::kSmemBytes);
+            // without a carveout preference the occupancy query assumes the
+            // smallest shared-memory split that fits one CTA
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcy::k_ypass_tc<false>, tcy::kThreads,
-                                                      tcy::kSmemBytes);
-        if (per_sm < 1) per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcy::k_ypass_tc<false>, tcy::kThreads,
+                                                          tcy::kSmemBytes) != cudaSuccess)
+            per_sm = 0;
+        // the same bound from the kernel's registers and the SM's shared memory
+        cudaFuncAttributes fa;
+        int smem_sm = 0;
+        if (cudaFuncGetAttributes(&fa, tcy::k_ypass_tc<false>) == cudaSuccess &&
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            fa.numRegs > 0) {
+            const int by_regs = 65536 / (fa.numRegs * tcy::kThreads);
+            const int by_smem = smem_sm / (tcy::kSmemBytes + 1024);
+            per_sm = std::max(per_sm, std::min(by_regs, by_smem));
+        }
+        per_sm = std::min(std::max(per_sm, 1), 8);
+        cudaGetLastError();
     }
     const long ntiles = (long)((d.Wx + tcy::kCols - 1) / tcy::kCols) * d.nz * F;
     if (ntiles == 0) return PNP_OK;
