@@ -66,6 +66,18 @@ enum { PNP_BC_PERIODIC = 0, PNP_BC_DIRICHLET = 1, PNP_BC_NOFLUX = 2 };
  * y lengths use the FP32 path. */
 enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF64 = 2, PNP_PREC_TF32SPLIT = 3 };
 
+/* descriptor flags.  PNP_FLAG_AUTOTUNE: pnp_create_problem (and the server's
+ * admission of a request) times the mu_ex pipeline on the device for the
+ * candidate padded lengths of each zero-extended axis (the smallest
+ * 2^a 3^b 5^c length and the register-FFT lengths up to 60% above it) and for
+ * the CTA tiles of the register-FFT kernels, and keeps the fastest plan; an
+ * explicit fft_len entry is kept as given.  The choice is cached for the
+ * process per (grid, boundaries, species count, stencil half-width, wells,
+ * precision), so later problems of the same shape reuse it without timing.
+ * Results do not depend on the tiles; another padded length changes mu_ex only
+ * by rounding. */
+#define PNP_FLAG_AUTOTUNE 1u
+
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
  * (equal to first order, positive for large steps), or the geometric form
@@ -101,7 +113,7 @@ typedef struct {
     int precision;                 /* PNP_PREC_FP64 / FP32 / DF64 / TF32SPLIT: default for the calls below */
     double lin_tol;                /* relative residual ||r|| / ||b|| of the linear solves; 0 -> adaptive:
                                       min(1e-6, max(1e-12, 0.01 x previous Gummel residual)) */
-    unsigned flags;                /* reserved, 0 */
+    unsigned flags;                /* PNP_FLAG_* bits, 0 for none */
 } pnp_problem_desc;
 
 typedef struct {
@@ -118,6 +130,9 @@ typedef struct {
     int well_halfwidth;            /* S of the square-well stencil (h) */
     size_t device_bytes;           /* device memory held by the problem */
     int mg_levels;                 /* multigrid levels of the linear solves */
+    int tile[3];                   /* CTA tiles of the register-FFT kernels (x lines, y and z
+                                      columns per CTA) fixed by the autotuner; 0 = built-in rule */
+    double tuned_ms;               /* mu_ex time the autotuner measured for the chosen plan, 0 if untuned */
 } pnp_problem_info;
 
 typedef struct pnp_problem pnp_problem;

@@ -56,6 +56,7 @@ void destroy_problem_internal(Problem *p) {
 }
 
 int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why) {
+    if (desc && (desc->flags & PNP_FLAG_AUTOTUNE)) return autotune_create(desc, out, why);
     Problem *p = new (std::nothrow) Problem();
     if (!p) return PNP_ERR_NOMEM;
     int rc = validate_and_copy(desc, p, why);
@@ -158,6 +159,8 @@ int pnp_get_problem_info(const pnp_problem *h, pnp_problem_info *info) {
     info->well_halfwidth = p->Ssw;
     info->device_bytes = p->device_bytes;
     info->mg_levels = p->mg_levels;
+    for (int c = 0; c < 3; ++c) info->tile[c] = p->tile[c];
+    info->tuned_ms = p->tuned_ms;
     return PNP_OK;
 }
 

@@ -1,0 +1,212 @@
+// Autotuner of the mu_ex plan: the padded FFT length of every zero-extended
+// axis (Sec 3.5 fixes only a lower bound, n + stencil reach) and the CTA
+// tiles of the register-FFT kernels are chosen by timing the whole pipeline
+// on the device, for the precision the problem computes in.
+//
+// Lengths: every combination of the per-axis candidates (the smallest
+// 2^a 3^b 5^c length, register-FFT lengths up to 60 % above it, and the
+// planner's own choice) builds its own spectra and is timed on a uniform bulk
+// density; the fastest problem is kept.  Tiles: the x kernels' lines per CTA,
+// the y kernels' columns per CTA and the z kernels' column pairs per CTA are
+// independent, so one run per candidate index times all three groups at once
+// through the per-stage timer.  The result is cached per shape for the
+// process: batched and served solves of one grid size pay for tuning once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mu_ex_core.cuh"
+
+namespace pnp {
+namespace {
+
+struct Tuned {
+    int L[3];
+    int tile[3];
+    double ms;
+};
+using Key = std::array<int, 13>;
+
+std::mutex g_mu;
+std::map<Key, Tuned> g_cache;
+
+Key key_of(const Problem *p, const pnp_problem_desc *d) {
+    return Key{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->bc[2], p->s, p->S, p->Ssw, p->precision,
+               d->fft_len[0], d->fft_len[1], d->fft_len[2]};
+}
+
+// mean time of one mu_ex over `reps` runs after a warm-up; per-stage means
+// in stage_ms.  Negative when the pipeline fails.
+double time_plan(Problem *p, const double *d_rho, double *d_mu, int reps, double *stage_ms) {
+    const int prec = p->precision;
+    if (mu_ex_enqueue(p, prec, d_rho, d_mu, p->stream) != PNP_OK) return -1.0;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return -1.0;
+    p->timer.collect(nullptr, nullptr, 0);
+    p->timer.enabled = true;
+    int rc = PNP_OK;
+    for (int r = 0; r < reps && rc == PNP_OK; ++r) rc = mu_ex_enqueue(p, prec, d_rho, d_mu, p->stream);
+    p->timer.enabled = false;
+    double ms[kNumStages];
+    int n[kNumStages];
+    p->timer.collect(ms, n, kNumStages);
+    int flag = 0;
+    cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess || rc != PNP_OK) return -1.0;
+    if (flag) {
+        cudaMemsetAsync(p->d_flag, 0, sizeof(int), p->stream);
+        cudaStreamSynchronize(p->stream);
+        return -1.0;
+    }
+    double tot = 0;
+    for (int k = 0; k < kNumStages; ++k) {
+        stage_ms[k] = ms[k] / reps;
+        tot += stage_ms[k];
+    }
+    return tot;
+}
+
+// lanes per line of the register FFT of length L (0: shared-memory FFT)
+int reg_lanes(int L) {
+    int G = 0;
+    with_shape(L, [&](auto a, auto b) { G = Shape<decltype(a)::value, decltype(b)::value>::G; });
+    return G;
+}
+
+void tile_candidates(int G, int axis, std::vector<int> *out) {
+    out->assign(1, 0);     // the built-in rule
+    if (!G) return;
+    if (axis == 0) {
+        for (int thr : {64, 128, 256, 512})
+            if (thr / G >= 1) out->push_back(thr / G);
+    } else if (axis == 1) {
+        for (int tx : {2, 4, 8, 16, 32})
+            if (tx * G <= 1024) out->push_back(tx);
+    } else {
+        for (int tx : {1, 2, 4, 8, 16})
+            if (2 * tx * G <= 1024) out->push_back(tx);
+    }
+    std::sort(out->begin() + 1, out->end());
+    out->erase(std::unique(out->begin() + 1, out->end()), out->end());
+}
+
+}  // namespace
+
+int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *why) {
+    pnp_problem_desc d = *desc;
+    d.flags &= ~PNP_FLAG_AUTOTUNE;
+    Problem *best = nullptr;
+    int rc = create_problem_internal(&d, &best, why);
+    if (rc) return rc;
+    const Key key = key_of(best, &d);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            const Tuned t = it->second;
+            if (!std::equal(t.L, t.L + 3, best->L)) {
+                pnp_problem_desc d2 = d;
+                for (int c = 0; c < 3; ++c) d2.fft_len[c] = t.L[c];
+                Problem *q = nullptr;
+                if (create_problem_internal(&d2, &q, nullptr) == PNP_OK) {
+                    destroy_problem_internal(best);
+                    best = q;
+                }
+            }
+            if (std::equal(t.L, t.L + 3, best->L)) {
+                std::copy(t.tile, t.tile + 3, best->tile);
+                best->tuned_ms = t.ms;
+            }
+            *out = best;
+            return PNP_OK;
+        }
+    }
+
+    // a uniform bulk density of every species (the pipeline's cost does not
+    // depend on the values)
+    const size_t N = best->npts(), nf = (size_t)best->s * N;
+    std::vector<double> h(nf);
+    for (int i = 0; i < best->s; ++i) std::fill(h.begin() + i * N, h.begin() + (i + 1) * N, best->rho_b[i]);
+    double *d_rho = nullptr, *d_mu = nullptr;
+    if (cudaMalloc(&d_rho, nf * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d_mu, nf * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(d_rho, h.data(), nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d_rho);
+        cudaFree(d_mu);
+        cudaGetLastError();
+        *out = best;          // untuned but valid
+        return PNP_OK;
+    }
+    const int reps = 2;
+    double stage[kNumStages];
+    double t_best = time_plan(best, d_rho, d_mu, reps, stage);
+    if (t_best < 0) t_best = 1e30;
+
+    // padded lengths
+    std::vector<int> cand[3];
+    for (int c = 0; c < 3; ++c) {
+        if (d.fft_len[c] > 0) cand[c].assign(1, best->L[c]);
+        else length_candidates(best, c, &cand[c]);
+    }
+    for (int a : cand[0])
+        for (int b : cand[1])
+            for (int e : cand[2]) {
+                if (a == best->L[0] && b == best->L[1] && e == best->L[2]) continue;
+                pnp_problem_desc d2 = d;
+                d2.fft_len[0] = a;
+                d2.fft_len[1] = b;
+                d2.fft_len[2] = e;
+                Problem *q = nullptr;
+                if (create_problem_internal(&d2, &q, nullptr) != PNP_OK) continue;
+                const double t = time_plan(q, d_rho, d_mu, reps, stage);
+                if (t >= 0 && t < t_best) {
+                    destroy_problem_internal(best);
+                    best = q;
+                    t_best = t;
+                } else {
+                    destroy_problem_internal(q);
+                }
+            }
+
+    // tiles: x stages {0, 4, 8}, y stages {1, 3, 5, 7}, z stages {2, 6}
+    static const std::vector<int> groups[3] = {{0, 4, 8}, {1, 3, 5, 7}, {2, 6}};
+    std::vector<int> tc[3];
+    for (int c = 0; c < 3; ++c) tile_candidates(reg_lanes(best->L[c]), c, &tc[c]);
+    const size_t rounds = std::max({tc[0].size(), tc[1].size(), tc[2].size()});
+    std::vector<double> gt[3];
+    for (int c = 0; c < 3; ++c) gt[c].assign(tc[c].size(), 1e30);
+    for (size_t r = 0; r < rounds; ++r) {
+        for (int c = 0; c < 3; ++c) best->tile[c] = tc[c][r % tc[c].size()];
+        if (time_plan(best, d_rho, d_mu, reps, stage) < 0) continue;
+        for (int c = 0; c < 3; ++c) {
+            double g = 0;
+            for (int k : groups[c]) g += stage[k];
+            double &slot = gt[c][r % tc[c].size()];
+            slot = std::min(slot, g);
+        }
+    }
+    for (int c = 0; c < 3; ++c)
+        best->tile[c] = tc[c][std::min_element(gt[c].begin(), gt[c].end()) - gt[c].begin()];
+    const double t_final = time_plan(best, d_rho, d_mu, reps, stage);
+    best->tuned_ms = t_final > 0 ? t_final : 0.0;
+    cudaFree(d_rho);
+    cudaFree(d_mu);
+
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        Tuned t;
+        std::copy(best->L, best->L + 3, t.L);
+        std::copy(best->tile, best->tile + 3, t.tile);
+        t.ms = best->tuned_ms;
+        g_cache[key] = t;
+    }
+    *out = best;
+    return PNP_OK;
+}
+
+}  // namespace pnp

@@ -579,6 +579,17 @@ template <auto K> static void ensure_smem() {
     (void)done;
 }
 
+// dynamic shared memory the register kernels may request (ensure_smem)
+constexpr long kSmemCap = 200 * 1024;
+
+// lines per CTA of the x kernels: the tuned tile if set, else 256 threads;
+// at most 1024 threads, the shared-memory cap and the line pairs there are
+static int x_lines(const Problem *p, int G, long ex_bytes, int npairs) {
+    int P = p->tile[0] > 0 ? p->tile[0] : 256 / G;
+    P = std::min<long>(P, std::min<long>(1024 / G, kSmemCap / ex_bytes));
+    return std::max(1, std::min(P, npairs));
+}
+
 // split derivative stage (see stage 5 of run_pipeline)
 constexpr bool kSplitDerivatives = true;
 
@@ -609,7 +620,7 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     tm.begin(0, st);
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
-            const int P = std::max(1, std::min(256 / G, d.npairs));
+            const int P = x_lines(p, G, Shape<N1, N2>::EX * (long)cs, d.npairs);
             ensure_smem<k_xfwd_r<T, N1, N2>>();
             dim3 g((d.npairs + P - 1) / P, d.nz, s);
             k_xfwd_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(d_rho, N, A, d, twx, P);
@@ -633,7 +644,10 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
         }
         if (!with_shape(d.Ly, [&](auto a, auto b) {
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
-                const int TX = pow2_le(std::min<long>(256 / G, 16));
+                int TX = pow2_le(std::min<long>(256 / G, 16));
+                if (p->tile[1] > 0)
+                    TX = std::max(1, std::min<int>(p->tile[1],
+                                                   (int)std::min<long>(1024 / G, kSmemCap / (Shape<N1, N2>::EX * (long)cs))));
                 dim3 g((d.Wx + TX - 1) / TX, d.nz, F);
                 const size_t sm = (size_t)TX * Shape<N1, N2>::EX * cs;
                 if (inv) {
@@ -664,7 +678,10 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
                 // paired columns (ky, Ly - ky): 2 TX columns per CTA
                 const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
-                const int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
+                int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
+                if (p->tile[2] > 0)
+                    TX = std::max(1, std::min<int>(p->tile[2], (int)std::min<long>(512 / G, (kSmemCap - (long)G * G * cs) /
+                                                                                         (2 * per_col))));
                 dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
                 const size_t sm = 2 * TX * per_col + (size_t)G * G * cs;   // + twiddle table
                 if (back) {
@@ -697,7 +714,7 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
             if (kSplitDerivatives) {
-                const int P = std::max(1, std::min(256 / G, d.npairs));
+                const int P = x_lines(p, G, Shape<N1, N2>::EX * (long)cs, d.npairs);
                 const size_t sm = P * Shape<N1, N2>::EX * cs;
                 dim3 g((d.npairs + P - 1) / P, d.nz, kNumWeighted);
                 ensure_smem<k_xinv_raw_r<T, N1, N2, V>>();
@@ -729,7 +746,7 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     const double *U = p->has_wells ? p->d_U : nullptr;
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
-            const int P = std::max(1, std::min(256 / G, d.npairs));
+            const int P = x_lines(p, G, Shape<N1, N2>::EX * (long)cs, d.npairs);
             ensure_smem<k_xinv_r<T, N1, N2>>();
             dim3 g((d.npairs + P - 1) / P, d.nz, s);
             k_xinv_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(A, d_mu, N, d, twx, U, sc, P);

@@ -369,6 +369,30 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     return plan_lengths(p, d->fft_len);
 }
 
+// register-FFT lengths of the mu_ex kernels
+static const int kRegLengths[] = {16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 256};
+
+void length_candidates(const Problem *p, int c, std::vector<int> *out) {
+    out->clear();
+    const int n[3] = {p->nx, p->ny, p->nz};
+    if (p->bc[c] == PNP_BC_PERIODIC) {
+        out->push_back(n[c]);
+        return;
+    }
+    const bool even = (c == 0);
+    const int minL = n[c] + std::max(p->S, p->Ssw);
+    const int L0 = next_smooth(minL, even);
+    out->push_back(L0);
+    int extra = 0;
+    for (int f : kRegLengths)
+        if (f > L0 && f <= L0 + (6 * L0) / 10 && extra < 2) {
+            out->push_back(f);
+            ++extra;
+        }
+    if (std::find(out->begin(), out->end(), p->L[c]) == out->end()) out->push_back(p->L[c]);
+    std::sort(out->begin(), out->end());
+}
+
 int plan_lengths(Problem *p, const int fft_len[3]) {
     double Rmax = 0;
     for (double r : p->R) Rmax = std::max(Rmax, r);
@@ -392,7 +416,7 @@ int plan_lengths(Problem *p, const int fft_len[3]) {
                 // smallest legal length, or a register-FFT length when one is
                 // within 30% of it
                 L = next_smooth(minL, even);
-                for (int f : {16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 256})
+                for (int f : kRegLengths)
                     if (f >= minL && f <= L + (3 * L) / 10 && f >= L) {
                         L = f;
                         break;

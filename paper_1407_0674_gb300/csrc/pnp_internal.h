@@ -98,6 +98,8 @@ struct Problem {
     int deferred = 0;                 // host-side deferred status
     StageTimer timer;
     int mg_levels = 0;
+    int tile[3] = {0, 0, 0};          // register-FFT CTA tiles (x lines, y columns, z columns); 0: rule
+    double tuned_ms = 0;              // mu_ex time measured by the autotuner
 
     size_t npts() const { return (size_t)nx * ny * nz; }
 };
@@ -105,12 +107,16 @@ struct Problem {
 // plan.cpp
 int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why);
 int plan_lengths(Problem *p, const int fft_len[3]);
+void length_candidates(const Problem *p, int axis, std::vector<int> *out);
 void gauss_legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w);
 void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil out[kNumKernels]);
 void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
 void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
 double bjerrum_length_h(double T, double eps_r, double h_nm);
 void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu);
+
+// autotune.cu: time candidate padded lengths and tiles, keep the fastest
+int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *why);
 
 // mu_ex.cu
 int mu_ex_setup(Problem *p);                 // workspace, spectra, mu_sh

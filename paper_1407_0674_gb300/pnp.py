@@ -35,6 +35,7 @@ ERR_UNKNOWN_TICKET = -9
 ERR_TOO_LARGE = -10
 
 BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
+FLAG_AUTOTUNE = 1
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -74,7 +75,8 @@ class Stats(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("fft_len", ctypes.c_int * 3), ("stencil_halfwidth", ctypes.c_int),
-                ("well_halfwidth", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("mg_levels", ctypes.c_int)]
+                ("well_halfwidth", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("mg_levels", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("tuned_ms", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -196,6 +198,7 @@ class DescHolder:
             d.fft_len[c] = int(spec.fft_len[c])
         d.precision = PREC[precision]
         d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
+        d.flags = FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0
         self.desc = d
 
 
@@ -241,7 +244,8 @@ class Problem:
         i = Info()
         _check(lib().pnp_get_problem_info(self.h, ctypes.byref(i)), "pnp_get_problem_info")
         return {"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
-                "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "mg_levels": i.mg_levels}
+                "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "mg_levels": i.mg_levels,
+                "tile": tuple(i.tile), "tuned_ms": i.tuned_ms}
 
     def excess_mu(self, rho, precision=None):
         """pnp_excess_mu on host arrays; returns mu_ex [s, nz, ny, nx]."""

@@ -58,6 +58,7 @@ class ProblemSpec:
     sw_half: bool = True                     # keep the 1/2 of the mean-field mu_sh
     fft_len: Tuple[int, int, int] = (0, 0, 0)  # padded FFT lengths for the GPU plan (0 = auto)
     lin_tol: float = 0.0                     # linear-solve relative residual (0 = library default)
+    autotune: bool = False                   # GPU plan: time candidate lengths and tiles, keep the fastest
 
     @property
     def s(self) -> int:
