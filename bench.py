@@ -19,6 +19,7 @@ Multi-GPU: the workload does not shard, so N ranks run N independent replicas
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -47,9 +48,15 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=24, help="edge of the reference-arm sample box")
     ap.add_argument("--n", type=int, default=N_EDGE, help="grid edge (profiling runs use smaller cases)")
     ap.add_argument("--pad", type=int, default=PAD, help="padded FFT length")
+    ap.add_argument("--bias-points", type=int, default=11, help="film3: points of the 0..1 kT/e bias sweep")
+    ap.add_argument("--max-iter3", type=int, default=2000, help="film3: Gummel iteration cap per bias point")
+    ap.add_argument("--solve-prec", default="df64", choices=["fp64", "df64", "fp32", "tf32split"],
+                    help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
+    ap.add_argument("--autotune", type=int, default=1, help="autotune the batched / served problems' plans")
     ap.add_argument("--variants", default="fp64,df64,fp32,tf32split", help="precisions to time, headline first")
-    ap.add_argument("--workload", default="mu_ex", choices=["mu_ex", "film", "batch", "serve"],
-                    help="mu_ex (headline), film (one 32^3 Gummel solve), batch (64 solves), serve (arrivals)")
+    ap.add_argument("--workload", default="mu_ex", choices=["mu_ex", "film", "film3", "batch", "serve"],
+                    help="mu_ex (headline), film (one 32^3 Gummel solve), film3 (128x128x256 bias sweep), "
+                         "batch (64 solves), serve (arrivals)")
     ap.add_argument("--batch", type=int, default=64, help="solves in the batch workload")
     ap.add_argument("--seq", type=int, default=8, help="solves timed one at a time as the sequential baseline")
     ap.add_argument("--requests", type=int, default=40, help="served requests")
@@ -436,7 +443,7 @@ def run_solves(args, world, rank, local):
     import torch
     from paper_1407_0674_gb300 import build as lb
     from paper_1407_0674_gb300 import pnp
-    from workloads import batch_specs, film_gummel, serving_arrivals, serving_spec
+    from workloads import batch_specs, film3, film_gummel, serving_arrivals, serving_spec
 
     torch.cuda.set_device(local)
     lb.build()
@@ -457,8 +464,49 @@ def run_solves(args, world, rank, local):
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
+    if args.workload == "film3":
+        # bias sweep on the 128x128x256 film, each point warm-started from the
+        # previous one: plain FP64 against the mixed-precision mu_ex
+        biases = [k / max(1, args.bias_points - 1) for k in range(args.bias_points)]
+        runs = {}
+        for prec in ("fp64", args.solve_prec):
+            phi0 = rho0 = None
+            solve_s = wall_s = 0.0
+            rec = []
+            for b in biases:
+                spec = film3(bias=b, max_iter=args.max_iter3)
+                t0 = time.perf_counter()
+                with pnp.Problem(spec, precision=prec) as P:
+                    t1 = time.perf_counter()
+                    phi, rho, st = P.gummel_solve(phi0, rho0, raise_on_error=False)
+                    solve_s += time.perf_counter() - t1
+                wall_s += time.perf_counter() - t0
+                phi0, rho0 = phi, rho
+                rec.append((b, st, rho))
+            runs[prec] = (solve_s, wall_s, rec)
+        s64, w64, r64 = runs["fp64"]
+        sm, wm, rm = runs[args.solve_prec]
+        errs = [max(float(np.abs(a[2][i] - c[2][i]).max() / np.abs(c[2][i]).max()) for i in range(3))
+                for a, c in zip(rm, r64)]
+        n = len(biases)
+        line = {"metric": "PNP solves/s", "value": world * n / wm, "unit": "solves/s", "n_gpus": world,
+                "steps": n, "warmup": 0, "ms_per_step": wm / n * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
+                "config": {"workload": f"film 128x128x256, 3 mobile species (R 2/2/1 h), wells 3 kT on 4096 "
+                                       f"sites, bias sweep 0..1 kT/e in {n} points, warm-started, residual 1e-8",
+                           "mu_ex_precision": args.solve_prec},
+                "solve_seconds": sm, "fp64_plain": {"solves_per_s": n / w64, "wall_s": w64, "solve_seconds": s64,
+                                                    "iterations": [r[1]["iterations"] for r in r64],
+                                                    "status": [r[1]["status"] for r in r64]},
+                "speedup_vs_fp64": w64 / wm,
+                "iterations": [r[1]["iterations"] for r in rm], "status": [r[1]["status"] for r in rm],
+                "max_rel_err_rho_vs_fp64": max(errs)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload == "batch":
         specs = batch_specs(args.batch)
+        served = [dataclasses.replace(s, autotune=args.autotune) for s in specs]
         # sequential baseline: the plain FP64 form, one solve at a time
         seq = []
         seq_res = {}
@@ -471,8 +519,8 @@ def run_solves(args, world, rank, local):
         srv = pnp.Server(max_slots=64)
         t0 = time.perf_counter()
         tickets = []
-        for s in specs:
-            rc, t = srv.submit(s)
+        for s in served:
+            rc, t = srv.submit(s, precision=args.solve_prec)
             if rc != 0:
                 raise RuntimeError(f"submit {rc}")
             tickets.append(t)
@@ -492,10 +540,11 @@ def run_solves(args, world, rank, local):
         lat = [v[3] for v in done.values()]
         line = {"metric": "PNP solves/s", "value": world * len(specs) / wall, "unit": "solves/s", "n_gpus": world,
                 "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
                 "config": {"workload": f"{len(specs)} independent Gummel solves, grids from "
                                        "{32^3,48^3,64^3,80x80x96,96^3}, T U(250,400) K, wells 0.3 eV/kT, packing "
-                                       "U(0.1,0.35), served concurrently (one CUDA graph per solve)"},
+                                       "U(0.1,0.35), served concurrently (one CUDA graph per solve)",
+                           "mu_ex_precision": args.solve_prec, "autotune": bool(args.autotune)},
                 "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq),
                                     "mean_s": float(np.mean(seq))},
                 "speedup_vs_sequential": (len(specs) / wall) / (len(seq) / sum(seq)),
@@ -508,6 +557,7 @@ def run_solves(args, world, rank, local):
     # serve
     arr = serving_arrivals(args.requests, rate=args.rate, hi=args.max_edge)
     specs = [serving_spec(n, bias, T) for (_, n, bias, T) in arr]
+    served = [dataclasses.replace(s, autotune=args.autotune) for s in specs]
     seq = []
     for s in specs[:args.seq]:
         with pnp.Problem(s) as P:
@@ -523,7 +573,7 @@ def run_solves(args, world, rank, local):
     while nxt < len(arr) or pending:
         now = time.perf_counter() - t0
         while nxt < len(arr) and arr[nxt][0] <= now:
-            rc, t = srv.submit(specs[nxt])
+            rc, t = srv.submit(served[nxt], precision=args.solve_prec)
             if rc == 0:
                 pending[t] = arr[nxt][0]
             else:
@@ -539,9 +589,10 @@ def run_solves(args, world, rank, local):
     srv.close()
     line = {"metric": "PNP solves/s", "value": world * len(lat) / wall, "unit": "solves/s", "n_gpus": world,
             "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
             "config": {"workload": f"{len(arr)} served Gummel solves, Poisson arrivals {args.rate}/s, cubic grids "
-                                   f"log-uniform 32..{args.max_edge}, bias U(0,1), T U(250,400) K, budget 150 GB"},
+                                   f"log-uniform 32..{args.max_edge}, bias U(0,1), T U(250,400) K, budget 150 GB",
+                       "mu_ex_precision": args.solve_prec, "autotune": bool(args.autotune)},
             "latency_p50_ms": _pct(lat, 50) * 1e3, "latency_p99_ms": _pct(lat, 99) * 1e3,
             "completed_ok": sum(1 for s in statuses if s == 0), "statuses": sorted(set(statuses)),
             "sequential_fp64": {"solves": len(seq), "mean_s": float(np.mean(seq)) if seq else None}}

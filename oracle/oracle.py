@@ -100,6 +100,9 @@ def _declare(L):
     L.oracle_np_flux.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
     L.oracle_gummel.restype = ctypes.c_int
     L.oracle_gummel.argtypes = [P, _dp, _dp, _dp, _dp, _ip, _dp, ctypes.POINTER(ctypes.c_long)]
+    L.oracle_equilibrium.restype = ctypes.c_int
+    L.oracle_equilibrium.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _ip,
+                                     ctypes.POINTER(ctypes.c_double)]
     L.oracle_num_threads.restype = ctypes.c_int
 
 
@@ -310,6 +313,22 @@ def gummel(spec, phi0=None, rho0=None, lin_tol=1e-13):
                              ctypes.byref(it), _ptr(hist), ctypes.byref(lin))
     return {"phi": phi, "rho": rho, "status": st, "iters": it.value, "hist": hist[:it.value],
             "lin_iters": lin.value, "lB": P.lB}
+
+
+def equilibrium(spec, lam=None, tol=1e-10, max_iter=1000, lin_tol=1e-13):
+    """Equilibrium cDFT initial guess (Sec 3.2): Boltzmann densities about
+    the reservoirs with the Poisson-Boltzmann potential.  lam defaults to the
+    problem's lambda_rho.  Returns a dict with phi, rho, status (0 converged,
+    1 not converged, 2 packing/overflow), iters, residual."""
+    P = Problem(spec, lin_tol=lin_tol)
+    phi = np.zeros(P.shape)
+    rho = np.zeros((P.s,) + P.shape)
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    lam = spec.lambda_rho if lam is None else lam
+    st = lib().oracle_equilibrium(P.ref, ctypes.c_double(lam), ctypes.c_double(tol), ctypes.c_int(max_iter),
+                                  _ptr(phi), _ptr(rho), ctypes.byref(it), ctypes.byref(res))
+    return {"phi": phi, "rho": rho, "status": st, "iters": it.value, "residual": res.value, "lB": P.lB}
 
 
 def num_threads() -> int:

@@ -740,6 +740,40 @@ static int pcg(const fdop_t *A, const double *b, double *x, double tol, int maxi
     return it;
 }
 
+/* Jacobi-PCG for (A + diag(shift)) x = b, x = initial guess on entry. */
+static int pcg_shifted(const fdop_t *A, const double *shift, const double *b, double *x, double tol, int maxit)
+{
+    long N = (long)A->nx * A->ny * A->nz;
+    double *r = malloc(sizeof(double) * N), *z = malloc(sizeof(double) * N);
+    double *pd = malloc(sizeof(double) * N), *Ap = malloc(sizeof(double) * N);
+    double *dg = malloc(sizeof(double) * N);
+    fd_diag(A, dg);
+    for (long k = 0; k < N; ++k) dg[k] += shift[k];
+    fd_apply(A, x, Ap);
+    for (long k = 0; k < N; ++k) r[k] = b[k] - Ap[k] - shift[k] * x[k];
+    double bn = sqrt(dot(N, b, b));
+    if (bn == 0.0) bn = 1.0;
+    for (long k = 0; k < N; ++k) { z[k] = r[k] / dg[k]; pd[k] = z[k]; }
+    double rz = dot(N, r, z);
+    int it = 0;
+    double rn = sqrt(dot(N, r, r));
+    while (rn > tol * bn && it < maxit) {
+        fd_apply(A, pd, Ap);
+        for (long k = 0; k < N; ++k) Ap[k] += shift[k] * pd[k];
+        double alpha = rz / dot(N, pd, Ap);
+        for (long k = 0; k < N; ++k) { x[k] += alpha * pd[k]; r[k] -= alpha * Ap[k]; }
+        for (long k = 0; k < N; ++k) z[k] = r[k] / dg[k];
+        double rz2 = dot(N, r, z);
+        double beta = rz2 / rz;
+        rz = rz2;
+        for (long k = 0; k < N; ++k) pd[k] = z[k] + beta * pd[k];
+        rn = sqrt(dot(N, r, r));
+        ++it;
+    }
+    free(r); free(z); free(pd); free(Ap); free(dg);
+    return it;
+}
+
 static fdop_t fd_alloc(const oracle_problem *p)
 {
     fdop_t A;
@@ -925,6 +959,101 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
     if (iters) *iters = n > p->max_iter ? p->max_iter : n;
     if (lin_iters) *lin_iters = lin;
     free(mu); free(phis); free(rb); free(mub); free(rho_new);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Equilibrium cDFT initial guess (Sec 3.2, choice of initial guess): the
+ * static equilibrium of the mobile species in the potential of the
+ * electrodes, which then starts the Gummel iteration.  At equilibrium every
+ * species follows the Boltzmann law about its reservoir,
+ *     rho_i = rho_b,i exp(mu_b,i - mu_ex,i[rho] - q_i phi),
+ * and phi solves the Poisson equation with these densities (Poisson-Boltzmann
+ * with the cDFT excess term).  One iteration, in this order:
+ *   mu_ex from rho;  c_i = rho_b,i exp(mu_b,i - mu_ex,i);
+ *   one Newton step of the Poisson-Boltzmann equation in phi at fixed c:
+ *     (A + diag 4 pi lB sum_i q_i^2 c_i e^{-q_i phi}) dphi = b(phi) - A phi,
+ *     b(phi) = 4 pi lB (rho_f + sum_i q_i c_i e^{-q_i phi}) + Dirichlet terms,
+ *     dphi clamped to +-1 at each point, phi += dphi;
+ *   rho*_i = c_i e^{-q_i phi};  rho_i <- rho_i exp(step), step = lam ln(rho*_i / rho_i)
+ *     limited to +-0.2 (the step-limited geometric relaxation);
+ *   stop when max(|dphi|_inf, max_i |drho_i|_inf / rho_b,i) < tol.
+ * Starts from phi linear in z between the Dirichlet values and rho = rho_b.
+ * Returns 0 converged, 1 not converged, 2 packing or overflow.  The linear
+ * solve uses the oracle's Jacobi-PCG at the problem's lin_tol.          */
+int oracle_equilibrium(const oracle_problem *p, double lam, double tol, int max_iter,
+                       double *phi, double *rho, int *iters, double *res)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    int s = p->s;
+    double *mu = malloc(sizeof(double) * s * N), *c = malloc(sizeof(double) * s * N);
+    double *mub = malloc(sizeof(double) * s);
+    double *b = malloc(sizeof(double) * N), *Aphi = malloc(sizeof(double) * N), *dphi = malloc(sizeof(double) * N);
+    fdop_t A = fd_alloc(p);
+    poisson_operator(p, &A);
+    oracle_bulk_mu(s, p->R, p->rho_b, mub);
+    for (long k = 0; k < N; ++k) {
+        int z = (int)(k / plane);
+        phi[k] = p->phi_lo + (p->phi_hi - p->phi_lo) * (z + 1.0) / (p->nz + 1.0);
+    }
+    for (int i = 0; i < s; ++i)
+        for (long k = 0; k < N; ++k) rho[i * N + k] = p->rho_b[i];
+    int status = 1, n;
+    double rr = 0.0;
+    for (n = 1; n <= max_iter; ++n) {
+        if (oracle_excess_mu(p, rho, mu) > 0) { status = 2; break; }
+        for (int i = 0; i < s; ++i)
+            for (long k = 0; k < N; ++k) c[i * N + k] = p->rho_b[i] * exp(mub[i] - mu[i * N + k]);
+        /* Newton step: Jacobian = Poisson operator + diagonal screening term */
+        double *shift = malloc(sizeof(double) * N);
+        for (long k = 0; k < N; ++k) {
+            double ch = p->rho_f ? p->rho_f[k] : 0.0, sc = 0.0;
+            for (int i = 0; i < s; ++i) {
+                double r = c[i * N + k] * exp(-p->q[i] * phi[k]);
+                ch += p->q[i] * r;
+                sc += (double)p->q[i] * p->q[i] * r;
+            }
+            b[k] = 4.0 * M_PI * p->lB * ch;
+            shift[k] = 4.0 * M_PI * p->lB * sc;
+        }
+        for (long k = 0; k < plane; ++k) {
+            b[k] += A.czlo[k] * p->phi_lo;
+            b[N - plane + k] += A.cz[N - plane + k] * p->phi_hi;
+        }
+        fd_apply(&A, phi, Aphi);
+        for (long k = 0; k < N; ++k) { b[k] -= Aphi[k]; dphi[k] = 0.0; }
+        int bad = 0;
+        for (long k = 0; k < N; ++k) if (!isfinite(b[k]) || !isfinite(shift[k])) bad = 1;
+        if (bad) { free(shift); status = 2; break; }
+        pcg_shifted(&A, shift, b, dphi, p->lin_tol, p->lin_max_iter);
+        free(shift);
+        double dmax = 0.0;
+        for (long k = 0; k < N; ++k) {
+            double d = dphi[k] > 1.0 ? 1.0 : (dphi[k] < -1.0 ? -1.0 : dphi[k]);
+            phi[k] += d;
+            if (fabs(d) > dmax) dmax = fabs(d);
+        }
+        rr = dmax;
+        for (int i = 0; i < s; ++i) {
+            double drho = 0.0;
+            for (long k = 0; k < N; ++k) {
+                double rs = c[i * N + k] * exp(-p->q[i] * phi[k]);
+                double step = lam * log(rs / rho[i * N + k]);
+                step = step > 0.2 ? 0.2 : (step < -0.2 ? -0.2 : step);
+                double v = rho[i * N + k] * exp(step);
+                if (!isfinite(v) || !(v > 0.0)) bad = 1;
+                double d = fabs(v - rho[i * N + k]) / p->rho_b[i];
+                if (d > drho) drho = d;
+                rho[i * N + k] = v;
+            }
+            if (drho > rr) rr = drho;
+        }
+        if (bad) { status = 2; break; }
+        if (rr < tol) { status = 0; break; }
+    }
+    if (iters) *iters = n > max_iter ? max_iter : n;
+    if (res) *res = rr;
+    free(mu); free(c); free(mub); free(b); free(Aphi); free(dphi); free(A.cx);
     return status;
 }
 

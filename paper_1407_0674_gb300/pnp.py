@@ -312,8 +312,8 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, spec, phi0=None, rho0=None):
-        dh = DescHolder(spec)
+    def submit(self, spec, phi0=None, rho0=None, precision="fp64"):
+        dh = DescHolder(spec, precision)
         t = ctypes.c_uint64()
         p0 = None if phi0 is None else _f64(phi0)
         r0 = None if rho0 is None else _f64(rho0)
