@@ -78,6 +78,20 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * by rounding. */
 #define PNP_FLAG_AUTOTUNE 1u
 
+/* PNP_FLAG_EQUILIBRIUM_INIT: pnp_gummel_solve (without a warm start) first
+ * solves the static equilibrium of the mobile species in the electrodes'
+ * potential and starts the Gummel iteration from it (Sec 3.2, choice of
+ * initial guess).  Equilibrium: rho_i = rho_b,i exp(mu_b,i - mu_ex,i - q_i phi)
+ * with phi from the Poisson equation of these densities.  Each iteration
+ * takes mu_ex from rho, one Newton step of that Poisson-Boltzmann equation in
+ * phi (the Poisson operator plus the screening term 4 pi lB sum q^2 rho on
+ * the diagonal, solved by the same multigrid-preconditioned CG; the step is
+ * clamped to +-1 kT/e per point), and moves rho toward the Boltzmann
+ * densities by the step-limited geometric relaxation with lambda_rho; it ends
+ * when max(|dphi|, max_i |drho_i| / rho_b,i) < eq_tol or at eq_max_iter.
+ * With this flag max_iter may be 0: the call then returns the equilibrium. */
+#define PNP_FLAG_EQUILIBRIUM_INIT 2u
+
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
  * (equal to first order, positive for large steps), or the geometric form
@@ -114,6 +128,9 @@ typedef struct {
     double lin_tol;                /* relative residual ||r|| / ||b|| of the linear solves; 0 -> adaptive:
                                       min(1e-6, max(1e-12, 0.01 x previous Gummel residual)) */
     unsigned flags;                /* PNP_FLAG_* bits, 0 for none */
+    double eq_tol;                 /* PNP_FLAG_EQUILIBRIUM_INIT: residual that ends the equilibrium stage
+                                      (0 -> 1e-6) */
+    int eq_max_iter;               /* and its iteration cap (0 -> 1000) */
 } pnp_problem_desc;
 
 typedef struct {
@@ -122,6 +139,8 @@ typedef struct {
     double residual;               /* last Gummel residual */
     long long linear_iterations;   /* PCG iterations summed over all solves */
     double seconds;                /* wall time of the call */
+    int init_iterations;           /* iterations of the equilibrium initial guess (0 if not run) */
+    double init_residual;          /* its last residual */
 } pnp_stats;
 
 typedef struct {

@@ -73,6 +73,7 @@ class _Problem(ctypes.Structure):
         ("lin_tol", ctypes.c_double),
         ("lin_max_iter", ctypes.c_int),
         ("rho_mix", ctypes.c_int),
+        ("screened", ctypes.c_int),
     ]
 
 
@@ -159,6 +160,7 @@ class Problem:
         st.lin_tol = lin_tol
         st.lin_max_iter = lin_max_iter
         st.rho_mix = int(getattr(spec, "rho_mix", 0))
+        st.screened = 1 if getattr(spec, "screened_poisson", False) else 0
         self.st = st
 
     @property

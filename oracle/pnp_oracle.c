@@ -217,6 +217,8 @@ typedef struct {
     int lin_max_iter;
     int rho_mix;               /* 0: linear relaxation (Sec 3.2), 1: geometric,
                                   2: geometric with |step in ln rho| <= 0.2 */
+    int screened;              /* Gummel Poisson step: 0 linear solve, 1 one Newton step
+                                  with the densities' Boltzmann dependence on phi */
 } oracle_problem;
 
 static grid_t cdft_grid(const oracle_problem *p)
@@ -820,6 +822,43 @@ int oracle_poisson(const oracle_problem *p, const double *rho, double *phi, doub
     return it;
 }
 
+/* The Poisson step of the Gummel iteration with the densities' dependence
+ * on phi kept to first order: with the Slotboom variables and mu_ex frozen,
+ * rho_i(phi) = rho_i exp(-q_i (phi - phi_old)), and one Newton step of the
+ * Poisson equation from phi_old is
+ *   (A + diag 4 pi lB sum_i q_i^2 rho_i) dphi = b(rho) - A phi_old,
+ *   phi* = phi_old + dphi.
+ * Its fixed point is the Poisson solution (dphi = 0 there); unlike the plain
+ * solve it carries the screening response, so the relaxed iteration stays
+ * stable when the domain is many Debye lengths long.  phis gets phi*.     */
+static int poisson_newton_step(const oracle_problem *p, const double *rho, const double *phi, double *phis)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    fdop_t A = fd_alloc(p);
+    poisson_operator(p, &A);
+    double *b = malloc(sizeof(double) * N), *Aphi = malloc(sizeof(double) * N);
+    double *shift = malloc(sizeof(double) * N), *dphi = calloc(N, sizeof(double));
+    for (long k = 0; k < N; ++k) {
+        double ch = p->rho_f ? p->rho_f[k] : 0.0, sc = 0.0;
+        for (int i = 0; i < p->s; ++i) {
+            ch += p->q[i] * rho[i * N + k];
+            sc += (double)p->q[i] * p->q[i] * rho[i * N + k];
+        }
+        b[k] = 4.0 * M_PI * p->lB * ch;
+        shift[k] = 4.0 * M_PI * p->lB * sc;
+    }
+    for (long k = 0; k < plane; ++k) {
+        b[k] += A.czlo[k] * p->phi_lo;
+        b[N - plane + k] += A.cz[N - plane + k] * p->phi_hi;
+    }
+    fd_apply(&A, phi, Aphi);
+    for (long k = 0; k < N; ++k) b[k] -= Aphi[k];
+    int it = pcg_shifted(&A, shift, b, dphi, p->lin_tol, p->lin_max_iter);
+    for (long k = 0; k < N; ++k) phis[k] = phi[k] + dphi[k];
+    free(b); free(Aphi); free(shift); free(dphi); free(A.cx);
+    return it;
+}
+
 /* Slotboom Nernst-Planck solve (Sec 2.1 and 3.1) for species i:
  *   Dbar = D exp(-(q phi + mu)),  face coefficient = harmonic mean of the two
  *   node values, Dirichlet rhobar on the z faces from the reservoir
@@ -882,7 +921,9 @@ void oracle_np_flux(const oracle_problem *p, int i, const double *phi, const dou
 
 /* ------------------------------------------------------------------ */
 /* Relaxed Gummel iteration (Sec 3.2):
- *   mu_ex from rho^{n-1}; Poisson -> phi*; phi^n = l1 phi* + (1-l1) phi^{n-1};
+ *   mu_ex from rho^{n-1}; Poisson -> phi* (the linear solve with rho^{n-1}, or
+ *   with p->screened one Newton step that keeps the densities' Boltzmann
+ *   dependence on phi, see poisson_newton_step); phi^n = l1 phi* + (1-l1) phi^{n-1};
  *   per species Slotboom NP solve with Dbar from phi^n and mu_ex -> rhobar;
  *   rho* = rhobar exp(-(q phi^n + mu_ex)); rho^n = l2 rho* + (1-l2) rho^{n-1}
  *   (rho_mix 0, as printed) or rho^n = rho^{n-1} (rho* / rho^{n-1})^l2
@@ -921,7 +962,8 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
     for (n = 1; n <= p->max_iter; ++n) {
         if (oracle_excess_mu(p, rho, mu) > 0) { status = 2; break; }
         memcpy(phis, phi, sizeof(double) * N);
-        lin += oracle_poisson(p, rho, phis, 0);
+        if (p->screened) lin += poisson_newton_step(p, rho, phi, phis);
+        else lin += oracle_poisson(p, rho, phis, 0);
         double dphi = 0.0;
         for (long k = 0; k < N; ++k) {
             double v = p->lambda_phi * phis[k] + (1.0 - p->lambda_phi) * phi[k];

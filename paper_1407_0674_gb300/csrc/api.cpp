@@ -214,18 +214,24 @@ int pnp_status(pnp_problem *h) {
 
 int pnp_gummel_solve(pnp_problem *h, const double *phi0, const double *rho0, double *phi_out, double *rho_out,
                      pnp_stats *stats) {
-    if (!h) return PNP_ERR_INVALID;
+    if (stats) *stats = pnp_stats{};
+    auto fail = [&](int code) {
+        if (stats) stats->status = code;
+        return code;
+    };
+    if (!h) return fail(PNP_ERR_INVALID);
     Problem *p = h->impl;
     auto t0 = std::chrono::steady_clock::now();
     const size_t N = p->npts(), n = N * p->s;
     if (rho0)
         for (size_t k = 0; k < n; ++k)
-            if (!(rho0[k] > 0.0) || !std::isfinite(rho0[k])) return PNP_ERR_INVALID;
+            if (!(rho0[k] > 0.0) || !std::isfinite(rho0[k])) return fail(PNP_ERR_INVALID);
     if (phi0)
         for (size_t k = 0; k < N; ++k)
-            if (!std::isfinite(phi0[k])) return PNP_ERR_INVALID;
+            if (!std::isfinite(phi0[k])) return fail(PNP_ERR_INVALID);
     if (!p->d_io) {
-        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
+        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess)
+            return fail(PNP_ERR_NOMEM);
         p->device_bytes += sizeof(double) * (2 * n + N);
     }
     cudaStream_t st = p->stream;
@@ -240,7 +246,7 @@ int pnp_gummel_solve(pnp_problem *h, const double *phi0, const double *rho0, dou
         e = cudaMemcpyAsync(d_phi, phi0, sizeof(double) * N, cudaMemcpyHostToDevice, st);
         d_phi0 = d_phi;
     }
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail(cuda_status(e));
     pnp_stats local{};
     int rc = gummel_run(p, d_phi0, d_rho0, d_phi, d_rho, &local, st);
     if (rc == PNP_OK || rc == PNP_ERR_NOT_CONVERGED) {

@@ -30,6 +30,7 @@ namespace pnp {
 struct Op {
     int nx, ny, nz;
     const double *cx, *cy, *cz, *czlo;
+    const double *dg = nullptr;    // optional extra diagonal (Poisson-Boltzmann screening)
 };
 
 struct Level {
@@ -38,6 +39,7 @@ struct Level {
     int fx, fy, fz;                // aggregation factors to the next level
     double *cx, *cy, *cz, *czlo;   // operator being solved (Poisson or NP)
     double *pcx, *pcy, *pcz, *pczlo;   // Poisson copy (built once)
+    double *dg;                    // diagonal term of the screened Poisson operator
     double *x, *b, *r;
 };
 
@@ -55,6 +57,9 @@ struct DevStats {
     double residual;       // last Gummel residual
     long long lin;         // linear iterations over the solve
     double lin_tol;        // current tolerance of the linear solves (adaptive mode)
+    int eq_enable;         // run the equilibrium stage (set before each launch)
+    int eq_iters;          // its iterations
+    double eq_residual;    // its last residual
 };
 
 struct GummelState {
@@ -73,6 +78,7 @@ struct GummelState {
     unsigned long long *dmax = nullptr;
     size_t bytes = 0;
     bool poisson_ready = false;
+    bool shift = false;            // operators carry the levels' dg while capturing
 };
 
 enum { S_RZ = 0, S_PAP, S_RR, S_ALPHA, S_BETA, S_RZNEW, S_BB, S_TGT, S_COUNT };
@@ -86,6 +92,7 @@ __device__ __forceinline__ double op_diag(const Op &A, int i, int j, int k, size
     double d = A.cx[p] + A.cy[p] + A.cz[p];
     d += A.cx[pidx(im, j, k, A.nx, A.ny)] + A.cy[pidx(i, jm, k, A.nx, A.ny)];
     d += k > 0 ? A.cz[p - (size_t)A.nx * A.ny] : A.czlo[p];
+    if (A.dg) d += A.dg[p];
     return d;
 }
 
@@ -444,7 +451,7 @@ __global__ void k_coarse_smem(Op A, double *__restrict__ x_out, const double *__
     const Op S{A.nx, A.ny, A.nz, cx, cy, cz, cl};
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
-        dg[p] = op_diag(S, i, j, k, p);
+        dg[p] = op_diag(S, i, j, k, p) + (A.dg ? A.dg[p] : 0.0);
     }
     __syncthreads();
     const int order[4] = {0, 1, 1, 0};
@@ -542,6 +549,75 @@ __global__ void k_final_check(const double *__restrict__ partial, int nb, double
 }
 
 // ---------------------------------------------------------------------------
+// equilibrium cDFT initial guess (Sec 3.2, choice of initial guess)
+constexpr int kMaxSpecies = 8;
+constexpr double kEqPhiStep = 1.0;        // |Newton step of phi| per point, kT/e
+struct EqConst {
+    int s;
+    int q[kMaxSpecies];
+    double cb[kMaxSpecies];       // rho_b,i exp(mu_b,i): rho_i = cb_i exp(-(mu_ex,i + q_i phi))
+    double inv_rb[kMaxSpecies];
+    double lam;
+};
+
+// Newton right-hand side of the Poisson-Boltzmann equation at the current
+// phi with the Boltzmann densities of mu_ex: rhs = b(phi) - A phi, and the
+// screening term dg = 4 pi lB sum q^2 rho (A: the Poisson operator)
+__global__ void k_eq_rhs(Op A, PhysConst c, EqConst e, const double *__restrict__ phi, const double *__restrict__ mu,
+                         const double *__restrict__ rho_f, double *__restrict__ rhs, double *__restrict__ dg,
+                         int *__restrict__ flag) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    const size_t plane = (size_t)c.nx * c.ny;
+    bool bad = false;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / plane;
+        double ch = rho_f ? rho_f[p] : 0.0, sc = 0.0;
+        for (int a = 0; a < e.s; ++a) {
+            const double r = e.cb[a] * exp(-(mu[a * n + p] + e.q[a] * phi[p]));
+            ch += e.q[a] * r;
+            sc += (double)(e.q[a] * e.q[a]) * r;
+        }
+        double b = 4.0 * M_PI * c.lB * ch;
+        if (k == 0) b += c.phi_lo;
+        if (k + 1 == c.nz) b += c.phi_hi;
+        const double v = b - (op_diag(A, i, j, k, p) * phi[p] - op_nbr(A, phi, i, j, k, p));
+        const double d = 4.0 * M_PI * c.lB * sc;
+        rhs[p] = v;
+        dg[p] = d;
+        if (!isfinite(v) || !isfinite(d)) bad = true;
+    }
+    if (bad) atomicOr(flag, kFlagOverflow);
+}
+
+// phi += clamp(dphi); rho moves toward the Boltzmann densities of the new phi
+// by the step-limited geometric relaxation; track the residual
+__global__ void k_eq_update(size_t n, EqConst e, double *__restrict__ phi, const double *__restrict__ dphi,
+                            const double *__restrict__ mu, double *__restrict__ rho,
+                            unsigned long long *__restrict__ dmax, int *__restrict__ flag) {
+    double m = 0;
+    bool bad = false;
+    GRID_LOOP(p, n) {
+        const double d = fmin(fmax(dphi[p], -kEqPhiStep), kEqPhiStep);
+        const double ph = phi[p] + d;
+        phi[p] = ph;
+        m = fmax(m, fabs(d));
+        for (int a = 0; a < e.s; ++a) {
+            const size_t t = a * n + p;
+            const double rs = e.cb[a] * exp(-(mu[t] + e.q[a] * ph));
+            const double old = rho[t];
+            const double step = fmin(fmax(e.lam * log(rs / old), -kMixStepLimit), kMixStepLimit);
+            const double v = old * exp(step);
+            if (!isfinite(v) || !(v > 0)) bad = true;
+            m = fmax(m, fabs(v - old) * e.inv_rb[a]);
+            rho[t] = v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+    if (bad) atomicOr(flag, kFlagOverflow);
+}
+
+// ---------------------------------------------------------------------------
 // loop control on the device (conditional graph nodes)
 
 // start of a linear solve: target = tol^2 ||b||^2; enter the loop unless the
@@ -588,27 +664,60 @@ __global__ void k_gummel_check(const unsigned long long *dmax, const int *flag, 
     cudaGraphSetConditional(h, cont);
 }
 
-__global__ void k_stats_reset(DevStats *st) {
+// end of an equilibrium iteration: residual, status, continue or hand over
+// to the Gummel loop (which an error skips)
+__global__ void k_eq_check(const unsigned long long *dmax, const int *flag, double tol, int max_iter, DevStats *st,
+                           cudaGraphConditionalHandle h_eq, cudaGraphConditionalHandle h_g) {
+    const unsigned long long bits = *dmax;
+    const double res = __longlong_as_double((long long)bits);
+    const int it = ++st->eq_iters;
+    st->eq_residual = res;
+    st->lin_tol = fmin(1e-6, fmax(1e-12, 0.01 * res));
+    const int f = *flag;
+    unsigned cont = 0;
+    if (f & kFlagPacking) st->status = PNP_ERR_PACKING;
+    else if (f & (kFlagOverflow | kFlagNonFinite)) st->status = PNP_ERR_OVERFLOW;
+    else if (res < tol) st->status = PNP_OK;
+    else if (it >= max_iter) st->status = PNP_ERR_NOT_CONVERGED;
+    else cont = 1;
+    cudaGraphSetConditional(h_eq, cont);
+    if (!cont && (f & (kFlagPacking | kFlagOverflow | kFlagNonFinite))) cudaGraphSetConditional(h_g, 0u);
+}
+
+// first node of a graph with the equilibrium stage: enter it if requested,
+// and the Gummel loop if it has iterations
+__global__ void k_eq_gate(const DevStats *st, cudaGraphConditionalHandle h_eq, cudaGraphConditionalHandle h_g,
+                          int gummel) {
+    cudaGraphSetConditional(h_eq, st->eq_enable ? 1u : 0u);
+    cudaGraphSetConditional(h_g, gummel ? 1u : 0u);
+}
+
+__global__ void k_stats_reset(DevStats *st, int eq_enable) {
     st->lin_tol = 1e-6;
     st->status = PNP_ERR_NOT_CONVERGED;
     st->iters = 0;
     st->pcg_it = 0;
     st->residual = 0;
     st->lin = 0;
+    st->eq_enable = eq_enable;
+    st->eq_iters = 0;
+    st->eq_residual = 0;
 }
 
 // ---------------------------------------------------------------------------
 // host orchestration
 static int grid_for(size_t n) { return (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16); }
 
-static Op op_of(const Level &L) { return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo}; }
+static Op op_of(const Level &L, bool shift = false) {
+    return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo, shift ? L.dg : nullptr};
+}
 
 // one V(1,1) cycle for level l: x = M b (x, b default to the level's vectors)
 static void vcycle(GummelState *g, int l, cudaStream_t st, double *x = nullptr, const double *b = nullptr) {
     Level &L = g->lv[l];
     if (!x) x = L.x;
     if (!b) b = L.b;
-    const Op A = op_of(L);
+    const Op A = op_of(L, g->shift);
     const int G = grid_for(L.n);
     if (l + 1 == (int)g->lv.size()) {
         if (L.n <= (size_t)kCoarseMax)
@@ -646,8 +755,10 @@ static void dot(GummelState *g, const double *a, const double *b, size_t n, int 
 }
 
 // Append a conditional WHILE node to the capture on `st`; later captured work
-// depends on it.  Returns its body graph and handle (default value `dflt`).
-static cudaError_t add_while(cudaStream_t st, unsigned dflt, cudaGraphConditionalHandle *h, cudaGraph_t *body) {
+// depends on it.  Returns its body graph and handle (default value `dflt`);
+// with `have_handle` the caller's handle *h is used instead of a new one.
+static cudaError_t add_while(cudaStream_t st, unsigned dflt, cudaGraphConditionalHandle *h, cudaGraph_t *body,
+                             bool have_handle = false) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -655,7 +766,7 @@ static cudaError_t add_while(cudaStream_t st, unsigned dflt, cudaGraphConditiona
     size_t nd = 0;
     cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, &ed, &nd);
     if (e != cudaSuccess) return e;
-    e = cudaGraphConditionalHandleCreate(h, cg, dflt, cudaGraphCondAssignDefault);
+    if (!have_handle) e = cudaGraphConditionalHandleCreate(h, cg, dflt, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return e;
     cudaGraphNodeParams prm = {};
     prm.type = cudaGraphNodeTypeConditional;
@@ -676,7 +787,7 @@ static cudaError_t add_while(cudaStream_t st, unsigned dflt, cudaGraphConditiona
 static cudaError_t pcg_capture(GummelState *g, double *x, const double *b, double tol, int maxit, int *flag,
                                cudaStream_t st, cudaStream_t sb) {
     Level &L0 = g->lv[0];
-    const Op A = op_of(L0);
+    const Op A = op_of(L0, g->shift);
     const size_t n = L0.n;
     const int G = grid_for(n);
     const int NB = std::min(G, kRedBlocks);
@@ -770,6 +881,8 @@ int gummel_setup(Problem *p) {
         ok = alloc(&L.cx, L.n) && alloc(&L.cy, L.n) && alloc(&L.cz, L.n) && alloc(&L.czlo, L.n) &&
              alloc(&L.pcx, L.n) && alloc(&L.pcy, L.n) && alloc(&L.pcz, L.n) && alloc(&L.pczlo, L.n) &&
              alloc(&L.x, L.n) && alloc(&L.b, L.n) && alloc(&L.r, L.n);
+        L.dg = nullptr;
+        if (ok && p->eq_init) ok = alloc(&L.dg, L.n);
     }
     ok = ok && alloc(&g->mu, N * p->s) && alloc(&g->phi, N) && alloc(&g->rho, N * p->s) &&
          alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
@@ -798,7 +911,8 @@ void gummel_free(Problem *p) {
     GummelState *g = p->gs;
     if (!g) return;
     for (auto &L : g->lv) {
-        for (double *a : {L.cx, L.cy, L.cz, L.czlo, L.pcx, L.pcy, L.pcz, L.pczlo, L.x, L.b, L.r}) dfree(a, p->stream);
+        for (double *a : {L.cx, L.cy, L.cz, L.czlo, L.pcx, L.pcy, L.pcz, L.pczlo, L.dg, L.x, L.b, L.r})
+            dfree(a, p->stream);
     }
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
@@ -835,9 +949,55 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
     cudaGraphConditionalHandle hg;
     cudaGraph_t body = nullptr;
     int rc = PNP_OK;
-    if (e == cudaSuccess) e = add_while(st, 1, &hg, &body);
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && p->eq_init) {
+        // equilibrium stage: a gate node, then its own WHILE loop; the Gummel
+        // loop's handle is set by the gate and cleared by a failed stage
+        cudaGraphConditionalHandle he;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&he, cg, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hg, cg, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) k_eq_gate<<<1, 1, 0, st>>>(g->stats, he, hg, p->max_iter > 0 ? 1 : 0);
+        cudaGraph_t ebody = nullptr;
+        if (e == cudaSuccess) e = add_while(st, 0, &he, &ebody, true);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(sb, ebody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            EqConst ec{};
+            ec.s = s;
+            for (int i = 0; i < s; ++i) {
+                ec.q[i] = p->q[i];
+                ec.cb[i] = p->rho_b[i] * std::exp(p->mu_bulk[i]);
+                ec.inv_rb[i] = 1.0 / p->rho_b[i];
+            }
+            ec.lam = p->lambda_rho;
+            rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
+            cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
+            set_operator(g, true);
+            Level &L0 = g->lv[0];
+            k_eq_rhs<<<G, 256, 0, sb>>>(op_of(L0), c, ec, g->phi, g->mu, d_rhof, g->rhs, L0.dg, p->d_flag);
+            for (size_t l = 0; l + 1 < g->lv.size(); ++l) {
+                Level &F = g->lv[l], &C = g->lv[l + 1];
+                k_restrict<<<grid_for(C.n), 256, 0, sb>>>(F.dg, F.nx, F.ny, F.fx, F.fy, F.fz, C.nx, C.ny, C.nz, C.dg);
+            }
+            k_fill<<<G, 256, 0, sb>>>(g->x, 0.0, N);
+            g->shift = true;
+            e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
+            g->shift = false;
+            set_operator(g, true);
+            k_eq_update<<<G, 256, 0, sb>>>(N, ec, g->phi, g->x, g->mu, g->rho, g->dmax, p->d_flag);
+            k_eq_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->eq_tol, p->eq_max_iter, g->stats, he, hg);
+            cudaError_t e2 = cudaStreamEndCapture(sb, &ebody);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = add_while(st, 0, &hg, &body, true);
+    } else if (e == cudaSuccess) {
+        e = add_while(st, 1, &hg, &body);
+    }
+    if (e == cudaSuccess && rc == PNP_OK)
+        e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess && rc == PNP_OK) {
         // 1. mu_ex from rho^{n-1}
         rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
         cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
@@ -926,7 +1086,7 @@ int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaSt
         for (int i = 0; i < s; ++i) k_fill<<<G, 256, 0, st>>>(g->rho + i * N, p->rho_b[i], N);
     }
     cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
-    k_stats_reset<<<1, 1, 0, st>>>(g->stats);
+    k_stats_reset<<<1, 1, 0, st>>>(g->stats, (p->eq_init && !d_phi0 && !d_rho0) ? 1 : 0);
     return cuda_status(cudaGraphLaunch(g->exec, st));
 }
 
@@ -951,6 +1111,8 @@ void gummel_decode_stats(const void *raw, pnp_stats *out) {
     out->residual = hs->residual;
     out->linear_iterations = hs->lin;
     out->status = hs->status;
+    out->init_iterations = hs->eq_iters;
+    out->init_residual = hs->eq_residual;
 }
 
 int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho, pnp_stats *stats,
@@ -970,6 +1132,8 @@ int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d
         stats->residual = local.residual;
         stats->linear_iterations = local.linear_iterations;
         stats->status = local.status;
+        stats->init_iterations = local.init_iterations;
+        stats->init_residual = local.init_residual;
     }
     return local.status;
 }

@@ -298,7 +298,10 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     if (!(d->lambda_phi > 0 && d->lambda_phi <= 1) || !(d->lambda_rho > 0 && d->lambda_rho <= 1))
         return bad("relaxation parameters must be in (0, 1]");
     if (d->rho_mix < PNP_MIX_LINEAR || d->rho_mix > PNP_MIX_GEOMETRIC_LIMITED) return bad("bad rho_mix");
-    if (!(d->tol > 0) || d->max_iter < 1) return bad("tol must be > 0 and max_iter >= 1");
+    const bool eq = (d->flags & PNP_FLAG_EQUILIBRIUM_INIT) != 0;
+    if (!(d->tol > 0) || d->max_iter < (eq ? 0 : 1))
+        return bad("tol must be > 0 and max_iter >= 1 (>= 0 with the equilibrium initial guess)");
+    if (d->eq_tol < 0 || d->eq_max_iter < 0) return bad("eq_tol and eq_max_iter must be >= 0");
     if (d->precision != PNP_PREC_FP64 && d->precision != PNP_PREC_FP32 && d->precision != PNP_PREC_DF64 &&
         d->precision != PNP_PREC_TF32SPLIT)
         return bad("bad precision");
@@ -357,6 +360,9 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->rho_mix = d->rho_mix;
     p->tol = d->tol;
     p->max_iter = d->max_iter;
+    p->eq_init = eq;
+    p->eq_tol = d->eq_tol > 0 ? d->eq_tol : 1e-6;
+    p->eq_max_iter = d->eq_max_iter > 0 ? d->eq_max_iter : 1000;
     p->quad[0] = d->quad_nmu; p->quad[1] = d->quad_ntheta; p->quad[2] = d->quad_nr;
     p->wquad[0] = d->well_nmu; p->wquad[1] = d->well_ntheta; p->wquad[2] = d->well_nr;
     p->sw_half = d->sw_half ? 1 : 0;

@@ -69,6 +69,9 @@ struct Problem {
     int rho_mix = 0;
     double tol = 1e-8;
     int max_iter = 500;
+    bool eq_init = false;             // equilibrium initial guess before the Gummel loop
+    double eq_tol = 1e-6;
+    int eq_max_iter = 1000;
     int quad[3] = {0, 0, 0}, wquad[3] = {0, 0, 0};
     int sw_half = 1;
     int precision = 0;

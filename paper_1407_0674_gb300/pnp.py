@@ -36,6 +36,7 @@ ERR_TOO_LARGE = -10
 
 BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
 FLAG_AUTOTUNE = 1
+FLAG_EQUILIBRIUM_INIT = 2
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -65,12 +66,15 @@ class Desc(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("lin_tol", ctypes.c_double),
         ("flags", ctypes.c_uint),
+        ("eq_tol", ctypes.c_double),
+        ("eq_max_iter", ctypes.c_int),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("residual", ctypes.c_double),
-                ("linear_iterations", ctypes.c_longlong), ("seconds", ctypes.c_double)]
+                ("linear_iterations", ctypes.c_longlong), ("seconds", ctypes.c_double),
+                ("init_iterations", ctypes.c_int), ("init_residual", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -198,7 +202,10 @@ class DescHolder:
             d.fft_len[c] = int(spec.fft_len[c])
         d.precision = PREC[precision]
         d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
-        d.flags = FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0
+        d.flags = (FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0) | \
+            (FLAG_EQUILIBRIUM_INIT if getattr(spec, "eq_init", False) else 0)
+        d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
+        d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         self.desc = d
 
 
@@ -285,7 +292,8 @@ class Problem:
         r0 = None if rho0 is None else _f64(rho0)
         rc = lib().pnp_gummel_solve(self.h, _ptr(p0), _ptr(r0), _ptr(phi), _ptr(rho), ctypes.byref(st))
         stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
-                 "linear_iterations": st.linear_iterations, "seconds": st.seconds}
+                 "linear_iterations": st.linear_iterations, "seconds": st.seconds,
+                 "init_iterations": st.init_iterations, "init_residual": st.init_residual}
         if raise_on_error and rc not in (OK,):
             raise PnpError(rc, "pnp_gummel_solve")
         return phi, rho, stats
@@ -334,7 +342,8 @@ class Server:
             return rc, None, None, None
         self._shapes.pop(ticket, None)
         stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
-                 "linear_iterations": st.linear_iterations, "seconds": st.seconds}
+                 "linear_iterations": st.linear_iterations, "seconds": st.seconds,
+                 "init_iterations": st.init_iterations, "init_residual": st.init_residual}
         return rc, phi, rho, stats
 
     def stats(self):

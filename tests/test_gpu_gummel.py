@@ -148,3 +148,66 @@ def test_not_converged_and_invalid(pnp):
         with pytest.raises(pnp.PnpError) as e:
             P.gummel_solve()
         assert e.value.code == pnp.ERR_INVALID
+
+
+# ---------------------------------------------------------------------------
+# equilibrium cDFT initial guess (PNP_FLAG_EQUILIBRIUM_INIT)
+
+def eq_spec(bias, **kw):
+    spec = dilute(0.0, bias, mix=1)
+    for k, v in dict(eq_init=True, max_iter=0, lin_tol=1e-13, **kw).items():
+        setattr(spec, k, v)
+    return spec
+
+
+def test_equilibrium_trajectory_matches_oracle(pnp):
+    """Three equilibrium iterations alone (max_iter 0): Newton steps of the
+    Poisson-Boltzmann equation and the Boltzmann relaxation, against the
+    oracle's."""
+    spec = eq_spec(0.5, eq_tol=1e-30, eq_max_iter=3)
+    ref = oracle.equilibrium(spec, tol=1e-30, max_iter=3)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+    assert st["status"] == pnp.ERR_NOT_CONVERGED and st["iterations"] == 0
+    assert st["init_iterations"] == 3 == ref["iters"]
+    assert rel(phi, ref["phi"], 1.0) <= TOL
+    for i in range(spec.s):
+        assert rel(rho[i], ref["rho"][i]) <= TOL
+
+
+def test_equilibrium_converged_matches_oracle(pnp):
+    spec = eq_spec(0.5, eq_tol=1e-10, eq_max_iter=2000)
+    ref = oracle.equilibrium(spec, tol=1e-10, max_iter=2000)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+    assert ref["status"] == 0 and st["status"] == 0
+    assert rel(phi, ref["phi"], 1.0) <= TOL
+    for i in range(spec.s):
+        assert rel(rho[i], ref["rho"][i]) <= TOL
+
+
+def test_equilibrium_start_reaches_the_same_solution(pnp):
+    """A biased solve started from the equilibrium converges to the state the
+    default start reaches (one fixed point), in fewer Gummel iterations."""
+    base = dilute(0.0, 0.5, mix=1)
+    spec = dilute(0.0, 0.5, mix=1)
+    spec.eq_init, spec.eq_tol = True, 1e-8
+    with pnp.Problem(base) as P:
+        phi0, rho0, st0 = P.gummel_solve()
+    with pnp.Problem(spec) as P:
+        phi1, rho1, st1 = P.gummel_solve()
+    assert st0["status"] == 0 and st1["status"] == 0 and st1["init_iterations"] > 0
+    assert rel(phi1, phi0, 1.0) <= 1e-8
+    for i in range(spec.s):
+        assert rel(rho1[i], rho0[i]) <= 1e-8
+    assert st1["iterations"] < st0["iterations"]
+
+
+def test_equilibrium_skipped_with_warm_start(pnp):
+    spec = dilute(0.0, 0.5, mix=1)
+    spec.eq_init = True
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve()
+        phi2, rho2, st2 = P.gummel_solve(phi0=phi, rho0=rho)
+    assert st["init_iterations"] > 0 and st2["init_iterations"] == 0
+    assert st2["iterations"] <= 2

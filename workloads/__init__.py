@@ -59,6 +59,10 @@ class ProblemSpec:
     fft_len: Tuple[int, int, int] = (0, 0, 0)  # padded FFT lengths for the GPU plan (0 = auto)
     lin_tol: float = 0.0                     # linear-solve relative residual (0 = library default)
     autotune: bool = False                   # GPU plan: time candidate lengths and tiles, keep the fastest
+    eq_init: bool = False                    # start the Gummel loop from the equilibrium cDFT state
+    eq_tol: float = 0.0                      # its stopping residual (0 = library default)
+    eq_max_iter: int = 0                     # its iteration cap (0 = library default)
+    screened_poisson: bool = False           # Gummel Poisson step as one screened Newton step
 
     @property
     def s(self) -> int:
