@@ -92,6 +92,16 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * With this flag max_iter may be 0: the call then returns the equilibrium. */
 #define PNP_FLAG_EQUILIBRIUM_INIT 2u
 
+/* PNP_FLAG_SCREENED_POISSON: the Poisson step of each Gummel iteration keeps
+ * the densities' first-order Boltzmann dependence on phi (Slotboom variables
+ * and mu_ex frozen): one Newton step from the current phi,
+ *   (A + diag 4 pi lB sum_i q_i^2 rho_i) dphi = 4 pi lB (rho_f + sum_i q_i rho_i) - A phi,
+ * phi* = phi + dphi, then the usual relaxation.  Same fixed point as the
+ * plain Poisson solve; the plain relaxed iteration is unstable once the box
+ * is many Debye lengths long (the loop gain of its slowest charge mode grows
+ * as lambda_phi lambda_rho kappa^2 / k^2), the screened one is not. */
+#define PNP_FLAG_SCREENED_POISSON 4u
+
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
  * (equal to first order, positive for large steps), or the geometric form

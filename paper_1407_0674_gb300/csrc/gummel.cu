@@ -301,6 +301,44 @@ __global__ void k_poisson_rhs(PhysConst c, const double *__restrict__ rho, int s
     }
 }
 
+// Screened Poisson step of the Gummel iteration: Newton right-hand side
+// b(rho) - A phi at the current densities and the screening term
+// dg = 4 pi lB sum q^2 rho (A: the Poisson operator)
+__global__ void k_scr_rhs(Op A, PhysConst c, const double *__restrict__ rho, int s, const int *__restrict__ q,
+                          const double *__restrict__ rho_f, const double *__restrict__ phi, double *__restrict__ rhs,
+                          double *__restrict__ dg) {
+    const size_t n = (size_t)c.nx * c.ny * c.nz;
+    const size_t plane = (size_t)c.nx * c.ny;
+    GRID_LOOP(p, n) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / plane;
+        double ch = rho_f ? rho_f[p] : 0.0, sc = 0.0;
+        for (int a = 0; a < s; ++a) {
+            const double r = rho[a * n + p];
+            ch += q[a] * r;
+            sc += (double)(q[a] * q[a]) * r;
+        }
+        double b = 4.0 * M_PI * c.lB * ch;
+        if (k == 0) b += c.phi_lo;
+        if (k + 1 == c.nz) b += c.phi_hi;
+        rhs[p] = b - (op_diag(A, i, j, k, p) * phi[p] - op_nbr(A, phi, i, j, k, p));
+        dg[p] = 4.0 * M_PI * c.lB * sc;
+    }
+}
+
+// phi* = phi + dphi, then phi_new = l1 phi* + (1 - l1) phi; track max |phi_new - phi|
+__global__ void k_relax_phi_step(double *__restrict__ phi, const double *__restrict__ dphi, double l1, size_t n,
+                                 unsigned long long *__restrict__ dmax) {
+    double m = 0;
+    GRID_LOOP(p, n) {
+        const double ps = phi[p] + dphi[p];
+        const double v = l1 * ps + (1.0 - l1) * phi[p];
+        m = fmax(m, fabs(v - phi[p]));
+        phi[p] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+}
+
 // phi_new = l1 phi* + (1 - l1) phi ; track max |phi_new - phi|
 __global__ void k_relax_phi(double *__restrict__ phi, const double *__restrict__ phis, double l1, size_t n,
                             unsigned long long *__restrict__ dmax) {
@@ -882,7 +920,7 @@ int gummel_setup(Problem *p) {
              alloc(&L.pcx, L.n) && alloc(&L.pcy, L.n) && alloc(&L.pcz, L.n) && alloc(&L.pczlo, L.n) &&
              alloc(&L.x, L.n) && alloc(&L.b, L.n) && alloc(&L.r, L.n);
         L.dg = nullptr;
-        if (ok && p->eq_init) ok = alloc(&L.dg, L.n);
+        if (ok && (p->eq_init || p->screened)) ok = alloc(&L.dg, L.n);
     }
     ok = ok && alloc(&g->mu, N * p->s) && alloc(&g->phi, N) && alloc(&g->rho, N * p->s) &&
          alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
@@ -1001,14 +1039,30 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
         // 1. mu_ex from rho^{n-1}
         rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
         cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
-        // 2. Poisson for phi*, starting from phi
+        // 2. Poisson for phi*, starting from phi; 3. relax phi
         set_operator(g, true);
-        k_poisson_rhs<<<G, 256, 0, sb>>>(c, g->rho, s, d_q, d_rhof, g->rhs);
-        k_copy<<<G, 256, 0, sb>>>(g->x, g->phi, N);
-        e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
-        set_operator(g, true);
-        // 3. relax phi
-        k_relax_phi<<<G, 256, 0, sb>>>(g->phi, g->x, p->lambda_phi, N, g->dmax);
+        if (p->screened) {
+            // one Newton step with the densities' Boltzmann response:
+            // (A + dg) dphi = b(rho) - A phi, phi* = phi + dphi
+            Level &L0 = g->lv[0];
+            k_scr_rhs<<<G, 256, 0, sb>>>(op_of(L0), c, g->rho, s, d_q, d_rhof, g->phi, g->rhs, L0.dg);
+            for (size_t l = 0; l + 1 < g->lv.size(); ++l) {
+                Level &F = g->lv[l], &C = g->lv[l + 1];
+                k_restrict<<<grid_for(C.n), 256, 0, sb>>>(F.dg, F.nx, F.ny, F.fx, F.fy, F.fz, C.nx, C.ny, C.nz, C.dg);
+            }
+            k_fill<<<G, 256, 0, sb>>>(g->x, 0.0, N);
+            g->shift = true;
+            e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
+            g->shift = false;
+            set_operator(g, true);
+            k_relax_phi_step<<<G, 256, 0, sb>>>(g->phi, g->x, p->lambda_phi, N, g->dmax);
+        } else {
+            k_poisson_rhs<<<G, 256, 0, sb>>>(c, g->rho, s, d_q, d_rhof, g->rhs);
+            k_copy<<<G, 256, 0, sb>>>(g->x, g->phi, N);
+            e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
+            set_operator(g, true);
+            k_relax_phi<<<G, 256, 0, sb>>>(g->phi, g->x, p->lambda_phi, N, g->dmax);
+        }
         // 4. Nernst-Planck per species
         for (int i = 0; i < s && e == cudaSuccess; ++i) {
             NpConst nc;

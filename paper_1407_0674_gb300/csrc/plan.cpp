@@ -361,6 +361,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->tol = d->tol;
     p->max_iter = d->max_iter;
     p->eq_init = eq;
+    p->screened = (d->flags & PNP_FLAG_SCREENED_POISSON) != 0;
     p->eq_tol = d->eq_tol > 0 ? d->eq_tol : 1e-6;
     p->eq_max_iter = d->eq_max_iter > 0 ? d->eq_max_iter : 1000;
     p->quad[0] = d->quad_nmu; p->quad[1] = d->quad_ntheta; p->quad[2] = d->quad_nr;

@@ -70,6 +70,7 @@ struct Problem {
     double tol = 1e-8;
     int max_iter = 500;
     bool eq_init = false;             // equilibrium initial guess before the Gummel loop
+    bool screened = false;            // Gummel Poisson step as one screened Newton step
     double eq_tol = 1e-6;
     int eq_max_iter = 1000;
     int quad[3] = {0, 0, 0}, wquad[3] = {0, 0, 0};

@@ -37,6 +37,7 @@ ERR_TOO_LARGE = -10
 BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
 FLAG_AUTOTUNE = 1
 FLAG_EQUILIBRIUM_INIT = 2
+FLAG_SCREENED_POISSON = 4
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -203,7 +204,8 @@ class DescHolder:
         d.precision = PREC[precision]
         d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
         d.flags = (FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0) | \
-            (FLAG_EQUILIBRIUM_INIT if getattr(spec, "eq_init", False) else 0)
+            (FLAG_EQUILIBRIUM_INIT if getattr(spec, "eq_init", False) else 0) | \
+            (FLAG_SCREENED_POISSON if getattr(spec, "screened_poisson", False) else 0)
         d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         self.desc = d

@@ -142,8 +142,11 @@ def mu_microbench(n: int = 128, seed: int = 2, fft_len: int = 0,
 # size), species +1 (R 2h, eta 0.2), -1 (R 2h) and -1 (R 1h) with the anion
 # densities set to half the cation's (bulk electroneutrality); cation wells
 # 3 kT deep on 4096 sites (seed 0) at the full size; fixed charge seed 1.
+# The box is ~200 Debye lengths long: the plain relaxed Gummel iteration is
+# unstable there, so the solve uses the screened Poisson step, the
+# equilibrium initial guess and the step-limited geometric relaxation.
 def film3(nx: int = 128, ny: int = 128, nz: int = 256, nsites: Optional[int] = None,
-          bias: float = 0.0, tol: float = 1e-8, max_iter: int = 500) -> ProblemSpec:
+          bias: float = 0.0, tol: float = 1e-8, max_iter: int = 2000) -> ProblemSpec:
     if nsites is None:
         nsites = max(1, (nx * ny * nz) // 1024)
     rb1 = bulk_density(0.2, 2.0)
@@ -152,7 +155,8 @@ def film3(nx: int = 128, ny: int = 128, nz: int = 256, nsites: Optional[int] = N
     return ProblemSpec(nx=nx, ny=ny, nz=nz, bc=("P", "P", "D"), R=(2.0, 2.0, 1.0), q=(1, -1, -1),
                        rho_b=(rb1, rb1 / 2, rb1 / 2), depth=(3.0, 0.0, 0.0), well_inner=4.0,
                        well_outer=5.0, sites=sites, rho_f=rho_f, phi_lo=0.0, phi_hi=bias, tol=tol,
-                       lambda_phi=0.3, lambda_rho=0.05, rho_mix=1, max_iter=max_iter)
+                       lambda_phi=0.3, lambda_rho=0.05, rho_mix=2, max_iter=max_iter,
+                       screened_poisson=True, eq_init=True)
 
 
 # --------------------------------------------------------------------------
