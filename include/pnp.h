@@ -106,8 +106,13 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
  * (equal to first order, positive for large steps), or the geometric form
  * with its step in ln rho limited to +-0.2 per iteration (deep square wells
- * cannot push the packing fraction past 1 in one step; same fixed point). */
-enum { PNP_MIX_LINEAR = 0, PNP_MIX_GEOMETRIC = 1, PNP_MIX_GEOMETRIC_LIMITED = 2 };
+ * cannot push the packing fraction past 1 in one step; same fixed point);
+ * PNP_MIX_ADAPTIVE is the step-limited form with a factor per point, halved
+ * (down to lambda_rho / 1024) when the point's step in ln rho changes sign
+ * from the previous iteration and grown by 10% (up to lambda_rho) otherwise:
+ * densely packed points in deep wells, whose response is too stiff for one
+ * global factor, stop alternating at the step limit. */
+enum { PNP_MIX_LINEAR = 0, PNP_MIX_GEOMETRIC = 1, PNP_MIX_GEOMETRIC_LIMITED = 2, PNP_MIX_ADAPTIVE = 3 };
 
 typedef struct {
     int nx, ny, nz;                /* grid points per axis */

@@ -216,7 +216,9 @@ typedef struct {
     double lin_tol;            /* PCG relative residual target */
     int lin_max_iter;
     int rho_mix;               /* 0: linear relaxation (Sec 3.2), 1: geometric,
-                                  2: geometric with |step in ln rho| <= 0.2 */
+                                  2: geometric with |step in ln rho| <= 0.2,
+                                  3: 2 with a per-point factor: halved when the
+                                     step changes sign, else grown 10% up to l2 */
     int screened;              /* Gummel Poisson step: 0 linear solve, 1 one Newton step
                                   with the densities' Boltzmann dependence on phi */
 } oracle_problem;
@@ -930,7 +932,11 @@ void oracle_np_flux(const oracle_problem *p, int i, const double *phi, const dou
  *   (rho_mix 1: the same update to first order, kept positive and bounded for
  *   the large first steps of a dense fluid next to a hard wall), or that step
  *   in ln rho limited to +-0.2 per iteration (rho_mix 2: deep square wells
- *   cannot push the packing fraction past 1 in one step; same fixed point);
+ *   cannot push the packing fraction past 1 in one step; same fixed point),
+ *   or that with a factor per point (rho_mix 3): halved (down to l2/1024)
+ *   when the point's step changes sign from the last iteration, else grown
+ *   by 10% up to l2 -- the stiff, densely packed points of deep wells then
+ *   stop alternating at the step limit; same fixed point;
  *   stop when max(|dphi|_inf, max_i |drho_i|_inf / rho_b,i) < tol.
  * Initial state (when phi0/rho0 are NULL): phi linear in z between the
  * Dirichlet values, rho = rho_b.  Returns 0 converged, 1 not converged,
@@ -945,6 +951,9 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
     double *rb = malloc(sizeof(double) * N);
     double *mub = malloc(sizeof(double) * s);
     double *rho_new = malloc(sizeof(double) * s * N);
+    /* rho_mix 3: per-point relaxation factor and last step in ln rho */
+    double *lam = malloc(sizeof(double) * s * N), *prev = calloc((size_t)s * N, sizeof(double));
+    for (long k = 0; k < s * N; ++k) lam[k] = p->lambda_rho;
     oracle_bulk_mu(s, p->R, p->rho_b, mub);
     if (phi0) memcpy(phi, phi0, sizeof(double) * N);
     else
@@ -983,6 +992,15 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
                 double v;
                 if (p->rho_mix == 0) {
                     v = p->lambda_rho * rs + (1.0 - p->lambda_rho) * rho[i * N + k];
+                } else if (p->rho_mix == 3) {
+                    long t = i * N + k;
+                    double d = log(rs / rho[t]);
+                    if (d * prev[t] < 0.0) lam[t] = fmax(0.5 * lam[t], p->lambda_rho / 1024.0);
+                    else lam[t] = fmin(1.1 * lam[t], p->lambda_rho);
+                    double step = lam[t] * d;
+                    step = step > 0.2 ? 0.2 : (step < -0.2 ? -0.2 : step);
+                    prev[t] = step;
+                    v = rho[t] * exp(step);
                 } else {
                     double step = p->lambda_rho * log(rs / rho[i * N + k]);
                     if (p->rho_mix == 2) step = step > 0.2 ? 0.2 : (step < -0.2 ? -0.2 : step);
@@ -1000,7 +1018,7 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
     }
     if (iters) *iters = n > p->max_iter ? p->max_iter : n;
     if (lin_iters) *lin_iters = lin;
-    free(mu); free(phis); free(rb); free(mub); free(rho_new);
+    free(mu); free(phis); free(rb); free(mub); free(rho_new); free(lam); free(prev);
     return status;
 }
 

@@ -74,6 +74,7 @@ struct GummelState {
     cudaGraphExec_t exec = nullptr;
     double *rhs = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr;
     double *partial = nullptr;     // kRedBlocks
+    double *lam = nullptr, *prev = nullptr;   // PNP_MIX_ADAPTIVE: per-point factor and last step
     double *scal = nullptr;        // device scalars
     unsigned long long *dmax = nullptr;
     size_t bytes = 0;
@@ -409,6 +410,7 @@ __global__ void k_np_setup(PhysConst c, NpConst s, const double *__restrict__ ph
 // max |rho_new - rho| / rho_b
 __global__ void k_np_finish(size_t n, double q, double l2, int mix, double inv_rb, const double *__restrict__ phi,
                             const double *__restrict__ mu, const double *__restrict__ rbar, double *__restrict__ rho,
+                            double *__restrict__ lam, double *__restrict__ prev,
                             unsigned long long *__restrict__ dmax, int *__restrict__ flag) {
     double m = 0;
     bool bad = false;
@@ -418,6 +420,15 @@ __global__ void k_np_finish(size_t n, double q, double l2, int mix, double inv_r
         double v;
         if (mix == PNP_MIX_LINEAR) {
             v = l2 * rs + (1.0 - l2) * old;
+        } else if (mix == PNP_MIX_ADAPTIVE) {
+            // per-point factor: halved when the step in ln rho changes sign
+            const double d = log(rs / old);
+            double a = lam[p];
+            a = d * prev[p] < 0.0 ? fmax(0.5 * a, l2 / 1024.0) : fmin(1.1 * a, l2);
+            const double step = fmin(fmax(a * d, -kMixStepLimit), kMixStepLimit);
+            lam[p] = a;
+            prev[p] = step;
+            v = old * exp(step);
         } else {
             double step = l2 * log(rs / old);
             if (mix == PNP_MIX_GEOMETRIC_LIMITED) step = fmin(fmax(step, -kMixStepLimit), kMixStepLimit);
@@ -926,6 +937,7 @@ int gummel_setup(Problem *p) {
          alloc(&g->rhs, N) && alloc(&g->x, N) && alloc(&g->r, N) &&
          alloc(&g->z, N) && alloc(&g->pv, N) && alloc(&g->Ap, N) && alloc(&g->partial, kRedBlocks) &&
          alloc(&g->scal, S_COUNT);
+    if (ok && p->rho_mix == PNP_MIX_ADAPTIVE) ok = alloc(&g->lam, N * p->s) && alloc(&g->prev, N * p->s);
     if (ok) {
         if (dmalloc((void **)&g->dmax, sizeof(unsigned long long), p->stream) != cudaSuccess) ok = false;
         if (ok && dmalloc((void **)&g->stats, sizeof(DevStats), p->stream) != cudaSuccess) ok = false;
@@ -956,7 +968,8 @@ void gummel_free(Problem *p) {
     if (g->graph) cudaGraphDestroy(g->graph);
     for (int k = 0; k < 2; ++k)
         if (g->cap[k]) cudaStreamDestroy(g->cap[k]);
-    for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal})
+    for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal, g->lam,
+                      g->prev})
         dfree(a, p->stream);
     dfree(g->dmax, p->stream);
     dfree(g->stats, p->stream);
@@ -1078,7 +1091,8 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
             coarsen_all(g, sb);
             e = pcg_capture(g, g->x, g->rhs, p->lin_tol, maxlin, p->d_flag, sb, sc);
             k_np_finish<<<G, 256, 0, sb>>>(N, (double)p->q[i], p->lambda_rho, p->rho_mix, 1.0 / p->rho_b[i], g->phi,
-                                           g->mu + i * N, g->x, g->rho + i * N, g->dmax, p->d_flag);
+                                           g->mu + i * N, g->x, g->rho + i * N, g->lam ? g->lam + i * N : nullptr,
+                                           g->prev ? g->prev + i * N : nullptr, g->dmax, p->d_flag);
         }
         // 5. residual, status, continue?
         k_gummel_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->tol, p->max_iter, g->stats, hg);
@@ -1138,6 +1152,10 @@ int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaSt
         k_copy<<<G, 256, 0, st>>>(g->rho, d_rho0, N * s);
     } else {
         for (int i = 0; i < s; ++i) k_fill<<<G, 256, 0, st>>>(g->rho + i * N, p->rho_b[i], N);
+    }
+    if (g->lam) {
+        k_fill<<<G, 256, 0, st>>>(g->lam, p->lambda_rho, N * s);
+        k_fill<<<G, 256, 0, st>>>(g->prev, 0.0, N * s);
     }
     cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
     k_stats_reset<<<1, 1, 0, st>>>(g->stats, (p->eq_init && !d_phi0 && !d_rho0) ? 1 : 0);

@@ -297,7 +297,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     if (d->temperature_K <= 0 || d->eps_r <= 0 || d->h_nm <= 0) return bad("temperature, eps_r, h_nm must be > 0");
     if (!(d->lambda_phi > 0 && d->lambda_phi <= 1) || !(d->lambda_rho > 0 && d->lambda_rho <= 1))
         return bad("relaxation parameters must be in (0, 1]");
-    if (d->rho_mix < PNP_MIX_LINEAR || d->rho_mix > PNP_MIX_GEOMETRIC_LIMITED) return bad("bad rho_mix");
+    if (d->rho_mix < PNP_MIX_LINEAR || d->rho_mix > PNP_MIX_ADAPTIVE) return bad("bad rho_mix");
     const bool eq = (d->flags & PNP_FLAG_EQUILIBRIUM_INIT) != 0;
     if (!(d->tol > 0) || d->max_iter < (eq ? 0 : 1))
         return bad("tol must be > 0 and max_iter >= 1 (>= 0 with the equilibrium initial guess)");

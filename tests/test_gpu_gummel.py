@@ -240,3 +240,14 @@ def test_screened_long_box_converges_where_plain_does_not(pnp):
     assert rel(phi, ref["phi"], 1.0) <= TOL
     for i in range(spec.s):
         assert rel(rho[i], ref["rho"][i]) <= TOL
+
+
+def test_adaptive_relaxation_trajectory(pnp):
+    """Per-point adaptive relaxation (PNP_MIX_ADAPTIVE) on the deep-well batch
+    physics at 12^3: eight iterations match the oracle's."""
+    from workloads import batch_specs
+    spec = batch_specs(1, grids=[(12, 12, 12)])[0]
+    spec.depth = (12.0, 0.0)
+    spec.rho_mix = 3
+    spec.tol, spec.max_iter, spec.lin_tol = 1e-30, 8, 1e-13
+    compare(spec, pnp)

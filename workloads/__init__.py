@@ -165,7 +165,10 @@ def film3(nx: int = 128, ny: int = 128, nz: int = 256, nsites: Optional[int] = N
 # fraction U(0.1, 0.35) split equally over the two ions, fixed-charge seeds
 # 100..163, sites at one per 512 cells (seed = fixed-charge seed + 1000).
 # Wells 9-14 kT deep on a fluid at packing up to 0.35 need the step-limited
-# geometric density relaxation.
+# geometric density relaxation with per-point factors (with one global factor
+# the densely packed well shells alternate at the step limit); grids of 64
+# planes and more are many Debye lengths long and need the screened Poisson
+# step.
 BATCH_GRIDS = [(32, 32, 32), (48, 48, 48), (64, 64, 64), (80, 80, 96), (96, 96, 96)]
 KB_EV_PER_K = 8.617333262e-5
 
@@ -188,7 +191,8 @@ def batch_specs(count: int = 64, seed: int = 4, grids=None, max_iter: int = 2000
         out.append(ProblemSpec(nx=nx, ny=ny, nz=nz, bc=("P", "P", "D"), R=(R, R), q=(1, -1),
                                rho_b=(rb, rb), depth=(depth, 0.0), well_inner=4.0, well_outer=5.0,
                                sites=sites, rho_f=rho_f, temperature_K=T, phi_lo=0.0, phi_hi=0.1,
-                               lambda_phi=0.3, lambda_rho=0.05, rho_mix=2, tol=tol, max_iter=max_iter))
+                               lambda_phi=0.3, lambda_rho=0.05, rho_mix=3, tol=tol, max_iter=max_iter,
+                               screened_poisson=True))
     return out
 
 
@@ -228,5 +232,6 @@ def serving_spec(n: int, bias: float, T: float, max_iter: int = 2000, tol: float
     spec = film_gummel(n, n, n, tol=tol, max_iter=max_iter, phi_hi=bias)
     spec.temperature_K = T
     spec.depth = (0.3 / (KB_EV_PER_K * T), 0.0)
-    spec.rho_mix = 2
+    spec.rho_mix = 3                  # per-point relaxation factors (deep wells)
+    spec.screened_poisson = True      # edges up to 256: many Debye lengths
     return spec
