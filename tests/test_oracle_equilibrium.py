@@ -121,3 +121,16 @@ def test_screened_and_plain_gummel_share_the_biased_fixed_point():
     rb = spec.rho_b[0]
     assert np.abs(a["phi"] - b["phi"]).max() <= 1e-8
     assert max(np.abs(a["rho"][i] - b["rho"][i]).max() / rb for i in range(2)) <= 1e-8
+
+
+def test_adaptive_relaxation_shares_the_fixed_point():
+    """Per-point adaptive relaxation (rho_mix 3) reaches the state of the
+    global step-limited relaxation: only the path differs."""
+    import dataclasses
+    spec = small_film(0.5)
+    a = oracle.gummel(dataclasses.replace(spec, rho_mix=2))
+    b = oracle.gummel(dataclasses.replace(spec, rho_mix=3))
+    assert a["status"] == 0 and b["status"] == 0
+    rb = spec.rho_b[0]
+    assert np.abs(a["phi"] - b["phi"]).max() <= 1e-8
+    assert max(np.abs(a["rho"][i] - b["rho"][i]).max() / rb for i in range(2)) <= 1e-8
