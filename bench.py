@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_EDGE, help="grid edge (profiling runs use smaller cases)")
     ap.add_argument("--pad", type=int, default=PAD, help="padded FFT length")
     ap.add_argument("--bias-points", type=int, default=11, help="film3: points of the 0..1 kT/e bias sweep")
+    ap.add_argument("--film3-start", default="warm", choices=["warm", "eq"],
+                    help="film3: warm-start each bias point from the previous one, or start each from its equilibrium")
     ap.add_argument("--max-iter3", type=int, default=2000, help="film3: Gummel iteration cap per bias point")
     ap.add_argument("--solve-prec", default="df64", choices=["fp64", "df64", "fp32", "tf32split"],
                     help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
@@ -465,11 +467,14 @@ def run_solves(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
     if args.workload == "film3":
-        # bias sweep on the 128x128x256 film, each point started from its
-        # equilibrium (Sec 3.2): plain FP64 against the mixed-precision mu_ex
+        # bias sweep on the 128x128x256 film: the first point from its
+        # equilibrium (Sec 3.2), the others warm-started from the previous
+        # point (or each from its equilibrium with --film3-start eq); plain
+        # FP64 against the mixed-precision mu_ex
         biases = [k / max(1, args.bias_points - 1) for k in range(args.bias_points)]
         runs = {}
         for prec in ("fp64", args.solve_prec):
+            phi0 = rho0 = None
             solve_s = wall_s = 0.0
             rec = []
             for b in biases:
@@ -477,10 +482,14 @@ def run_solves(args, world, rank, local):
                 t0 = time.perf_counter()
                 with pnp.Problem(spec, precision=prec) as P:
                     t1 = time.perf_counter()
-                    phi, rho, st = P.gummel_solve(raise_on_error=False)
+                    phi, rho, st = P.gummel_solve(phi0, rho0, raise_on_error=False)
                     solve_s += time.perf_counter() - t1
                 wall_s += time.perf_counter() - t0
+                if args.film3_start == "warm" and st["status"] == 0:
+                    phi0, rho0 = phi, rho
                 rec.append((b, st, rho))
+                print(f"film3 {prec} bias {b:.2f}: status {st['status']} init {st['init_iterations']} "
+                      f"it {st['iterations']} {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
             runs[prec] = (solve_s, wall_s, rec)
         s64, w64, r64 = runs["fp64"]
         sm, wm, rm = runs[args.solve_prec]
@@ -491,8 +500,9 @@ def run_solves(args, world, rank, local):
                 "steps": n, "warmup": 0, "ms_per_step": wm / n * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
                 "config": {"workload": f"film 128x128x256, 3 mobile species (R 2/2/1 h), wells 3 kT on 4096 "
-                                       f"sites, bias sweep 0..1 kT/e in {n} points, each from its equilibrium, "
-                                       "residual 1e-8",
+                                       f"sites, bias sweep 0..1 kT/e in {n} points, "
+                                       + ("each from its equilibrium" if args.film3_start == "eq" else
+                                          "first from its equilibrium, then warm-started") + ", residual 1e-8",
                            "mu_ex_precision": args.solve_prec},
                 "solve_seconds": sm, "fp64_plain": {"solves_per_s": n / w64, "wall_s": w64, "solve_seconds": s64,
                                                     "iterations": [r[1]["iterations"] for r in r64],
@@ -533,10 +543,15 @@ def run_solves(args, world, rank, local):
                 rc, phi, rho, st = srv.poll(t)
                 if rc != pnp.PENDING:
                     done[k] = (rc, rho, st, time.perf_counter() - t0)
+                    print(f"batch {k}: status {rc} it {st['iterations']} at {done[k][3]:.1f} s", file=sys.stderr,
+                          flush=True)
             time.sleep(0.002)
         wall = time.perf_counter() - t0
         srv.close()
-        errs = [float(np.abs(done[k][1] - seq_res[k][0]).max() / np.abs(seq_res[k][0]).max()) for k in seq_res]
+        # solves that converged in both runs
+        both = [k for k in seq_res if seq_res[k][1]["status"] == 0 and done[k][0] == 0]
+        errs = [float(np.abs(done[k][1] - seq_res[k][0]).max() / np.abs(seq_res[k][0]).max()) for k in both]
+        seq_ok = sum(1 for k in seq_res if seq_res[k][1]["status"] == 0)
         ok = sum(1 for v in done.values() if v[0] in (0,))
         lat = [v[3] for v in done.values()]
         line = {"metric": "PNP solves/s", "value": world * len(specs) / wall, "unit": "solves/s", "n_gpus": world,
@@ -547,10 +562,12 @@ def run_solves(args, world, rank, local):
                                        "U(0.1,0.35), served concurrently (one CUDA graph per solve)",
                            "mu_ex_precision": args.solve_prec, "autotune": bool(args.autotune)},
                 "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq),
-                                    "mean_s": float(np.mean(seq))},
+                                    "mean_s": float(np.mean(seq)), "converged": seq_ok,
+                                    "iterations": [seq_res[k][1]["iterations"] for k in seq_res]},
                 "speedup_vs_sequential": (len(specs) / wall) / (len(seq) / sum(seq)),
                 "max_rel_err_vs_sequential": max(errs) if errs else None,
-                "converged": ok, "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+                "converged": ok, "status": [done[k][0] for k in range(len(specs))],
+                "compared_solves": len(both), "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
                 "iterations_mean": float(np.mean([v[2]["iterations"] for v in done.values()]))}
         if rank == 0:
             print(json.dumps(line), flush=True)
@@ -585,6 +602,8 @@ def run_solves(args, world, rank, local):
             if rc != pnp.PENDING:
                 lat.append(time.perf_counter() - t0 - pending.pop(t))
                 statuses.append(rc)
+                print(f"serve: status {rc} it {st['iterations']} latency {lat[-1]:.1f} s", file=sys.stderr,
+                      flush=True)
         time.sleep(0.002)
     wall = time.perf_counter() - t0
     srv.close()

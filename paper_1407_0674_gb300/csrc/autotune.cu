@@ -132,12 +132,22 @@ int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *wh
     const size_t N = best->npts(), nf = (size_t)best->s * N;
     std::vector<double> h(nf);
     for (int i = 0; i < best->s; ++i) std::fill(h.begin() + i * N, h.begin() + (i + 1) * N, best->rho_b[i]);
+    // stream-ordered buffers on a stream of the tuner's own (no device-wide
+    // synchronisation: a server tunes new shapes while other solves run; the
+    // problems timed below may be destroyed during the search)
     double *d_rho = nullptr, *d_mu = nullptr;
-    if (cudaMalloc(&d_rho, nf * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&d_mu, nf * sizeof(double)) != cudaSuccess ||
-        cudaMemcpy(d_rho, h.data(), nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d_rho);
-        cudaFree(d_mu);
+    cudaStream_t ts = nullptr;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess ||
+        dmalloc((void **)&d_rho, nf * sizeof(double), ts) != cudaSuccess ||
+        dmalloc((void **)&d_mu, nf * sizeof(double), ts) != cudaSuccess ||
+        cudaMemcpyAsync(d_rho, h.data(), nf * sizeof(double), cudaMemcpyHostToDevice, ts) != cudaSuccess ||
+        cudaStreamSynchronize(ts) != cudaSuccess) {
+        if (ts) {
+            dfree(d_rho, ts);
+            dfree(d_mu, ts);
+            cudaStreamSynchronize(ts);
+            cudaStreamDestroy(ts);
+        }
         cudaGetLastError();
         *out = best;          // untuned but valid
         return PNP_OK;
@@ -194,8 +204,11 @@ int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *wh
         best->tile[c] = tc[c][std::min_element(gt[c].begin(), gt[c].end()) - gt[c].begin()];
     const double t_final = time_plan(best, d_rho, d_mu, reps, stage);
     best->tuned_ms = t_final > 0 ? t_final : 0.0;
-    cudaFree(d_rho);
-    cudaFree(d_mu);
+    cudaStreamSynchronize(best->stream);
+    dfree(d_rho, ts);
+    dfree(d_mu, ts);
+    cudaStreamSynchronize(ts);
+    cudaStreamDestroy(ts);
 
     {
         std::lock_guard<std::mutex> lk(g_mu);
