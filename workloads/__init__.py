@@ -197,8 +197,10 @@ def batch_specs(count: int = 64, seed: int = 4, grids=None, max_iter: int = 2000
 
 
 def _smooth_sizes(lo: int, hi: int) -> List[int]:
+    """Even 2^a 3^b 5^c sizes in [lo, hi] (x is periodic and carries the
+    two-for-one real transform, so it must be even)."""
     out = []
-    for n in range(lo, hi + 1):
+    for n in range(lo + (lo % 2), hi + 1, 2):
         m = n
         for p in (2, 3, 5):
             while m % p == 0:
@@ -210,7 +212,7 @@ def _smooth_sizes(lo: int, hi: int) -> List[int]:
 
 # --------------------------------------------------------------------------
 # Served requests: Poisson arrivals at `rate` per second (seed 5), cubic
-# grids with log-uniform edge in [32, 256] rounded to a 2^a 3^b 5^c size,
+# grids with log-uniform edge in [32, 256] rounded to an even 2^a 3^b 5^c size,
 # bias U(0, 1) kT/e, temperature U(250, 400) K (well depth 0.3 eV / kT).
 def serving_arrivals(count: int = 600, rate: float = 20.0, seed: int = 5, lo: int = 32, hi: int = 256):
     """[(arrival time s, edge n, bias, temperature)]; build each problem with serving_spec."""
