@@ -580,8 +580,10 @@ def run_solves(args, world, rank, local):
     for s in specs[:args.seq]:
         with pnp.Problem(s) as P:
             t0 = time.perf_counter()
-            P.gummel_solve(raise_on_error=False)
+            _, _, st = P.gummel_solve(raise_on_error=False)
             seq.append(time.perf_counter() - t0)
+        print(f"serve sequential n {s.nx}: status {st['status']} it {st['iterations']} {seq[-1]:.1f} s",
+              file=sys.stderr, flush=True)
     srv = pnp.Server(max_slots=64)
     t0 = time.perf_counter()
     pending = {}
@@ -610,8 +612,9 @@ def run_solves(args, world, rank, local):
     line = {"metric": "PNP solves/s", "value": world * len(lat) / wall, "unit": "solves/s", "n_gpus": world,
             "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
-            "config": {"workload": f"{len(arr)} served Gummel solves, Poisson arrivals {args.rate}/s, cubic grids "
-                                   f"log-uniform 32..{args.max_edge}, bias U(0,1), T U(250,400) K, budget 150 GB",
+            "config": {"workload": f"{len(arr)} served Gummel solves (32^3-film physics), Poisson arrivals "
+                                   f"{args.rate}/s, cubic grids log-uniform 32..{args.max_edge}, bias U(0,1), "
+                                   "T U(250,400) K, budget 150 GB",
                        "mu_ex_precision": args.solve_prec, "autotune": bool(args.autotune)},
             "latency_p50_ms": _pct(lat, 50) * 1e3, "latency_p99_ms": _pct(lat, 99) * 1e3,
             "completed_ok": sum(1 for s in statuses if s == 0), "statuses": sorted(set(statuses)),

@@ -231,9 +231,11 @@ def serving_arrivals(count: int = 600, rate: float = 20.0, seed: int = 5, lo: in
 
 
 def serving_spec(n: int, bias: float, T: float, max_iter: int = 2000, tol: float = 1e-8) -> ProblemSpec:
+    """The 32^3 film's physics (2 ions, R 2h, packing 0.2 each, 1 kT wells on
+    one site per 512 cells, fixed charge) on an n^3 grid at bias and T (which
+    sets the Bjerrum length)."""
     spec = film_gummel(n, n, n, tol=tol, max_iter=max_iter, phi_hi=bias)
     spec.temperature_K = T
-    spec.depth = (0.3 / (KB_EV_PER_K * T), 0.0)
-    spec.rho_mix = 3                  # per-point relaxation factors (deep wells)
+    spec.rho_mix = 3                  # per-point relaxation factors
     spec.screened_poisson = True      # edges up to 256: many Debye lengths
     return spec
