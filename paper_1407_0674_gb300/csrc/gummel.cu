@@ -913,9 +913,12 @@ int gummel_setup(Problem *p) {
         Level L{};
         L.nx = nx; L.ny = ny; L.nz = nz;
         L.n = (size_t)nx * ny * nz;
-        L.fx = (nx % 2 == 0 && nx >= 4) ? 2 : 1;
-        L.fy = (ny % 2 == 0 && ny >= 4) ? 2 : 1;
-        L.fz = (nz % 2 == 0 && nz >= 4) ? 2 : 1;
+        // aggregate 2, 3 or 5 cells per axis, whichever divides: every
+        // 2^a 3^b 5^c extent coarsens to a handful of unknowns
+        auto fac = [](int n) { return (n >= 4 && n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : (n % 5 == 0) ? 5 : 1; };
+        L.fx = fac(nx);
+        L.fy = fac(ny);
+        L.fz = fac(nz);
         bool last = L.n <= 8 || (L.fx == 1 && L.fy == 1 && L.fz == 1) || g->lv.size() >= 16;
         if (last) L.fx = L.fy = L.fz = 1;
         g->lv.push_back(L);
