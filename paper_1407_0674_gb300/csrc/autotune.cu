@@ -78,18 +78,19 @@ int reg_lanes(int L) {
     return G;
 }
 
+// the register kernels are compiled for at most kMaxThreads per CTA
 void tile_candidates(int G, int axis, std::vector<int> *out) {
     out->assign(1, 0);     // the built-in rule
     if (!G) return;
     if (axis == 0) {
-        for (int thr : {64, 128, 256, 512})
+        for (int thr : {64, 128, 256})
             if (thr / G >= 1) out->push_back(thr / G);
     } else if (axis == 1) {
         for (int tx : {2, 4, 8, 16, 32})
-            if (tx * G <= 1024) out->push_back(tx);
+            if (tx * G <= kMaxThreads) out->push_back(tx);
     } else {
         for (int tx : {1, 2, 4, 8, 16})
-            if (2 * tx * G <= 1024) out->push_back(tx);
+            if (2 * tx * G <= kMaxThreads) out->push_back(tx);
     }
     std::sort(out->begin() + 1, out->end());
     out->erase(std::unique(out->begin() + 1, out->end()), out->end());

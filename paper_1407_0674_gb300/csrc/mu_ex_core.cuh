@@ -579,14 +579,16 @@ template <auto K> static void ensure_smem() {
     (void)done;
 }
 
-// dynamic shared memory the register kernels may request (ensure_smem)
+// dynamic shared memory the register kernels may request (ensure_smem), and
+// their threads per CTA (their __launch_bounds__)
 constexpr long kSmemCap = 200 * 1024;
+constexpr int kMaxThreads = 256;
 
 // lines per CTA of the x kernels: the tuned tile if set, else 256 threads;
 // at most 1024 threads, the shared-memory cap and the line pairs there are
 static int x_lines(const Problem *p, int G, long ex_bytes, int npairs) {
     int P = p->tile[0] > 0 ? p->tile[0] : 256 / G;
-    P = std::min<long>(P, std::min<long>(1024 / G, kSmemCap / ex_bytes));
+    P = std::min<long>(P, std::min<long>(kMaxThreads / G, kSmemCap / ex_bytes));
     return std::max(1, std::min(P, npairs));
 }
 
@@ -646,8 +648,8 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
                 int TX = pow2_le(std::min<long>(256 / G, 16));
                 if (p->tile[1] > 0)
-                    TX = std::max(1, std::min<int>(p->tile[1],
-                                                   (int)std::min<long>(1024 / G, kSmemCap / (Shape<N1, N2>::EX * (long)cs))));
+                    TX = std::max(1, std::min<int>(p->tile[1], (int)std::min<long>(kMaxThreads / G,
+                                                                                    kSmemCap / (Shape<N1, N2>::EX * (long)cs))));
                 dim3 g((d.Wx + TX - 1) / TX, d.nz, F);
                 const size_t sm = (size_t)TX * Shape<N1, N2>::EX * cs;
                 if (inv) {
@@ -680,8 +682,9 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
                 int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));
                 if (p->tile[2] > 0)
-                    TX = std::max(1, std::min<int>(p->tile[2], (int)std::min<long>(512 / G, (kSmemCap - (long)G * G * cs) /
-                                                                                         (2 * per_col))));
+                    TX = std::max(1, std::min<int>(p->tile[2], (int)std::min<long>(kMaxThreads / (2 * G),
+                                                                                    (kSmemCap - (long)G * G * cs) /
+                                                                                        (2 * per_col))));
                 dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
                 const size_t sm = 2 * TX * per_col + (size_t)G * G * cs;   // + twiddle table
                 if (back) {
