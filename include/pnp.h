@@ -296,6 +296,14 @@ int pnp_poll(pnp_server *s, uint64_t ticket, double *phi_out, double *rho_out, p
 int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
 
 /* Static message for an error code. */
+/* Failure-path self-test with no counterpart in the paper: launches one
+ * kernel that waits on an mbarrier nothing ever completes, with the same
+ * globally-timed bounded wait the tensor-core kernels use, limited to
+ * limit_ms (0 < limit_ms <= 1000).  Returns PNP_ERR_TIMEOUT when the wait
+ * gave up and reported it (the expected result), PNP_ERR_INVALID for a bad
+ * limit, PNP_ERR_CUDA on a runtime error.  The device stays usable. */
+int pnp_selftest_bounded_wait(double limit_ms);
+
 const char *pnp_error_string(int code);
 
 #ifdef __cplusplus

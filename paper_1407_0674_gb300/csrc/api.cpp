@@ -280,6 +280,8 @@ const char *pnp_stage_name(int stage) {
     return names[stage];
 }
 
+int pnp_selftest_bounded_wait(double limit_ms) { return bounded_wait_probe(limit_ms); }
+
 const char *pnp_error_string(int code) {
     switch (code) {
         case PNP_OK: return "ok";

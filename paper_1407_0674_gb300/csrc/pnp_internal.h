@@ -119,6 +119,9 @@ void octant_transform(const Stencil &st, const int L[3], const bool odd[3], doub
 double bjerrum_length_h(double T, double eps_r, double h_nm);
 void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu);
 
+// ypass_tc.cu: a kernel whose bounded mbarrier wait nothing completes
+int bounded_wait_probe(double limit_ms);
+
 // autotune.cu: time candidate padded lengths and tiles, keep the fastest
 int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *why);
 

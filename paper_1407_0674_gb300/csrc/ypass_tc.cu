@@ -87,7 +87,8 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         : "memory");
 }
 
-__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity,
+                                           unsigned long long limit_ns = kWaitLimitNs) {
     unsigned long long t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     for (;;) {
@@ -102,7 +103,7 @@ __device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
         if (ok) return true;
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > kWaitLimitNs) return false;
+        if (t - t0 > limit_ns) return false;
     }
 }
 
@@ -269,7 +270,40 @@ __global__ void __launch_bounds__(kThreads) k_ypass_tc(const float2 *__restrict_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// Failure-path check of the bounded wait: one thread waits on an mbarrier
+// that nothing arrives on, gives up after limit_ns and records the timeout
+// the way the pipeline kernels do.
+__global__ void k_bounded_wait_probe(unsigned long long limit_ns, int *flag) {
+    __shared__ uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
+    if (!wait_phase(b, 0, limit_ns)) atomicOr(flag, kFlagTimeout);
+}
+
 }  // namespace tcy
+
+int bounded_wait_probe(double limit_ms) {
+    if (!(limit_ms > 0) || limit_ms > 1000.0) return PNP_ERR_INVALID;
+    int *d_flag = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = dmalloc((void **)&d_flag, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        tcy::k_bounded_wait_probe<<<1, 1, 0, st>>>((unsigned long long)(limit_ms * 1e6), d_flag);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (d_flag) dfree(d_flag, st);
+    if (st) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    return (h & kFlagTimeout) ? PNP_ERR_TIMEOUT : PNP_OK;
+}
 
 // Real form of the 16-point DFT (forward: exp(-2 pi i n k / 16); inverse:
 // conjugate) split into TF32 hi and lo parts: out[dir][hi/lo][j][k] with

@@ -127,6 +127,7 @@ def lib():
         L.pnp_poll.argtypes = [vp, ctypes.c_uint64, _dp, _dp, ctypes.POINTER(Stats)]
         L.pnp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
+        L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -209,6 +210,12 @@ class DescHolder:
         d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         self.desc = d
+
+
+def selftest_bounded_wait(limit_ms):
+    """pnp_selftest_bounded_wait: a device wait nothing completes, limited to
+    limit_ms; returns the code (ERR_TIMEOUT expected)."""
+    return lib().pnp_selftest_bounded_wait(float(limit_ms))
 
 
 def excess_mu_noalloc(spec, d_rho, d_mu, stream=None):

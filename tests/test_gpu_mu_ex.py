@@ -114,6 +114,38 @@ def test_tensor_core_y_pass(pnp, shape):
     assert not np.array_equal(mutc, mu32)       # the tensor-core path ran
 
 
+def test_generic_fft_length_144(pnp):
+    """144 = 2^4 3^2 has no register shape: the y axis runs the shared-memory
+    Stockham FFT (radix 4, 4, 3, 3) between register-FFT x and z axes."""
+    spec, rho = mu_microbench(shape=(12, 9, 10))
+    spec.fft_len = (32, 144, 16)
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (32, 144, 16)
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+
+
+def test_mixed_grid_sampled(pnp):
+    """A 64 x 48 x 40 grid with the default plan, on sampled points including
+    corners and faces."""
+    spec, rho = mu_microbench(shape=(64, 48, 40))
+    nx, ny, nz = 64, 48, 40
+    rng = np.random.default_rng(1)
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, 3), (nx // 2, 0, nz // 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, (nx, ny, nz))) for _ in range(16)]
+    flat = np.array([(z * ny + y) * nx + x for x, y, z in pts])
+    ref = oracle.excess_mu_sampled(spec, rho, flat)
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="fp64").reshape(3, -1)
+    for i in range(3):
+        assert np.abs(mu[i, flat] - ref[i]).max() / np.abs(mu[i]).max() <= FP64_TOL
+
+
 def test_explicit_odd_lengths(pnp):
     """Padded lengths with radix-3 and radix-5 stages (x even, y/z odd)."""
     spec, rho = mu_microbench(shape=(12, 10, 11))
