@@ -32,6 +32,12 @@ cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st) {
         });
     cudaError_t e = cudaMallocAsync(ptr, bytes, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        // an allocation failure is not sticky: clear it so the next launch's
+        // status check does not report it again
+        if (e == cudaErrorMemoryAllocation) cudaGetLastError();
+        *ptr = nullptr;
+    }
     return e;
 }
 
