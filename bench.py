@@ -6,9 +6,9 @@ lognormal(0, 0.1), seed 2), zero-padded to 256^3, through the C ABI
 (pnp_excess_mu_device) with inputs resident in device memory.
 
 Prints one JSON line (rank 0).  Metric: mu_ex Gpoints/s = output grid points /
-time, against the HBM roofline.  The headline is the FP32-FFT path with FP64
-derivatives (error against the FP64 path stated in the line, below 1e-6 on
-this workload); the plain FP64 form, the double-float FFT (FP64 accuracy) and
+time, against the HBM roofline.  The headline is the FP32-FFT path with the
+singular terms of the FMT derivatives in FP64 (error against the FP64 path
+stated in the line, below 1e-6 on this workload); the plain FP64 form, the double-float FFT (FP64 accuracy) and
 the 3xTF32 tensor-core variant are reported beside it, each with its error.
 `e2e` times pnp_excess_mu with host buffers (pinned), host->device and
 device->host copies inside the timed region.
@@ -223,8 +223,9 @@ PROFILED_TRAFFIC = {
 
 DTYPE = {"fp64": "f64",
          "df64": "df64 (FFT values as FP32 pairs, ~48-bit; FP64 derivatives)",
-         "fp32": "f32 FFT / f64 derivatives",
-         "tf32split": "f32 FFT with the y-axis radix-16 DFT stages as 3xTF32 tensor-core products / f64 derivatives"}
+         "fp32": "f32 FFT / f64 singular terms of the FMT derivatives",
+         "tf32split": "f32 FFT with the y-axis radix-16 DFT stages as 3xTF32 tensor-core products / "
+                      "f64 singular terms of the FMT derivatives"}
 VARIANT_NAME = {"fp64": "fp64_plain", "df64": "df64_fft", "fp32": "fp32_fft", "tf32split": "tf32split_fft"}
 # error bound each variant is tested to against the oracle (normwise per species)
 ERROR_BOUND = {"fp64": 1e-10, "df64": 1e-10, "fp32": 2e-5, "tf32split": 5e-5}

@@ -55,8 +55,11 @@ enum {
  * PERIODIC or NOFLUX (Sec 2.2, with the paper's y axis as z). */
 enum { PNP_BC_PERIODIC = 0, PNP_BC_DIRICHLET = 1, PNP_BC_NOFLUX = 2 };
 
-/* arithmetic of the FFT convolutions; the FMT derivatives, the Gummel update,
- * its norms and the linear solves are FP64 in every variant.  PNP_PREC_DF64
+/* arithmetic of the FFT convolutions; the Gummel update, its norms and the
+ * linear solves are FP64 in every variant, and so are the FMT derivatives
+ * except that the FP32 and TF32SPLIT variants evaluate only their singular
+ * functions of n3 (ln(1 - n3), the powers of 1/(1 - n3)) in FP64 and the
+ * products with the other weighted densities in FP32.  PNP_PREC_DF64
  * carries each FFT value as an unevaluated sum of two FP32 numbers (about 48
  * significant bits) and runs the transforms on the FP32 pipes, which GB300
  * executes ~58x faster than FP64; it meets the FP64 accuracy bar of mu_ex.

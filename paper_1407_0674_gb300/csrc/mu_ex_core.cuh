@@ -146,6 +146,43 @@ __global__ void k_dphi_fields(V *__restrict__ f, size_t N, int *__restrict__ fla
     if (bad) atomicOr(flag, kFlagPacking);
 }
 
+// The same derivatives for FP32 fields: the functions that are singular at
+// packing, ln(1 - n3) and the powers of 1/(1 - n3), in FP64; their products
+// with the other weighted densities in FP32 (the fields carry FP32 rounding
+// already).  Internal linkage: one copy per translation unit.
+static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int *__restrict__ flag) {
+    constexpr float k8pi = (float)(1.0 / (8.0 * M_PI)), k12pi = (float)(1.0 / (12.0 * M_PI)),
+                    k4pi = (float)(1.0 / (4.0 * M_PI));
+    bool bad = false;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        float n[kNumWeighted], psi[kNumWeighted];
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) n[a] = f[a * N + p];
+        const double n3 = (double)n[3];
+        const double gd = 1.0 / (1.0 - n3);
+        const float g = (float)gd, g2 = (float)(gd * gd), g3 = (float)(gd * gd * gd);
+        const float n0 = n[0], n1 = n[1], n2 = n[2];
+        const float v1v2 = n[4] * n[7] + n[5] * n[8] + n[6] * n[9];
+        const float v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
+        psi[0] = (float)(-log1p(-n3));
+        psi[1] = n2 * g;
+        psi[2] = n1 * g + (n2 * n2 - v2v2) * g2 * k8pi;
+        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0f * n2 * v2v2) * g3 * k12pi;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            psi[4 + c] = -n[7 + c] * g;
+            psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * g2 * k4pi;
+        }
+        bool ok = n3 < 1.0;
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a]);
+        if (!ok) bad = true;
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) f[a * N + p] = psi[a];
+    }
+    if (bad) atomicOr(flag, kFlagPacking);
+}
+
 }  // namespace pnp
 
 #include "mu_ex_reg.cuh"
@@ -722,7 +759,11 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 dim3 g((d.npairs + P - 1) / P, d.nz, kNumWeighted);
                 ensure_smem<k_xinv_raw_r<T, N1, N2, V>>();
                 k_xinv_raw_r<T, N1, N2, V><<<g, P * G, sm, st>>>(A, nf, d, twx, P);
-                k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag);
+                if constexpr (std::is_same<V, float>::value)
+                    k_dphi_fields_mixed<<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N,
+                                                                                                   p->d_flag);
+                else
+                    k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag);
                 ensure_smem<k_xfwd_r<T, N1, N2, V>>();
                 k_xfwd_r<T, N1, N2, V><<<g, P * G, sm, st>>>(nf, N, A, d, twx, P);
             } else {
