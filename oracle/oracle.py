@@ -74,6 +74,7 @@ class _Problem(ctypes.Structure):
         ("lin_max_iter", ctypes.c_int),
         ("rho_mix", ctypes.c_int),
         ("screened", ctypes.c_int),
+        ("fmt", ctypes.c_int),
     ]
 
 
@@ -101,6 +102,11 @@ def _declare(L):
     L.oracle_np_flux.argtypes = [P, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
     L.oracle_gummel.restype = ctypes.c_int
     L.oracle_gummel.argtypes = [P, _dp, _dp, _dp, _dp, _ip, _dp, ctypes.POINTER(ctypes.c_long)]
+    L.oracle_dphi_fmt.restype = ctypes.c_long
+    L.oracle_dphi_fmt.argtypes = [ctypes.c_int, ctypes.c_long, _dp, _dp]
+    L.oracle_fhs_fmt.restype = ctypes.c_double
+    L.oracle_fhs_fmt.argtypes = [ctypes.c_int, ctypes.c_long, _dp]
+    L.oracle_bulk_mu_fmt.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     L.oracle_equilibrium.restype = ctypes.c_int
     L.oracle_equilibrium.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _ip,
                                      ctypes.POINTER(ctypes.c_double)]
@@ -161,6 +167,7 @@ class Problem:
         st.lin_max_iter = lin_max_iter
         st.rho_mix = int(getattr(spec, "rho_mix", 0))
         st.screened = 1 if getattr(spec, "screened_poisson", False) else 0
+        st.fmt = int(getattr(spec, "fmt", 0))
         self.st = st
 
     @property
@@ -200,19 +207,20 @@ def weighted_densities(spec, rho=None, wave=None):
     return out
 
 
-def dphi(n):
-    """The ten FMT derivatives of Sec 2.3.1 (Rosenfeld).  Returns (psi, bad)."""
+def dphi(n, fmt=0):
+    """The ten FMT derivatives of Sec 2.3.1 (fmt 0 Rosenfeld, 1 White Bear).
+    Returns (psi, bad)."""
     n = _f64(n)
     N = n.size // 10
     psi = np.zeros_like(n)
-    bad = lib().oracle_dphi(N, _ptr(n), _ptr(psi))
+    bad = lib().oracle_dphi_fmt(int(fmt), N, _ptr(n), _ptr(psi))
     return psi, int(bad)
 
 
-def fhs(n):
-    """sum over the grid of the Rosenfeld Phi (h = 1), Sec 2.3.1."""
+def fhs(n, fmt=0):
+    """sum over the grid of Phi (h = 1), Sec 2.3.1 (fmt 0 Rosenfeld, 1 White Bear)."""
     n = _f64(n)
-    return lib().oracle_fhs(n.size // 10, _ptr(n))
+    return lib().oracle_fhs_fmt(int(fmt), n.size // 10, _ptr(n))
 
 
 def mu_hs(spec, psi):
@@ -262,12 +270,12 @@ def excess_mu_sampled(spec, rho, flat_idx):
     return out
 
 
-def bulk_mu(R, rho_b):
+def bulk_mu(R, rho_b, fmt=0):
     """Reservoir mu_ex: dPhi/dn at bulk n times the weight integrals."""
     R = _f64(R)
     rb = _f64(rho_b)
     out = np.zeros(len(R))
-    lib().oracle_bulk_mu(len(R), _ptr(R), _ptr(rb), _ptr(out))
+    lib().oracle_bulk_mu_fmt(int(fmt), len(R), _ptr(R), _ptr(rb), _ptr(out))
     return out
 
 

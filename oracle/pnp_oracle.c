@@ -221,6 +221,7 @@ typedef struct {
                                      step changes sign, else grown 10% up to l2 */
     int screened;              /* Gummel Poisson step: 0 linear solve, 1 one Newton step
                                   with the densities' Boltzmann dependence on phi */
+    int fmt;                   /* 0 Rosenfeld (Sec 2.3.1), 1 White Bear (MFMT) */
 } oracle_problem;
 
 static grid_t cdft_grid(const oracle_problem *p)
@@ -342,6 +343,86 @@ long oracle_dphi(long N, const double *n, double *psi)
         bad += flagged;
     }
     return bad;
+}
+
+/* White Bear (modified FMT) version of Phi, the variant Sec 2.3.1 names
+ * beside Rosenfeld's: the n2^3 term carries
+ *   phi3(x) = [x + (1-x)^2 ln(1-x)] / [x^2 (1-x)^2] / (36 pi)
+ * instead of 1/(24 pi (1-x)^2).  phi3 and its derivative are taken from the
+ * closed form for |x| >= 0.05 and from their power series
+ * phi3(x) = sum_k (k+1)(k+3)/(k+2) x^k below (the closed form cancels as
+ * x -> 0, and x = 0 off the domain); 25 terms leave < 1e-29.              */
+static void wb_phi3(double x, double *f, double *df)
+{
+    if (fabs(x) < 0.05) {
+        double v = 0.0, d = 0.0;
+        for (int k = 24; k >= 0; --k) v = v * x + (double)(k + 1) * (k + 3) / (k + 2);
+        for (int k = 24; k >= 1; --k) d = d * x + (double)k * (k + 1) * (k + 3) / (k + 2);
+        *f = v;
+        *df = d;
+        return;
+    }
+    double o = 1.0 - x, L = log(o);
+    double num = x + o * o * L, den = x * x * o * o;
+    double dnum = x - 2.0 * o * L, dden = 2.0 * x * o * (1.0 - 2.0 * x);
+    *f = num / den;
+    *df = (dnum * den - num * dden) / (den * den);
+}
+
+static double phi_white_bear(const double *a)
+{
+    double n0 = a[0], n1 = a[1], n2 = a[2], n3 = a[3];
+    double v1v2 = a[4] * a[7] + a[5] * a[8] + a[6] * a[9];
+    double v2v2 = a[7] * a[7] + a[8] * a[8] + a[9] * a[9];
+    double o = 1.0 - n3, f, df;
+    wb_phi3(n3, &f, &df);
+    return -n0 * log(o) + (n1 * n2 - v1v2) / o + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * f / (36.0 * M_PI);
+}
+
+/* The ten partial derivatives of the White Bear Phi (same order as
+ * oracle_dphi).  Returns the number of points with a packing error.      */
+long oracle_dphi_wb(long N, const double *n, double *psi)
+{
+    long bad = 0;
+    for (long pt = 0; pt < N; ++pt) {
+        double n0 = n[0 * N + pt], n1 = n[1 * N + pt], n2 = n[2 * N + pt], n3 = n[3 * N + pt];
+        double v1[3] = {n[4 * N + pt], n[5 * N + pt], n[6 * N + pt]};
+        double v2[3] = {n[7 * N + pt], n[8 * N + pt], n[9 * N + pt]};
+        int flagged = !(n3 < 1.0);
+        double o = 1.0 - n3, f = 0.0, df = 0.0;
+        if (!flagged) wb_phi3(n3, &f, &df);
+        double v1v2 = v1[0] * v2[0] + v1[1] * v2[1] + v1[2] * v2[2];
+        double v2v2 = v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2];
+        psi[0 * N + pt] = -log(o);
+        psi[1 * N + pt] = n2 / o;
+        psi[2 * N + pt] = n1 / o + (n2 * n2 - v2v2) * f / (12.0 * M_PI);
+        psi[3 * N + pt] = n0 / o + (n1 * n2 - v1v2) / (o * o)
+                          + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * df / (36.0 * M_PI);
+        for (int c = 0; c < 3; ++c) {
+            psi[(4 + c) * N + pt] = -v2[c] / o;
+            psi[(7 + c) * N + pt] = -v1[c] / o - n2 * v2[c] * f / (6.0 * M_PI);
+        }
+        for (int a = 0; a < 10; ++a)
+            if (!isfinite(psi[a * N + pt])) flagged = 1;
+        bad += flagged;
+    }
+    return bad;
+}
+
+long oracle_dphi_fmt(int fmt, long N, const double *n, double *psi)
+{
+    return fmt == 1 ? oracle_dphi_wb(N, n, psi) : oracle_dphi(N, n, psi);
+}
+
+double oracle_fhs_fmt(int fmt, long N, const double *n)
+{
+    double F = 0.0;
+    double a[10];
+    for (long pt = 0; pt < N; ++pt) {
+        for (int k = 0; k < 10; ++k) a[k] = n[k * N + pt];
+        F += fmt == 1 ? phi_white_bear(a) : phi_rosenfeld(a);
+    }
+    return F;
 }
 
 /* Free energy h^3 sum_Omega Phi(n) (h = 1); used by the adjoint checks.   */
@@ -469,7 +550,7 @@ long oracle_excess_mu(const oracle_problem *p, const double *rho, double *mu)
     double *rs = malloc(sizeof(double) * N);
     double *msh = malloc(sizeof(double) * p->s * N);
     oracle_weighted_densities(p, rho, n, 0, 0.0, 0);
-    long bad = oracle_dphi(N, n, psi);
+    long bad = oracle_dphi_fmt(p->fmt, N, n, psi);
     oracle_mu_hs(p, psi, mu);
     oracle_site_density(p, rs);
     oracle_mu_sh(p, rs, msh);
@@ -544,7 +625,7 @@ void oracle_excess_mu_sampled(const oracle_problem *p, const double *rho, int ns
     for (long pt = 0; pt < N; ++pt) {
         if (!mask[pt]) continue;
         for (int k = 0; k < 10; ++k) a[k] = n[k * N + pt];
-        oracle_dphi(1, a, b);
+        oracle_dphi_fmt(p->fmt, 1, a, b);
         for (int k = 0; k < 10; ++k) psi[k * N + pt] = b[k];
     }
     double *rs = 0;
@@ -614,7 +695,7 @@ void oracle_excess_mu_sampled(const oracle_problem *p, const double *rho, int ns
 
 /* Bulk mu_ex of the uniform reservoir: dPhi/dn_a at the bulk weighted
  * densities times the weight integrals (1, R, 4 pi R^2, 4 pi R^3 / 3).    */
-void oracle_bulk_mu(int s, const double *R, const double *rho_b, double *mu_b)
+void oracle_bulk_mu_fmt(int fmt, int s, const double *R, const double *rho_b, double *mu_b)
 {
     double a[10] = {0}, psi[10];
     for (int i = 0; i < s; ++i) {
@@ -623,10 +704,15 @@ void oracle_bulk_mu(int s, const double *R, const double *rho_b, double *mu_b)
         a[2] += rho_b[i] * 4.0 * M_PI * R[i] * R[i];
         a[3] += rho_b[i] * 4.0 * M_PI * R[i] * R[i] * R[i] / 3.0;
     }
-    oracle_dphi(1, a, psi);
+    oracle_dphi_fmt(fmt, 1, a, psi);
     for (int i = 0; i < s; ++i)
         mu_b[i] = psi[0] + R[i] * psi[1] + 4.0 * M_PI * R[i] * R[i] * psi[2]
                   + 4.0 * M_PI * R[i] * R[i] * R[i] / 3.0 * psi[3];
+}
+
+void oracle_bulk_mu(int s, const double *R, const double *rho_b, double *mu_b)
+{
+    oracle_bulk_mu_fmt(0, s, R, rho_b, mu_b);
 }
 
 /* ------------------------------------------------------------------ */
@@ -954,7 +1040,7 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
     /* rho_mix 3: per-point relaxation factor and last step in ln rho */
     double *lam = malloc(sizeof(double) * s * N), *prev = calloc((size_t)s * N, sizeof(double));
     for (long k = 0; k < s * N; ++k) lam[k] = p->lambda_rho;
-    oracle_bulk_mu(s, p->R, p->rho_b, mub);
+    oracle_bulk_mu_fmt(p->fmt, s, p->R, p->rho_b, mub);
     if (phi0) memcpy(phi, phi0, sizeof(double) * N);
     else
         for (long k = 0; k < N; ++k) {
@@ -1051,7 +1137,7 @@ int oracle_equilibrium(const oracle_problem *p, double lam, double tol, int max_
     double *b = malloc(sizeof(double) * N), *Aphi = malloc(sizeof(double) * N), *dphi = malloc(sizeof(double) * N);
     fdop_t A = fd_alloc(p);
     poisson_operator(p, &A);
-    oracle_bulk_mu(s, p->R, p->rho_b, mub);
+    oracle_bulk_mu_fmt(p->fmt, s, p->R, p->rho_b, mub);
     for (long k = 0; k < N; ++k) {
         int z = (int)(k / plane);
         phi[k] = p->phi_lo + (p->phi_hi - p->phi_lo) * (z + 1.0) / (p->nz + 1.0);

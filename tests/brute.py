@@ -141,3 +141,16 @@ def phi_rosenfeld(n):
     o = 1 - n3
     return (-n0 * np.log(o) + n1 * n2 / o + n2 ** 3 / (24 * np.pi * o ** 2)
             - (v1 * v2).sum(0) / o - n2 * (v2 * v2).sum(0) / (8 * np.pi * o ** 2))
+
+
+def phi_white_bear(n):
+    """White Bear (MFMT) Phi, numpy, complex-safe, closed form in n3 (valid away
+    from n3 = 0): the n2^3 term is (n2^3 - 3 n2 v2.v2) phi3(n3) / (36 pi) with
+    phi3(x) = [x + (1-x)^2 ln(1-x)] / [x^2 (1-x)^2]."""
+    n0, n1, n2, n3 = n[0], n[1], n[2], n[3]
+    v1 = n[4:7]
+    v2 = n[7:10]
+    o = 1 - n3
+    phi3 = (n3 + o ** 2 * np.log(o)) / (n3 ** 2 * o ** 2)
+    return (-n0 * np.log(o) + (n1 * n2 - (v1 * v2).sum(0)) / o
+            + (n2 ** 3 - 3 * n2 * (v2 * v2).sum(0)) * phi3 / (36 * np.pi))

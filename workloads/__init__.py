@@ -63,6 +63,7 @@ class ProblemSpec:
     eq_tol: float = 0.0                      # its stopping residual (0 = library default)
     eq_max_iter: int = 0                     # its iteration cap (0 = library default)
     screened_poisson: bool = False           # Gummel Poisson step as one screened Newton step
+    fmt: int = 0                             # hard-sphere functional: 0 Rosenfeld, 1 White Bear (MFMT)
 
     @property
     def s(self) -> int:
