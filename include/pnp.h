@@ -105,6 +105,13 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * as lambda_phi lambda_rho kappa^2 / k^2), the screened one is not. */
 #define PNP_FLAG_SCREENED_POISSON 4u
 
+/* hard-sphere functional (Sec 2.3.1): Rosenfeld's, whose derivatives the
+ * paper prints, or the White Bear (modified FMT) form it names beside it, in
+ * which the n2^3 term carries phi3(n3) / (36 pi),
+ * phi3(x) = [x + (1-x)^2 ln(1-x)] / [x^2 (1-x)^2], instead of
+ * 1 / (24 pi (1 - n3)^2); its bulk limit is the Carnahan-Starling fluid. */
+enum { PNP_FMT_ROSENFELD = 0, PNP_FMT_WHITE_BEAR = 1 };
+
 /* density relaxation of the Gummel update (Sec 3.2): the printed linear form
  * rho <- l2 rho* + (1 - l2) rho, the geometric form rho <- rho (rho* / rho)^l2
  * (equal to first order, positive for large steps), or the geometric form
@@ -149,6 +156,7 @@ typedef struct {
     double eq_tol;                 /* PNP_FLAG_EQUILIBRIUM_INIT: residual that ends the equilibrium stage
                                       (0 -> 1e-6) */
     int eq_max_iter;               /* and its iteration cap (0 -> 1000) */
+    int fmt;                       /* hard-sphere functional, PNP_FMT_* */
 } pnp_problem_desc;
 
 typedef struct {

@@ -40,6 +40,7 @@ struct Dims {
     int Wx;            // Lx / 2 + 1
     int Ox, Oy, Oz;    // octant extents
     int npairs;        // (ny + 1) / 2
+    int fmt;           // hard-sphere functional: PNP_FMT_ROSENFELD or PNP_FMT_WHITE_BEAR
 };
 
 struct SpeciesConst {
@@ -75,6 +76,7 @@ static Dims make_dims(const Problem *p) {
     d.Wx = d.Lx / 2 + 1;
     d.Ox = d.Lx / 2 + 1; d.Oy = d.Ly / 2 + 1; d.Oz = d.Lz / 2 + 1;
     d.npairs = (d.ny + 1) / 2;
+    d.fmt = p->fmt;
     return d;
 }
 
@@ -111,7 +113,32 @@ __device__ __forceinline__ T spec_at(const T *__restrict__ sp, const Dims &d, in
 }
 
 // Rosenfeld FMT derivatives of Sec 2.3.1, FP64.
-__device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double psi[kNumWeighted]) {
+// White Bear n3 function phi3(x) = [x + (1-x)^2 ln(1-x)] / [x^2 (1-x)^2] and
+// its derivative.  Near x = 0 the closed form cancels (and x is exactly 0
+// off the domain), so |x| < 0.05 sums the power series
+// phi3 = sum_k (k+1)(k+3)/(k+2) x^k to x^24.
+__device__ __forceinline__ void wb_phi3(double x, double &f, double &df) {
+    if (fabs(x) < 0.05) {
+        double v = 0.0, d = 0.0;
+#pragma unroll
+        for (int k = 24; k >= 1; --k) {
+            const double c = (double)((k + 1) * (k + 3)) / (double)(k + 2);
+            v = v * x + c;
+            d = d * x + k * c;
+        }
+        f = v * x + 1.5;
+        df = d;
+        return;
+    }
+    const double o = 1.0 - x, L = log(o);
+    f = (x + o * o * L) / (x * x * o * o);
+    df = (x - 2.0 * o * L) / (x * x * o * o) - 2.0 * (1.0 - 2.0 * x) * f / (x * o);
+}
+
+// dPhi/dn_alpha of Rosenfeld's functional (Sec 2.3.1) or of the White Bear
+// form (fmt 1: the n2^3 term carries phi3(n3) / 36 pi instead of
+// 1 / (24 pi (1 - n3)^2)); false at a packing violation.
+__device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double psi[kNumWeighted], int fmt = 0) {
     const double n0 = n[0], n1 = n[1], n2 = n[2], n3 = n[3];
     const double g = 1.0 / (1.0 - n3);
     const double g2 = g * g;
@@ -119,11 +146,22 @@ __device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double ps
     const double v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
     psi[0] = -log1p(-n3);
     psi[1] = n2 * g;
-    psi[2] = n1 * g + (n2 * n2 - v2v2) * g2 * (1.0 / (8.0 * M_PI));
-    psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * g2 * g * (1.0 / (12.0 * M_PI));
-    for (int c = 0; c < 3; ++c) {
-        psi[4 + c] = -n[7 + c] * g;
-        psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * g2 * (1.0 / (4.0 * M_PI));
+    if (fmt == PNP_FMT_WHITE_BEAR) {
+        double f = 0.0, df = 0.0;
+        if (n3 < 1.0) wb_phi3(n3, f, df);
+        psi[2] = n1 * g + (n2 * n2 - v2v2) * f * (1.0 / (12.0 * M_PI));
+        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * df * (1.0 / (36.0 * M_PI));
+        for (int c = 0; c < 3; ++c) {
+            psi[4 + c] = -n[7 + c] * g;
+            psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * f * (1.0 / (6.0 * M_PI));
+        }
+    } else {
+        psi[2] = n1 * g + (n2 * n2 - v2v2) * g2 * (1.0 / (8.0 * M_PI));
+        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0 * n2 * v2v2) * g2 * g * (1.0 / (12.0 * M_PI));
+        for (int c = 0; c < 3; ++c) {
+            psi[4 + c] = -n[7 + c] * g;
+            psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * g2 * (1.0 / (4.0 * M_PI));
+        }
     }
     bool ok = n3 < 1.0;
     for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a]);
@@ -133,13 +171,13 @@ __device__ __forceinline__ bool fmt_dphi(const double n[kNumWeighted], double ps
 // Rosenfeld dPhi/dn (FP64) in place on ten real fields [10][N] of type V:
 // n_alpha in, Psi_alpha out.
 template <typename V>
-__global__ void k_dphi_fields(V *__restrict__ f, size_t N, int *__restrict__ flag) {
+__global__ void k_dphi_fields(V *__restrict__ f, size_t N, int *__restrict__ flag, int fmt) {
     bool bad = false;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
         double n[kNumWeighted], psi[kNumWeighted];
 #pragma unroll
         for (int a = 0; a < kNumWeighted; ++a) n[a] = (double)f[a * N + p];
-        if (!fmt_dphi(n, psi)) bad = true;
+        if (!fmt_dphi(n, psi, fmt)) bad = true;
 #pragma unroll
         for (int a = 0; a < kNumWeighted; ++a) f[a * N + p] = (V)psi[a];
     }
@@ -150,7 +188,7 @@ __global__ void k_dphi_fields(V *__restrict__ f, size_t N, int *__restrict__ fla
 // packing, ln(1 - n3) and the powers of 1/(1 - n3), in FP64; their products
 // with the other weighted densities in FP32 (the fields carry FP32 rounding
 // already).  Internal linkage: one copy per translation unit.
-static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int *__restrict__ flag) {
+static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int *__restrict__ flag, int fmt) {
     constexpr float k8pi = (float)(1.0 / (8.0 * M_PI)), k12pi = (float)(1.0 / (12.0 * M_PI)),
                     k4pi = (float)(1.0 / (4.0 * M_PI));
     bool bad = false;
@@ -160,18 +198,31 @@ static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int 
         for (int a = 0; a < kNumWeighted; ++a) n[a] = f[a * N + p];
         const double n3 = (double)n[3];
         const double gd = 1.0 / (1.0 - n3);
-        const float g = (float)gd, g2 = (float)(gd * gd), g3 = (float)(gd * gd * gd);
+        // coefficient functions of n2^2 (psi2, vector psi) and n2^3 (psi3)
+        float c2, c3, cv;
+        if (fmt == PNP_FMT_WHITE_BEAR) {
+            double fw = 0.0, dfw = 0.0;
+            if (n3 < 1.0) wb_phi3(n3, fw, dfw);
+            c2 = (float)(fw * (1.0 / (12.0 * M_PI)));
+            c3 = (float)(dfw * (1.0 / (36.0 * M_PI)));
+            cv = (float)(fw * (1.0 / (6.0 * M_PI)));
+        } else {
+            c2 = (float)(gd * gd) * k8pi;
+            c3 = (float)(gd * gd * gd) * k12pi;
+            cv = (float)(gd * gd) * k4pi;
+        }
+        const float g = (float)gd, g2 = (float)(gd * gd);
         const float n0 = n[0], n1 = n[1], n2 = n[2];
         const float v1v2 = n[4] * n[7] + n[5] * n[8] + n[6] * n[9];
         const float v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
         psi[0] = (float)(-log1p(-n3));
         psi[1] = n2 * g;
-        psi[2] = n1 * g + (n2 * n2 - v2v2) * g2 * k8pi;
-        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0f * n2 * v2v2) * g3 * k12pi;
+        psi[2] = n1 * g + (n2 * n2 - v2v2) * c2;
+        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - 3.0f * n2 * v2v2) * c3;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             psi[4 + c] = -n[7 + c] * g;
-            psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * g2 * k4pi;
+            psi[7 + c] = -n[4 + c] * g - n2 * n[7 + c] * cv;
         }
         bool ok = n3 < 1.0;
 #pragma unroll
@@ -370,7 +421,7 @@ __global__ void k_xfused(typename vec2<T>::type *__restrict__ A, Dims d, FftAxis
                 n[a] = (double)(h ? v.y : v.x);
             }
             if (inside) {
-                if (!fmt_dphi(n, psi)) bad = 1;
+                if (!fmt_dphi(n, psi, d.fmt)) bad = 1;
             } else {
                 for (int a = 0; a < kNumWeighted; ++a) psi[a] = 0.0;
             }
@@ -760,10 +811,11 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 ensure_smem<k_xinv_raw_r<T, N1, N2, V>>();
                 k_xinv_raw_r<T, N1, N2, V><<<g, P * G, sm, st>>>(A, nf, d, twx, P);
                 if constexpr (std::is_same<V, float>::value)
-                    k_dphi_fields_mixed<<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N,
-                                                                                                   p->d_flag);
+                    k_dphi_fields_mixed<<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(
+                        nf, N, p->d_flag, p->fmt);
                 else
-                    k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag);
+                    k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag,
+                                                                                                p->fmt);
                 ensure_smem<k_xfwd_r<T, N1, N2, V>>();
                 k_xfwd_r<T, N1, N2, V><<<g, P * G, sm, st>>>(nf, N, A, d, twx, P);
             } else {

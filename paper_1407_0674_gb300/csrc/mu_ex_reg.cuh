@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256) k_xfused_r(typename vec2<T>::type *__rest
                     n[a] = (double)(h ? s.y : s.x);
                 }
                 if (x < d.nx && y < d.ny) {
-                    if (!fmt_dphi(n, psi)) bad = true;
+                    if (!fmt_dphi(n, psi, d.fmt)) bad = true;
                 } else {
 #pragma unroll
                     for (int a = 0; a < kNumWeighted; ++a) psi[a] = 0.0;

@@ -264,7 +264,9 @@ double bjerrum_length_h(double T, double eps_r, double h_nm) {
 // Reservoir excess chemical potential: in a uniform fluid every weighted
 // density is rho times the weight's integral, so mu_i = sum_alpha dPhi/dn_alpha
 // * int w_i^alpha with the integrals 1, R, 4 pi R^2, 4 pi R^3 / 3 (Sec 2.3.1).
-void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu) {
+// Reservoir chemical potential mu_b,i = sum_a dPhi/dn_a(bulk n) x (integral of
+// weight a of species i), for the problem's functional.
+void bulk_mu_fmt(const Problem &p, std::vector<double> &mu) {
     double n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     for (int i = 0; i < p.s; ++i) {
         double R = p.R[i], r = p.rho_b[i];
@@ -276,8 +278,31 @@ void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu) {
     double g = 1.0 / (1.0 - n3);
     double d0 = -std::log1p(-n3);
     double d1 = n2 * g;
-    double d2 = n1 * g + n2 * n2 * g * g / (8.0 * M_PI);
-    double d3 = n0 * g + n1 * n2 * g * g + n2 * n2 * n2 * g * g * g / (12.0 * M_PI);
+    double d2, d3;
+    if (p.fmt == PNP_FMT_WHITE_BEAR) {
+        // phi3 and its derivative: series below 0.05, closed form above
+        double f, df;
+        if (std::fabs(n3) < 0.05) {
+            f = 0.0;
+            df = 0.0;
+            double xp = 1.0;
+            for (int k = 0; k <= 24; ++k) {
+                const double c = (double)(k + 1) * (k + 3) / (k + 2);
+                f += c * xp;
+                if (k + 1 <= 24) df += (k + 1) * ((double)(k + 2) * (k + 4) / (k + 3)) * xp;
+                xp *= n3;
+            }
+        } else {
+            const double o = 1.0 - n3, L = std::log(o);
+            f = (n3 + o * o * L) / (n3 * n3 * o * o);
+            df = (n3 - 2.0 * o * L) / (n3 * n3 * o * o) - 2.0 * (1.0 - 2.0 * n3) * f / (n3 * o);
+        }
+        d2 = n1 * g + n2 * n2 * f / (12.0 * M_PI);
+        d3 = n0 * g + n1 * n2 * g * g + n2 * n2 * n2 * df / (36.0 * M_PI);
+    } else {
+        d2 = n1 * g + n2 * n2 * g * g / (8.0 * M_PI);
+        d3 = n0 * g + n1 * n2 * g * g + n2 * n2 * n2 * g * g * g / (12.0 * M_PI);
+    }
     mu.resize(p.s);
     for (int i = 0; i < p.s; ++i) {
         double R = p.R[i];
@@ -302,6 +327,8 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     if (!(d->tol > 0) || d->max_iter < (eq ? 0 : 1))
         return bad("tol must be > 0 and max_iter >= 1 (>= 0 with the equilibrium initial guess)");
     if (d->eq_tol < 0 || d->eq_max_iter < 0) return bad("eq_tol and eq_max_iter must be >= 0");
+    if (d->fmt != PNP_FMT_ROSENFELD && d->fmt != PNP_FMT_WHITE_BEAR) return bad("bad fmt");
+    p->fmt = d->fmt;
     if (d->precision != PNP_PREC_FP64 && d->precision != PNP_PREC_FP32 && d->precision != PNP_PREC_DF64 &&
         d->precision != PNP_PREC_TF32SPLIT)
         return bad("bad precision");
@@ -369,7 +396,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->sw_half = d->sw_half ? 1 : 0;
     p->precision = d->precision;
     p->lin_tol = d->lin_tol;      // 0: adaptive inner tolerance
-    bulk_mu_rosenfeld(*p, p->mu_bulk);
+    bulk_mu_fmt(*p, p->mu_bulk);
     double n3 = 0;
     for (int i = 0; i < p->s; ++i) n3 += p->rho_b[i] * 4.0 * M_PI * std::pow(p->R[i], 3) / 3.0;
     if (!(n3 < 1.0)) return bad("bulk packing fraction must be < 1");

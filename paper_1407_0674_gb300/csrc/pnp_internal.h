@@ -71,6 +71,7 @@ struct Problem {
     int max_iter = 500;
     bool eq_init = false;             // equilibrium initial guess before the Gummel loop
     bool screened = false;            // Gummel Poisson step as one screened Newton step
+    int fmt = 0;                      // PNP_FMT_ROSENFELD or PNP_FMT_WHITE_BEAR
     double eq_tol = 1e-6;
     int eq_max_iter = 1000;
     int quad[3] = {0, 0, 0}, wquad[3] = {0, 0, 0};
@@ -117,7 +118,7 @@ void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil ou
 void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
 void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
 double bjerrum_length_h(double T, double eps_r, double h_nm);
-void bulk_mu_rosenfeld(const Problem &p, std::vector<double> &mu);
+void bulk_mu_fmt(const Problem &p, std::vector<double> &mu);
 
 // ypass_tc.cu: a kernel whose bounded mbarrier wait nothing completes
 int bounded_wait_probe(double limit_ms);

@@ -69,6 +69,7 @@ class Desc(ctypes.Structure):
         ("flags", ctypes.c_uint),
         ("eq_tol", ctypes.c_double),
         ("eq_max_iter", ctypes.c_int),
+        ("fmt", ctypes.c_int),
     ]
 
 
@@ -209,6 +210,7 @@ class DescHolder:
             (FLAG_SCREENED_POISSON if getattr(spec, "screened_poisson", False) else 0)
         d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
+        d.fmt = int(getattr(spec, "fmt", 0))
         self.desc = d
 
 

@@ -251,3 +251,11 @@ def test_adaptive_relaxation_trajectory(pnp):
     spec.rho_mix = 3
     spec.tol, spec.max_iter, spec.lin_tol = 1e-30, 8, 1e-13
     compare(spec, pnp)
+
+
+def test_white_bear_trajectory_matches_oracle(pnp):
+    """Gummel iterations with the White Bear functional (its reservoir mu_b
+    enters the Dirichlet data of the Nernst-Planck solves)."""
+    spec = dilute(0.0, 0.5, mix=1, tol=1e-30, max_iter=5)
+    spec.fmt = 1
+    compare(spec, pnp)

@@ -114,6 +114,25 @@ def test_tensor_core_y_pass(pnp, shape):
     assert not np.array_equal(mutc, mu32)       # the tensor-core path ran
 
 
+@pytest.mark.parametrize("case", ["three_species_16", "film_wells_16", "ragged_13x11x9"])
+def test_white_bear_matches_oracle(pnp, case):
+    """The White Bear functional (PNP_FMT_WHITE_BEAR) in every precision."""
+    spec, rho = CASES[case]()
+    spec.fmt = 1
+    ref, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    with pnp.Problem(spec) as P:
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+    spec.fmt = 0
+    ros, _ = oracle.excess_mu(spec, rho)
+    assert normwise(mu, ros) > 1e-4          # a different functional
+
+
 def test_generic_fft_length_144(pnp):
     """144 = 2^4 3^2 has no register shape: the y axis runs the shared-memory
     Stockham FFT (radix 4, 4, 3, 3) between register-FFT x and z axes."""
