@@ -307,6 +307,19 @@ int pnp_poll(pnp_server *s, uint64_t ticket, double *phi_out, double *rho_out, p
 int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
 
 /* Static message for an error code. */
+/* Nernst-Planck current of species `species` through every z face (Sec 2.1,
+ * Sec 3.1; the paper's conductivity is the current over the applied field):
+ * flux[k+1] = sum over the x-y plane of Dbar_face (rhobar_k - rhobar_k+1)
+ * between planes k and k+1, k = -1 .. nz-1, where the planes -1 and nz are the
+ * Dirichlet reservoirs (rhobar = rho_b exp(q phi_face + mu_b)),
+ * Dbar = D exp(-(q phi + mu_ex)), rhobar = rho exp(q phi + mu_ex) with mu_ex
+ * evaluated in FP64 from rho, and face values the harmonic mean (h = 1).  At
+ * a converged steady state every entry is the same current.  phi
+ * [nz][ny][nx], rho [s][nz][ny][nx] (host, FP64), flux nz + 1 doubles (host).
+ * Needs a Dirichlet z axis.  Errors: PNP_ERR_INVALID (bad species, arrays,
+ * boundaries), PNP_ERR_PACKING, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
+int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double *rho, double *flux);
+
 /* Failure-path self-test with no counterpart in the paper: launches one
  * kernel that waits on an mbarrier nothing ever completes, with the same
  * globally-timed bounded wait the tensor-core kernels use, limited to

@@ -286,6 +286,38 @@ const char *pnp_stage_name(int stage) {
     return names[stage];
 }
 
+int pnp_plane_flux(pnp_problem *h, int species, const double *phi, const double *rho, double *flux) {
+    if (!h || !phi || !rho || !flux) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    if (species < 0 || species >= p->s || p->bc[2] != PNP_BC_DIRICHLET) return PNP_ERR_INVALID;
+    const size_t N = p->npts(), n = N * p->s;
+    for (size_t k = 0; k < n; ++k)
+        if (!(rho[k] >= 0.0) || !std::isfinite(rho[k])) return PNP_ERR_INVALID;
+    for (size_t k = 0; k < N; ++k)
+        if (!std::isfinite(phi[k])) return PNP_ERR_INVALID;
+    if (!p->d_io) {
+        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess)
+            return PNP_ERR_NOMEM;
+        p->device_bytes += sizeof(double) * (2 * n + N);
+    }
+    cudaStream_t st = p->stream;
+    p->last_stream = st;
+    double *d_rho = p->d_io, *d_phi = p->d_io + n, *d_mu = p->d_io + n + N, *d_flux = nullptr;
+    cudaError_t e = dmalloc((void **)&d_flux, sizeof(double) * (p->nz + 1), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rho, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_phi, phi, sizeof(double) * N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
+    int rc = cuda_status(e);
+    if (rc == PNP_OK) rc = mu_ex_enqueue(p, PNP_PREC_FP64, d_rho, d_mu, st);
+    if (rc == PNP_OK) rc = plane_flux(p, species, d_phi, d_mu + (size_t)species * N, d_rho + (size_t)species * N,
+                                      d_flux, st);
+    if (rc == PNP_OK)
+        rc = cuda_status(cudaMemcpyAsync(flux, d_flux, sizeof(double) * (p->nz + 1), cudaMemcpyDeviceToHost, st));
+    dfree(d_flux, st);
+    const int f = read_flag(p, st);
+    return rc ? rc : f;
+}
+
 int pnp_selftest_bounded_wait(double limit_ms) { return bounded_wait_probe(limit_ms); }
 
 const char *pnp_error_string(int code) {

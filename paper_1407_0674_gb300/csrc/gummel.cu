@@ -597,6 +597,48 @@ __global__ void k_final_check(const double *__restrict__ partial, int nb, double
     }
 }
 
+// Nernst-Planck current of one species through every z face (Sec 2.1, 3.1):
+// J_k = sum over the plane of Dbar_face (rhobar_k - rhobar_k+1) between planes
+// k and k+1 (k = -1 .. nz-1; the Dirichlet planes carry the reservoir values),
+// Dbar = D exp(-(q phi + mu)), rhobar = rho exp(q phi + mu), harmonic-mean
+// faces.  One CTA per face, fixed-order reduction.
+__global__ void k_plane_flux(PhysConst c, NpConst s, const double *__restrict__ phi, const double *__restrict__ mu,
+                             const double *__restrict__ rho, double *__restrict__ flux) {
+    __shared__ double sh[256];
+    const int kf = (int)blockIdx.x - 1;
+    const size_t plane = (size_t)c.nx * c.ny;
+    double acc = 0.0;
+    for (size_t t = threadIdx.x; t < plane; t += blockDim.x) {
+        double Da, ra, Db, rb;
+        if (kf < 0) {
+            Da = s.Dlo;
+            ra = s.rlo;
+        } else {
+            const size_t a = (size_t)kf * plane + t;
+            const double e = s.q * phi[a] + mu[a];
+            Da = s.D * exp(-e);
+            ra = rho[a] * exp(e);
+        }
+        if (kf + 1 >= c.nz) {
+            Db = s.Dhi;
+            rb = s.rhi;
+        } else {
+            const size_t b = (size_t)(kf + 1) * plane + t;
+            const double e = s.q * phi[b] + mu[b];
+            Db = s.D * exp(-e);
+            rb = rho[b] * exp(e);
+        }
+        acc += 2.0 * Da * Db / (Da + Db) * (ra - rb);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) flux[blockIdx.x] = sh[0];
+}
+
 // ---------------------------------------------------------------------------
 // equilibrium cDFT initial guess (Sec 3.2, choice of initial guess)
 constexpr int kMaxSpecies = 8;
@@ -1176,6 +1218,20 @@ int gummel_fetch(Problem *p, double *phi, double *rho, void *dev_stats_copy, cud
     if (dev_stats_copy && e == cudaSuccess)
         e = cudaMemcpyAsync(dev_stats_copy, g->stats, sizeof(DevStats), cudaMemcpyDefault, st);
     return cuda_status(e);
+}
+
+int plane_flux(Problem *p, int i, const double *d_phi, const double *d_mu, const double *d_rho, double *d_flux,
+               cudaStream_t st) {
+    PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
+    NpConst nc;
+    nc.D = p->D[i];
+    nc.q = p->q[i];
+    nc.Dlo = p->D[i] * std::exp(-(p->q[i] * p->phi_lo + p->mu_bulk[i]));
+    nc.Dhi = p->D[i] * std::exp(-(p->q[i] * p->phi_hi + p->mu_bulk[i]));
+    nc.rlo = p->rho_b[i] * std::exp(p->q[i] * p->phi_lo + p->mu_bulk[i]);
+    nc.rhi = p->rho_b[i] * std::exp(p->q[i] * p->phi_hi + p->mu_bulk[i]);
+    k_plane_flux<<<p->nz + 1, 256, 0, st>>>(c, nc, d_phi, d_mu, d_rho, d_flux);
+    return cuda_status(cudaGetLastError());
 }
 
 size_t gummel_stats_bytes() { return sizeof(DevStats); }

@@ -137,6 +137,8 @@ int gummel_setup(Problem *p);
 int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho,
                pnp_stats *stats, cudaStream_t st);
 void gummel_free(Problem *p);
+int plane_flux(Problem *p, int species, const double *d_phi, const double *d_mu, const double *d_rho,
+               double *d_flux, cudaStream_t st);
 int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaStream_t st);
 int gummel_fetch(Problem *p, double *phi, double *rho, void *dev_stats_copy, cudaStream_t st);
 size_t gummel_stats_bytes();

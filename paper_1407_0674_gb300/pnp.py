@@ -129,6 +129,7 @@ def lib():
         L.pnp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
+        L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -293,6 +294,15 @@ class Problem:
         if k < 0:
             raise PnpError(k, "pnp_stage_times")
         return {lib().pnp_stage_name(j).decode(): (float(ms[j]), int(n[j])) for j in range(k)}
+
+    def plane_flux(self, species, phi, rho):
+        """pnp_plane_flux: current of one species through the nz + 1 z faces."""
+        p = _f64(phi)
+        r = _f64(rho)
+        assert p.shape == self.shape and r.shape == (self.s,) + self.shape
+        out = np.empty(self.shape[0] + 1)
+        _check(lib().pnp_plane_flux(self.h, int(species), _ptr(p), _ptr(r), _ptr(out)), "pnp_plane_flux")
+        return out
 
     def gummel_solve(self, phi0=None, rho0=None, raise_on_error=True):
         """pnp_gummel_solve; returns (phi, rho, stats dict)."""

@@ -259,3 +259,25 @@ def test_white_bear_trajectory_matches_oracle(pnp):
     spec = dilute(0.0, 0.5, mix=1, tol=1e-30, max_iter=5)
     spec.fmt = 1
     compare(spec, pnp)
+
+
+def test_plane_flux_matches_oracle(pnp):
+    """pnp_plane_flux on a converged biased state: each face's current equals
+    the oracle's discrete flux (from the oracle's own mu_ex), and at steady
+    state every face carries the same current."""
+    spec = dilute(0.0, 0.5, mix=1)
+    with pnp.Problem(spec) as P:
+        phi, rho, st = P.gummel_solve()
+        flux = [P.plane_flux(i, phi, rho) for i in range(spec.s)]
+    assert st["status"] == 0
+    mu, _ = oracle.excess_mu(spec, rho)
+    mub = oracle.bulk_mu(spec.R, spec.rho_b)
+    for i in range(spec.s):
+        rbar = rho[i] * np.exp(spec.q[i] * phi + mu[i])
+        ref = oracle.np_flux(spec, i, phi, mu[i], mub[i], rbar)
+        scale = np.abs(ref).max()
+        assert scale > 0
+        assert np.abs(flux[i] - ref).max() <= 1e-9 * scale
+        assert np.abs(flux[i] - flux[i].mean()).max() <= 1e-4 * scale
+    # the cation and anion currents run in opposite directions
+    assert flux[0].mean() * flux[1].mean() < 0
