@@ -24,6 +24,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -589,9 +590,18 @@ static Launch launch_shape(const Problem *p, int prec) {
     return l;
 }
 
+// function attributes belong to a device's context: set them once per device
+static inline int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+
 template <typename T> static int set_smem_attrs() {
-    static bool done = false;
-    if (done) return PNP_OK;
+    static std::atomic<unsigned long long> done_mask{0};
+    const int dev = current_device();
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done_mask.load() & bit) return PNP_OK;
     const int big = 200 * 1024;
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaFuncSetAttribute(k_xfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -602,7 +612,7 @@ template <typename T> static int set_smem_attrs() {
     e = e ? e : cudaFuncSetAttribute(k_zback<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     e = e ? e : cudaFuncSetAttribute(k_xinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e != cudaSuccess) return cuda_status(e);
-    done = true;
+    done_mask.fetch_or(bit);
     return PNP_OK;
 }
 
@@ -660,11 +670,11 @@ template <typename F> static bool with_shape(int L, F &&f) {
 }
 
 template <auto K> static void ensure_smem() {
-    static const bool done = [] {
-        cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        return true;
-    }();
-    (void)done;
+    static std::atomic<unsigned long long> done_mask{0};
+    const unsigned long long bit = 1ull << (current_device() & 63);
+    if (done_mask.load() & bit) return;
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done_mask.fetch_or(bit);
 }
 
 // dynamic shared memory the register kernels may request (ensure_smem), and

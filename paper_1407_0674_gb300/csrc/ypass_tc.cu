@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "mu_ex_core.cuh"
 
@@ -342,33 +343,48 @@ bool ypass_tc_supported(const Dims &d) { return d.Ly == 256; }
 
 int launch_ypass_tc(bool inv, const float2 *in, float2 *out, const Dims &d, int rows_in, int n_in, int rows_out,
                     int n_out, int F, const float2 *tw, const float *bmat, int *flag, cudaStream_t st) {
-    static int per_sm = 0, sms = 0;
-    if (!per_sm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        for (int k = 0; k < 2; ++k) {
-            auto fn = k ? tcy::k_ypass_tc<true> : tcy::k_ypass_tc<false>;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tcy::kSmemBytes);
-            // without a carveout preference the occupancy query assumes the
-            // smallest shared-memory split that fits one CTA
-            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    // resident CTAs per SM and SM count, once per device
+    static std::mutex mu;
+    static int cached_per_sm[64] = {0}, cached_sms[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = 1, sms = 1;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && cached_per_sm[dev]) {
+            per_sm = cached_per_sm[dev];
+            sms = cached_sms[dev];
+        } else {
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            for (int k = 0; k < 2; ++k) {
+                auto fn = k ? tcy::k_ypass_tc<true> : tcy::k_ypass_tc<false>;
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tcy::kSmemBytes);
+                // without a carveout preference the occupancy query assumes the
+                // smallest shared-memory split that fits one CTA
+                cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+            }
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcy::k_ypass_tc<false>, tcy::kThreads,
+                                                              tcy::kSmemBytes) != cudaSuccess)
+                per_sm = 0;
+            // the same bound from the kernel's registers and the SM's shared memory
+            cudaFuncAttributes fa;
+            int smem_sm = 0;
+            if (cudaFuncGetAttributes(&fa, tcy::k_ypass_tc<false>) == cudaSuccess &&
+                cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+                fa.numRegs > 0) {
+                const int by_regs = 65536 / (fa.numRegs * tcy::kThreads);
+                const int by_smem = smem_sm / (tcy::kSmemBytes + 1024);
+                per_sm = std::max(per_sm, std::min(by_regs, by_smem));
+            }
+            per_sm = std::min(std::max(per_sm, 1), 8);
+            sms = std::max(sms, 1);
+            cudaGetLastError();
+            if (dev >= 0 && dev < 64) {
+                cached_per_sm[dev] = per_sm;
+                cached_sms[dev] = sms;
+            }
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcy::k_ypass_tc<false>, tcy::kThreads,
-                                                          tcy::kSmemBytes) != cudaSuccess)
-            per_sm = 0;
-        // the same bound from the kernel's registers and the SM's shared memory
-        cudaFuncAttributes fa;
-        int smem_sm = 0;
-        if (cudaFuncGetAttributes(&fa, tcy::k_ypass_tc<false>) == cudaSuccess &&
-            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
-            fa.numRegs > 0) {
-            const int by_regs = 65536 / (fa.numRegs * tcy::kThreads);
-            const int by_smem = smem_sm / (tcy::kSmemBytes + 1024);
-            per_sm = std::max(per_sm, std::min(by_regs, by_smem));
-        }
-        per_sm = std::min(std::max(per_sm, 1), 8);
-        cudaGetLastError();
     }
     const long ntiles = (long)((d.Wx + tcy::kCols - 1) / tcy::kCols) * d.nz * F;
     if (ntiles == 0) return PNP_OK;
