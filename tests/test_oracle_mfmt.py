@@ -4,7 +4,7 @@ paper names beside Rosenfeld's (Sec 2.3.1):
 1. Bulk: for one species the White Bear chemical potential is the
    Carnahan-Starling one, mu_ex = (8 eta - 9 eta^2 + 3 eta^3) / (1 - eta)^3 --
    through the reservoir formula and through the full oracle mu_ex on a
-   uniform periodic fluid.
+   uniform periodic fluid; for a mixture, the BMCSL equation of state.
 2. The ten derivatives against a complex step of an independent numpy Phi.
 3. The power series used near n3 = 0 (where the closed form cancels, and n3 is
    exactly 0 off the domain) against the closed form at 50 digits.
@@ -90,3 +90,23 @@ def test_series_near_zero_packing():
     psi, _ = oracle.dphi(n, fmt=1)
     assert psi[2, 0] * 12 * np.pi == pytest.approx(1.5, rel=1e-15)
     assert psi[3, 0] * 36 * np.pi == pytest.approx(8.0 / 3.0, rel=1e-15)
+
+
+def test_mixture_bulk_is_bmcsl():
+    """Three species: the White Bear reservoir chemical potentials equal the
+    derivatives of the Boublik-Mansoori-Carnahan-Starling-Leland excess free
+    energy density (an equation of state, not a density functional),
+    (6/pi) [(xi2^3/xi3^2 - xi0) ln(1 - xi3) + 3 xi1 xi2 / (1 - xi3)
+    + xi2^3 / (xi3 (1 - xi3)^2)],  xi_k = (pi/6) sum_i rho_i d_i^k."""
+    sp = pytest.importorskip("sympy")
+    R = [1.5, 2.0, 3.0]
+    eta = [0.1, 0.12, 0.08]
+    rb = [e / (4.0 / 3.0 * np.pi * r ** 3) for e, r in zip(eta, R)]
+    rho = sp.symbols("r0:3", positive=True)
+    xi = [sp.pi / 6 * sum(rho[i] * (2 * R[i]) ** k for i in range(3)) for k in range(4)]
+    F = (6 / sp.pi) * ((xi[2] ** 3 / xi[3] ** 2 - xi[0]) * sp.log(1 - xi[3]) + 3 * xi[1] * xi[2] / (1 - xi[3])
+                       + xi[2] ** 3 / (xi[3] * (1 - xi[3]) ** 2))
+    sub = {rho[i]: rb[i] for i in range(3)}
+    ref = [float(sp.diff(F, rho[i]).subs(sub)) for i in range(3)]
+    mu = oracle.bulk_mu(R, rb, fmt=1)
+    np.testing.assert_allclose(mu, ref, rtol=1e-13)
