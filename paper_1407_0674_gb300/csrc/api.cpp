@@ -1,6 +1,8 @@
 // C ABI of libpnp_gb300 (include/pnp.h): argument checking, device state
 // lifetime, host<->device staging and error mapping.
+#include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -17,7 +19,25 @@ int cuda_status(cudaError_t e) {
     return PNP_ERR_CUDA;
 }
 
+// Test hook: with PNP_FAULT_ALLOC_AT=k in the environment the k-th device
+// allocation of the process (1-based) reports cudaErrorMemoryAllocation on the
+// host without calling CUDA, so the error paths of every allocation site can
+// be driven without exhausting or faulting a GPU.  Inert when unset.
+static bool injected_alloc_failure() {
+    static const long fail_at = [] {
+        const char *v = std::getenv("PNP_FAULT_ALLOC_AT");
+        return v ? std::atol(v) : 0L;
+    }();
+    static std::atomic<long> count{0};
+    if (fail_at <= 0) return false;
+    return count.fetch_add(1) + 1 == fail_at;
+}
+
 cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st) {
+    if (injected_alloc_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     static std::once_flag pool_once[64];
     int dev = 0;
     cudaGetDevice(&dev);
@@ -63,6 +83,7 @@ void destroy_problem_internal(Problem *p) {
 
 int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why) {
     if (desc && (desc->flags & PNP_FLAG_AUTOTUNE)) return autotune_create(desc, out, why);
+    NvtxRange range("create_problem");
     Problem *p = new (std::nothrow) Problem();
     if (!p) return PNP_ERR_NOMEM;
     int rc = validate_and_copy(desc, p, why);

@@ -99,6 +99,7 @@ void tile_candidates(int G, int axis, std::vector<int> *out) {
 }  // namespace
 
 int autotune_create(const pnp_problem_desc *desc, Problem **out, std::string *why) {
+    NvtxRange range("autotune");
     pnp_problem_desc d = *desc;
     d.flags &= ~PNP_FLAG_AUTOTUNE;
     Problem *best = nullptr;

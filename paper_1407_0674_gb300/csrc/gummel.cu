@@ -989,7 +989,12 @@ int gummel_setup(Problem *p) {
         for (int k = 0; k < 2 && ok; ++k)
             if (cudaStreamCreateWithFlags(&g->cap[k], cudaStreamNonBlocking) != cudaSuccess) ok = false;
     }
-    if (!ok) return PNP_ERR_NOMEM;
+    if (!ok) {
+        // nothing half-built stays behind for a later solve to take as ready
+        cudaStreamSynchronize(p->stream);
+        gummel_free(p);
+        return PNP_ERR_NOMEM;
+    }
     p->device_bytes += g->bytes;
     p->mg_levels = (int)g->lv.size();
     cudaFuncSetAttribute(k_coarse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
@@ -999,7 +1004,9 @@ int gummel_setup(Problem *p) {
     k_poisson_coefs<<<grid_for(N), 256, 0, p->stream>>>(c, g->lv[0].cx, g->lv[0].cy, g->lv[0].cz, g->lv[0].czlo);
     coarsen_all(g, p->stream);
     set_operator(g, true);
-    return cuda_status(cudaStreamSynchronize(p->stream));
+    const int rc = cuda_status(cudaStreamSynchronize(p->stream));
+    if (rc) gummel_free(p);
+    return rc;
 }
 
 void gummel_free(Problem *p) {
@@ -1030,6 +1037,7 @@ void gummel_free(Problem *p) {
 // density update, and k_gummel_check, which ends the loop on convergence,
 // a status error or max_iter.  Works on g->phi and g->rho.
 static int build_graph(Problem *p, int *d_q, double *d_rhof) {
+    NvtxRange range("build_solve_graph");
     GummelState *g = p->gs;
     const size_t N = p->npts();
     const int s = p->s;
@@ -1160,6 +1168,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
 // Enqueue a whole solve on `st` (initial state, the solve graph, stats into
 // g->stats) without waiting.  Builds the graph on first use.
 int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaStream_t st) {
+    NvtxRange range("gummel_launch");
     if (p->bc[2] != PNP_BC_DIRICHLET || p->bc[0] == PNP_BC_DIRICHLET || p->bc[1] == PNP_BC_DIRICHLET)
         return PNP_ERR_INVALID;
     int rc = gummel_setup(p);
@@ -1188,7 +1197,13 @@ int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaSt
         g->keep_q = d_q;
         g->keep_rhof = d_rhof;
         rc = build_graph(p, d_q, d_rhof);
-        if (rc) return rc;
+        if (rc) {
+            dfree(g->keep_q, p->stream);
+            dfree(g->keep_rhof, p->stream);
+            g->keep_q = nullptr;
+            g->keep_rhof = nullptr;
+            return rc;
+        }
     }
     PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
     if (d_phi0) k_copy<<<G, 256, 0, st>>>(g->phi, d_phi0, N);

@@ -132,10 +132,23 @@ static void free_buffers(DeviceBuffers *db, cudaStream_t st) {
 }
 
 // FP64 spectra of every species' kernels, built on the host.
+// Builds into a local set and publishes it in p->buf[0] only when complete:
+// a failed build leaves nothing behind that a later call could take as ready.
+static int build_fp64_into(Problem *p, DeviceBuffers *db);
 static int build_fp64(Problem *p) {
     DeviceBuffers *db = new DeviceBuffers();
     db->prec = PNP_PREC_FP64;
+    const int rc = build_fp64_into(p, db);
+    if (rc) {
+        cudaStreamSynchronize(p->stream);
+        free_buffers(db, p->stream);
+        return rc;
+    }
     p->buf[0] = db;
+    return PNP_OK;
+}
+
+static int build_fp64_into(Problem *p, DeviceBuffers *db) {
     int rc = upload_twiddles(p, db, PNP_PREC_FP64);
     if (rc) return rc;
     const Dims d = make_dims(p);
@@ -184,22 +197,28 @@ int mu_ex_prepare(Problem *p, int prec) {
     if (p->buf[slot]) return PNP_OK;
     int rc = mu_ex_prepare(p, PNP_PREC_FP64);
     if (rc) return rc;
+    // built locally, published only when complete (see build_fp64)
     DeviceBuffers *db = new DeviceBuffers();
     db->prec = prec;
-    p->buf[slot] = db;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(p->stream);
+        free_buffers(db, p->stream);
+        return code;
+    };
     rc = upload_twiddles(p, db, prec);
-    if (rc) return rc;
+    if (rc) return fail(rc);
     const Dims d = make_dims(p);
     const size_t n = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p->s;
     const size_t esz = prec == PNP_PREC_FP32 ? sizeof(float) : sizeof(dd);
-    if (dmalloc(&db->spec, esz * n, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
+    if (dmalloc(&db->spec, esz * n, p->stream) != cudaSuccess) return fail(PNP_ERR_NOMEM);
     db->bytes += esz * n;
     if (prec == PNP_PREC_FP32)
         k_to_float<<<1024, 256, 0, p->stream>>>((const double *)p->buf[0]->spec, (float *)db->spec, n);
     else
         k_to_dd<<<1024, 256, 0, p->stream>>>((const double *)p->buf[0]->spec, (dd *)db->spec, n);
     cudaError_t e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    p->buf[slot] = db;
     p->device_bytes += db->bytes;
     return PNP_OK;
 }
@@ -277,6 +296,7 @@ int mu_ex_setup(Problem *p) {
 int mu_ex_enqueue(Problem *p, int prec, const double *d_rho, double *d_mu, cudaStream_t st) {
     int rc = mu_ex_prepare(p, prec);
     if (rc) return rc;
+    NvtxRange range("mu_ex");
     if (prec == PNP_PREC_FP64) return run_pipeline_fp64(p, p->buf[0], d_rho, d_mu, st);
     if (prec == PNP_PREC_DF64) return run_pipeline_df64(p, p->buf[2], d_rho, d_mu, st);
     return run_pipeline_fp32(p, p->buf[1], d_rho, d_mu, st, prec == PNP_PREC_TF32SPLIT);
@@ -295,7 +315,13 @@ cudaEvent_t StageTimer::get() {
     return e;
 }
 
+// Every stage is also an NVTX range named after the stage (a no-op unless a
+// tracing tool is attached).
+static const char *const kStageNames[kNumStages] = {"x_fwd", "y_fwd", "z_mac", "y_inv", "x_fused",
+                                                    "y_fwd_psi", "z_back", "y_inv_mu", "x_inv"};
+
 void StageTimer::begin(int s, cudaStream_t st) {
+    nvtxRangePushA(s >= 0 && s < kNumStages ? kStageNames[s] : "mu_ex stage");
     if (!enabled) return;
     cudaEvent_t a = get();
     cudaEventRecord(a, st);
@@ -304,6 +330,7 @@ void StageTimer::begin(int s, cudaStream_t st) {
 }
 
 void StageTimer::end(cudaStream_t st) {
+    nvtxRangePop();
     if (!enabled) return;
     cudaEvent_t b = get();
     cudaEventRecord(b, st);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -38,6 +39,14 @@ struct Stencil {
 };
 
 struct DeviceBuffers;   // per-precision device state of the mu_ex pipeline
+
+// scoped NVTX range (tracing tools show the library's phases on the timeline)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kNumStages = 9;
 struct StageTimer {

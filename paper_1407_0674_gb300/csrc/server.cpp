@@ -143,6 +143,7 @@ static void release(pnp_server *s, Request *r) {
 
 // start one admitted request: build the problem and enqueue its whole solve
 static int start(pnp_server *s, Request *r) {
+    NvtxRange range("server_admit");
     std::string why;
     int rc = create_problem_internal(&r->desc, &r->prob, &why);
     if (rc) return rc;
@@ -177,6 +178,7 @@ static int start(pnp_server *s, Request *r) {
 }
 
 static void finish(pnp_server *s, Request *r, int status) {
+    NvtxRange range("server_retire");
     r->t_end = std::chrono::steady_clock::now();
     if (status == PNP_PENDING) {
         gummel_decode_stats(r->h_stats, &r->stats);
