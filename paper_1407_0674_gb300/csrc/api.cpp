@@ -5,6 +5,9 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <limits>
+#include <thread>
+#include <vector>
 #include <mutex>
 #include <new>
 #include <string>
@@ -59,6 +62,39 @@ cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st) {
         *ptr = nullptr;
     }
     return e;
+}
+
+// Checks of caller arrays on the host: branch-free scans (no early exit, so
+// the compiler can vectorise them), split over threads for large arrays.
+// kind 0: finite; 1: >= 0 and finite; 2: > 0 and finite (NaN fails every one).
+static bool scan_values(const double *x, size_t n, int kind) {
+    bool ok = true;
+    const double big = std::numeric_limits<double>::max();
+    if (kind == 0)
+        for (size_t k = 0; k < n; ++k) ok &= (x[k] >= -big) & (x[k] <= big);
+    else if (kind == 1)
+        for (size_t k = 0; k < n; ++k) ok &= (x[k] >= 0.0) & (x[k] <= big);
+    else
+        for (size_t k = 0; k < n; ++k) ok &= (x[k] > 0.0) & (x[k] <= big);
+    return ok;
+}
+
+bool host_values_ok(const double *x, size_t n, int kind) {
+    const size_t kMinPerThread = (size_t)1 << 19;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned T = (unsigned)std::min<size_t>(std::min(hw, 16u), std::max<size_t>(1, n / kMinPerThread));
+    if (T <= 1) return scan_values(x, n, kind);
+    std::vector<std::thread> th;
+    std::vector<char> ok(T, 1);
+    const size_t chunk = (n + T - 1) / T;
+    for (unsigned t = 0; t < T; ++t) {
+        const size_t a = t * chunk, b = std::min(n, a + chunk);
+        th.emplace_back([&, t, a, b] { ok[t] = a < b ? scan_values(x + a, b - a, kind) : 1; });
+    }
+    for (auto &h : th) h.join();
+    for (char v : ok)
+        if (!v) return false;
+    return true;
 }
 
 void dfree(void *ptr, cudaStream_t st) {
@@ -197,8 +233,7 @@ int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precisio
     int prec = resolve_prec(p, precision);
     if (prec < 0) return PNP_ERR_INVALID;
     const size_t n = p->npts() * p->s;
-    for (size_t k = 0; k < n; ++k)
-        if (!(rho[k] >= 0.0) || !std::isfinite(rho[k])) return PNP_ERR_INVALID;
+    if (!host_values_ok(rho, n, 1)) return PNP_ERR_INVALID;
     if (!p->d_io) {
         if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + p->npts()), p->stream) != cudaSuccess)
             return PNP_ERR_NOMEM;
@@ -250,12 +285,8 @@ int pnp_gummel_solve(pnp_problem *h, const double *phi0, const double *rho0, dou
     Problem *p = h->impl;
     auto t0 = std::chrono::steady_clock::now();
     const size_t N = p->npts(), n = N * p->s;
-    if (rho0)
-        for (size_t k = 0; k < n; ++k)
-            if (!(rho0[k] > 0.0) || !std::isfinite(rho0[k])) return fail(PNP_ERR_INVALID);
-    if (phi0)
-        for (size_t k = 0; k < N; ++k)
-            if (!std::isfinite(phi0[k])) return fail(PNP_ERR_INVALID);
+    if (rho0 && !host_values_ok(rho0, n, 2)) return fail(PNP_ERR_INVALID);
+    if (phi0 && !host_values_ok(phi0, N, 0)) return fail(PNP_ERR_INVALID);
     if (!p->d_io) {
         if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess)
             return fail(PNP_ERR_NOMEM);
@@ -312,10 +343,7 @@ int pnp_plane_flux(pnp_problem *h, int species, const double *phi, const double 
     Problem *p = h->impl;
     if (species < 0 || species >= p->s || p->bc[2] != PNP_BC_DIRICHLET) return PNP_ERR_INVALID;
     const size_t N = p->npts(), n = N * p->s;
-    for (size_t k = 0; k < n; ++k)
-        if (!(rho[k] >= 0.0) || !std::isfinite(rho[k])) return PNP_ERR_INVALID;
-    for (size_t k = 0; k < N; ++k)
-        if (!std::isfinite(phi[k])) return PNP_ERR_INVALID;
+    if (!host_values_ok(rho, n, 1) || !host_values_ok(phi, N, 0)) return PNP_ERR_INVALID;
     if (!p->d_io) {
         if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess)
             return PNP_ERR_NOMEM;

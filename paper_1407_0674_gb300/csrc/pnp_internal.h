@@ -160,6 +160,8 @@ int cuda_status(cudaError_t e);
 // problem's stream, completed before return; cudaFreeAsync), so freeing one
 // problem never waits for work of the others.
 cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st);
+// caller arrays: kind 0 finite, 1 >= 0 and finite, 2 > 0 and finite
+bool host_values_ok(const double *x, size_t n, int kind);
 void dfree(void *ptr, cudaStream_t st);
 int create_problem_internal(const pnp_problem_desc *desc, Problem **out, std::string *why);
 void destroy_problem_internal(Problem *p);

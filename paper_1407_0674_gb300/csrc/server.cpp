@@ -296,12 +296,8 @@ int pnp_submit(pnp_server *s, const pnp_problem_desc *desc, const double *phi0, 
     if (probe.bc[2] != PNP_BC_DIRICHLET || probe.bc[0] == PNP_BC_DIRICHLET || probe.bc[1] == PNP_BC_DIRICHLET)
         return PNP_ERR_INVALID;
     const size_t N = probe.npts();
-    if (rho0)
-        for (size_t k = 0; k < N * probe.s; ++k)
-            if (!(rho0[k] > 0.0) || !std::isfinite(rho0[k])) return PNP_ERR_INVALID;
-    if (phi0)
-        for (size_t k = 0; k < N; ++k)
-            if (!std::isfinite(phi0[k])) return PNP_ERR_INVALID;
+    if (rho0 && !host_values_ok(rho0, N * probe.s, 2)) return PNP_ERR_INVALID;
+    if (phi0 && !host_values_ok(phi0, N, 0)) return PNP_ERR_INVALID;
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return PNP_ERR_NOMEM;
     deep_copy(desc, r.get(), phi0, rho0);
