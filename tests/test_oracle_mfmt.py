@@ -110,3 +110,21 @@ def test_mixture_bulk_is_bmcsl():
     ref = [float(sp.diff(F, rho[i]).subs(sub)) for i in range(3)]
     mu = oracle.bulk_mu(R, rb, fmt=1)
     np.testing.assert_allclose(mu, ref, rtol=1e-13)
+
+
+def test_white_bear_zero_bias_gummel_is_its_equilibrium():
+    """With the White Bear functional the Gummel iteration at zero bias and the
+    equilibrium solver (two algorithms; the reservoir mu_b of the functional
+    enters both through the Dirichlet data) reach the same state, which is
+    not the Rosenfeld one."""
+    import dataclasses
+    from test_oracle_equilibrium import small_film
+    spec = dataclasses.replace(small_film(0.0), fmt=1)
+    e = oracle.equilibrium(spec, tol=1e-11, max_iter=3000)
+    g = oracle.gummel(spec)
+    assert e["status"] == 0 and g["status"] == 0
+    rb = spec.rho_b[0]
+    assert np.abs(e["phi"] - g["phi"]).max() <= 1e-9
+    assert max(np.abs(e["rho"][i] - g["rho"][i]).max() / rb for i in range(2)) <= 1e-9
+    ros = oracle.equilibrium(dataclasses.replace(spec, fmt=0), tol=1e-11, max_iter=3000)
+    assert max(np.abs(ros["rho"][i] - e["rho"][i]).max() / rb for i in range(2)) > 1e-4
