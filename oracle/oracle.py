@@ -107,6 +107,8 @@ def _declare(L):
     L.oracle_fhs_fmt.restype = ctypes.c_double
     L.oracle_fhs_fmt.argtypes = [ctypes.c_int, ctypes.c_long, _dp]
     L.oracle_bulk_mu_fmt.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    L.oracle_gummel_anderson.restype = ctypes.c_int
+    L.oracle_gummel_anderson.argtypes = [P, ctypes.c_int, _dp, _dp, _ip, _dp]
     L.oracle_equilibrium.restype = ctypes.c_int
     L.oracle_equilibrium.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _ip,
                                      ctypes.POINTER(ctypes.c_double)]
@@ -339,6 +341,18 @@ def equilibrium(spec, lam=None, tol=1e-10, max_iter=1000, lin_tol=1e-13):
     st = lib().oracle_equilibrium(P.ref, ctypes.c_double(lam), ctypes.c_double(tol), ctypes.c_int(max_iter),
                                   _ptr(phi), _ptr(rho), ctypes.byref(it), ctypes.byref(res))
     return {"phi": phi, "rho": rho, "status": st, "iters": it.value, "residual": res.value, "lB": P.lB}
+
+
+def gummel_anderson(spec, m=3, lin_tol=1e-13):
+    """The relaxed Gummel iteration accelerated by Anderson mixing of depth m
+    on (phi, ln rho).  Returns a dict with phi, rho, status, iters, hist."""
+    P = Problem(spec, lin_tol=lin_tol)
+    phi = np.zeros(P.shape)
+    rho = np.zeros((P.s,) + P.shape)
+    it = ctypes.c_int()
+    hist = np.zeros(max(spec.max_iter, 1))
+    st = lib().oracle_gummel_anderson(P.ref, int(m), _ptr(phi), _ptr(rho), ctypes.byref(it), _ptr(hist))
+    return {"phi": phi, "rho": rho, "status": st, "iters": it.value, "hist": hist[:it.value]}
 
 
 def num_threads() -> int:

@@ -1109,6 +1109,171 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
 }
 
 /* ------------------------------------------------------------------ */
+/* Anderson acceleration of the relaxed Gummel iteration (an extension: the
+ * paper relaxes only).  The base map G is one sweep of oracle_gummel's loop
+ * body (mu_ex, Poisson step, phi relaxation, the NP solves and the density
+ * relaxation) acting on x = (phi, ln rho).  With f = G(x) - x and the last
+ * k <= m differences dX, dF of iterates and residuals,
+ *   gamma = argmin || f - dF gamma ||_2   (normal equations, tiny ridge),
+ *   x <- x + f - (dX + dF) gamma.
+ * If the extrapolated state is unphysical (packing or a non-finite value in
+ * the next sweep) the history is dropped and the plain iterate G(x) taken.
+ * Stops on the residual of the base map, max(|dphi|, max_i |drho_i| / rho_b,i)
+ * < tol, like the plain iteration; so the fixed point is the same.
+ * Returns 0 converged, 1 not converged, 2 packing of a plain iterate.     */
+static int gummel_sweep(const oracle_problem *p, const double *mub, const double *phi, const double *rho,
+                        double *phi_out, double *rho_out, double *mu, double *rb, double *rr)
+{
+    long N = (long)p->nx * p->ny * p->nz;
+    int s = p->s;
+    if (oracle_excess_mu(p, rho, mu) > 0) return 2;
+    memcpy(phi_out, phi, sizeof(double) * N);
+    if (p->screened) poisson_newton_step(p, rho, phi, phi_out);
+    else oracle_poisson(p, rho, phi_out, 0);
+    double r = 0.0;
+    for (long k = 0; k < N; ++k) {
+        double v = p->lambda_phi * phi_out[k] + (1.0 - p->lambda_phi) * phi[k];
+        if (fabs(v - phi[k]) > r) r = fabs(v - phi[k]);
+        phi_out[k] = v;
+    }
+    for (int i = 0; i < s; ++i) {
+        const double *mui = mu + i * N;
+        for (long k = 0; k < N; ++k) rb[k] = rho[i * N + k] * exp(p->q[i] * phi_out[k] + mui[k]);
+        oracle_np(p, i, phi_out, mui, mub[i], rb, 0);
+        for (long k = 0; k < N; ++k) {
+            double rs = rb[k] * exp(-(p->q[i] * phi_out[k] + mui[k]));
+            double old = rho[i * N + k], v;
+            if (p->rho_mix == 0) {
+                v = p->lambda_rho * rs + (1.0 - p->lambda_rho) * old;
+            } else {
+                double step = p->lambda_rho * log(rs / old);
+                if (p->rho_mix >= 2) step = step > 0.2 ? 0.2 : (step < -0.2 ? -0.2 : step);
+                v = old * exp(step);
+            }
+            if (!isfinite(v) || !(v > 0.0)) return 2;
+            double d = fabs(v - old) / p->rho_b[i];
+            if (d > r) r = d;
+            rho_out[i * N + k] = v;
+        }
+    }
+    *rr = r;
+    return 0;
+}
+
+/* solve the k x k system A y = b in place (Gaussian elimination, partial
+ * pivoting); returns 0 on success */
+static int small_solve(int k, double *A, double *b)
+{
+    for (int c = 0; c < k; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < k; ++r) if (fabs(A[r * k + c]) > fabs(A[piv * k + c])) piv = r;
+        if (A[piv * k + c] == 0.0) return 1;
+        if (piv != c) {
+            for (int j = 0; j < k; ++j) { double t = A[c * k + j]; A[c * k + j] = A[piv * k + j]; A[piv * k + j] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < k; ++r) {
+            double f = A[r * k + c] / A[c * k + c];
+            for (int j = c; j < k; ++j) A[r * k + j] -= f * A[c * k + j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = k - 1; c >= 0; --c) {
+        double v = b[c];
+        for (int j = c + 1; j < k; ++j) v -= A[c * k + j] * b[j];
+        b[c] = v / A[c * k + c];
+    }
+    return 0;
+}
+
+int oracle_gummel_anderson(const oracle_problem *p, int m, double *phi, double *rho, int *iters, double *hist)
+{
+    long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
+    int s = p->s;
+    long M = (long)(1 + s) * N;
+    if (m < 1) m = 1;
+    if (m > 16) m = 16;
+    double *mub = malloc(sizeof(double) * s), *mu = malloc(sizeof(double) * s * N), *rb = malloc(sizeof(double) * N);
+    double *x = malloc(sizeof(double) * M), *g = malloc(sizeof(double) * M), *f = malloc(sizeof(double) * M);
+    double *X = malloc(sizeof(double) * M * (m + 1)), *F = malloc(sizeof(double) * M * (m + 1));
+    double *phi_g = malloc(sizeof(double) * N), *rho_g = malloc(sizeof(double) * s * N);
+    double A[16 * 16], bvec[16];
+    oracle_bulk_mu_fmt(p->fmt, s, p->R, p->rho_b, mub);
+    for (long k = 0; k < N; ++k) {
+        int z = (int)(k / plane);
+        phi[k] = p->phi_lo + (p->phi_hi - p->phi_lo) * (z + 1.0) / (p->nz + 1.0);
+    }
+    for (int i = 0; i < s; ++i)
+        for (long k = 0; k < N; ++k) rho[i * N + k] = p->rho_b[i];
+    int hlen = 0, status = 1, n;
+    double rr = 0.0;
+    for (n = 1; n <= p->max_iter; ++n) {
+        int rc = gummel_sweep(p, mub, phi, rho, phi_g, rho_g, mu, rb, &rr);
+        if (rc && hlen > 0 && n > 1) {
+            /* the extrapolated state is unphysical: restart from the last plain iterate */
+            for (long k = 0; k < N; ++k) phi[k] = g[k];
+            for (long k = 0; k < s * N; ++k) rho[k] = exp(g[N + k]);
+            hlen = 0;
+            rc = gummel_sweep(p, mub, phi, rho, phi_g, rho_g, mu, rb, &rr);
+        }
+        if (rc) { status = 2; break; }
+        if (hist) hist[n - 1] = rr;
+        if (rr < p->tol) {
+            memcpy(phi, phi_g, sizeof(double) * N);
+            memcpy(rho, rho_g, sizeof(double) * s * N);
+            status = 0;
+            break;
+        }
+        for (long k = 0; k < N; ++k) { x[k] = phi[k]; g[k] = phi_g[k]; }
+        for (long k = 0; k < s * N; ++k) { x[N + k] = log(rho[k]); g[N + k] = log(rho_g[k]); }
+        for (long k = 0; k < M; ++k) f[k] = g[k] - x[k];
+        /* history ring: keep the last m+1 (x, f) pairs */
+        if (hlen == m + 1) {
+            memmove(X, X + M, sizeof(double) * M * m);
+            memmove(F, F + M, sizeof(double) * M * m);
+            hlen = m;
+        }
+        memcpy(X + M * hlen, x, sizeof(double) * M);
+        memcpy(F + M * hlen, f, sizeof(double) * M);
+        ++hlen;
+        int kd = hlen - 1;
+        double *xn = malloc(sizeof(double) * M);
+        for (long k = 0; k < M; ++k) xn[k] = g[k];
+        if (kd > 0) {
+            /* dF_j = F_{j+1} - F_j, dX_j = X_{j+1} - X_j */
+            double tr = 0.0;
+            for (int a = 0; a < kd; ++a) {
+                for (int b = 0; b <= a; ++b) {
+                    double sum = 0.0;
+                    for (long k = 0; k < M; ++k)
+                        sum += (F[M * (a + 1) + k] - F[M * a + k]) * (F[M * (b + 1) + k] - F[M * b + k]);
+                    A[a * kd + b] = A[b * kd + a] = sum;
+                }
+                tr += A[a * kd + a];
+                double sb = 0.0;
+                for (long k = 0; k < M; ++k) sb += (F[M * (a + 1) + k] - F[M * a + k]) * f[k];
+                bvec[a] = sb;
+            }
+            for (int a = 0; a < kd; ++a) A[a * kd + a] += 1e-12 * tr + 1e-300;
+            if (small_solve(kd, A, bvec) == 0) {
+                for (long k = 0; k < M; ++k) {
+                    double v = x[k] + f[k];
+                    for (int a = 0; a < kd; ++a)
+                        v -= bvec[a] * ((X[M * (a + 1) + k] - X[M * a + k]) + (F[M * (a + 1) + k] - F[M * a + k]));
+                    xn[k] = v;
+                }
+            }
+        }
+        for (long k = 0; k < N; ++k) phi[k] = xn[k];
+        for (long k = 0; k < s * N; ++k) rho[k] = exp(xn[N + k]);
+        free(xn);
+    }
+    if (iters) *iters = n > p->max_iter ? p->max_iter : n;
+    free(mub); free(mu); free(rb); free(x); free(g); free(f); free(X); free(F); free(phi_g); free(rho_g);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* Equilibrium cDFT initial guess (Sec 3.2, choice of initial guess): the
  * static equilibrium of the mobile species in the potential of the
  * electrodes, which then starts the Gummel iteration.  At equilibrium every
