@@ -202,6 +202,16 @@ void pnp_destroy_problem(pnp_problem *p);
 /* Report the plan of a problem. */
 int pnp_get_problem_info(const pnp_problem *p, pnp_problem_info *info);
 
+/* Validate and plan a descriptor on the host only (no device call): the padded
+ * lengths the problem would use without the autotuner (Sec 3.4: L >= n + S on
+ * every zero-extended axis, L = n on periodic ones), the stencil reaches and
+ * the estimated device footprint into *info (mg_levels, tile and tuned_ms are
+ * 0), and, when mu_reservoir is not NULL, the reservoir excess chemical
+ * potentials mu_b,i of the bulk densities (nspecies values, kT) for the
+ * descriptor's functional -- the Dirichlet data of the Nernst-Planck solves.
+ * Errors: PNP_ERR_INVALID (descriptor rejected). */
+int pnp_plan_problem(const pnp_problem_desc *desc, pnp_problem_info *info, double *mu_reservoir);
+
 /* mu_ex,i = mu_hs,i + mu_sh,i (Sec 2.3, Eq. potential-energy-relation) for
  * the densities rho [s][nz][ny][nx] (host, FP64, >= 0).  Weighted densities
  * n_alpha (Sec 2.3.1) by zero-padded FFT correlation with the weight stencils,

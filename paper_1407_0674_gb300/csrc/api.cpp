@@ -227,6 +227,22 @@ int pnp_get_problem_info(const pnp_problem *h, pnp_problem_info *info) {
     return PNP_OK;
 }
 
+int pnp_plan_problem(const pnp_problem_desc *desc, pnp_problem_info *info, double *mu_reservoir) {
+    if (!desc || !info) return PNP_ERR_INVALID;
+    Problem p;
+    std::string why;
+    const int rc = validate_and_copy(desc, &p, &why);
+    if (rc) return rc;
+    std::memset(info, 0, sizeof(*info));
+    for (int c = 0; c < 3; ++c) info->fft_len[c] = p.L[c];
+    info->stencil_halfwidth = p.S;
+    info->well_halfwidth = p.Ssw;
+    info->device_bytes = estimate_device_bytes(p);
+    if (mu_reservoir)
+        for (int i = 0; i < p.s; ++i) mu_reservoir[i] = p.mu_bulk[i];
+    return PNP_OK;
+}
+
 int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precision) {
     if (!h || !rho || !mu_ex) return PNP_ERR_INVALID;
     Problem *p = h->impl;

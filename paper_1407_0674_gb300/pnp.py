@@ -130,6 +130,7 @@ def lib():
         L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
+        L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -213,6 +214,17 @@ class DescHolder:
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         d.fmt = int(getattr(spec, "fmt", 0))
         self.desc = d
+
+
+def plan(spec, precision="fp64"):
+    """pnp_plan_problem: host-only validation and plan of a problem.  Returns
+    (info dict, reservoir mu_b per species)."""
+    dh = DescHolder(spec, precision)
+    i = Info()
+    mu = np.zeros(len(spec.R))
+    _check(lib().pnp_plan_problem(ctypes.byref(dh.desc), ctypes.byref(i), _ptr(mu)), "pnp_plan_problem")
+    return ({"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
+             "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes}, mu)
 
 
 def selftest_bounded_wait(limit_ms):

@@ -1,0 +1,91 @@
+"""The library's host-side planning, tested without a GPU through
+pnp_plan_problem: the reservoir chemical potentials it feeds to the
+Nernst-Planck boundary data (against the oracle, both functionals), the
+padded-length rule (Sec 3.4: L >= n + S on zero-extended axes, L = n on
+periodic ones; the smallest 2^a 3^b 5^c length, even on x, or a register-FFT
+length within 30 % above it) and descriptor rejection."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from workloads import ProblemSpec, bulk_density, film_gummel, mu_microbench
+
+REG = (16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 256)
+
+
+@pytest.fixture(scope="module")
+def pnp():
+    from paper_1407_0674_gb300 import build, pnp as mod
+    import os
+    if not os.path.exists(mod.LIB_PATH):
+        build.build()
+    return mod
+
+
+def smooth235(n):
+    for p in (2, 3, 5):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+def expected_length(n, need, periodic, even):
+    if periodic:
+        return n
+    m = n + need
+    L = m
+    while not (smooth235(L) and (not even or L % 2 == 0)):
+        L += 1
+    for f in REG:
+        if f >= L and f <= L + (3 * L) // 10:
+            return f
+    return L
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("R,eta", [((2.0,), (0.3,)), ((1.5, 2.0, 3.0), (0.1, 0.1, 0.1)), ((1.0, 2.5), (0.05, 0.3))])
+def test_reservoir_mu_matches_oracle(pnp, fmt, R, eta):
+    rb = tuple(bulk_density(e, r) for e, r in zip(eta, R))
+    spec = ProblemSpec(nx=8, ny=8, nz=8, bc=("P", "P", "D"), R=R, q=(0,) * len(R), rho_b=rb, fmt=fmt)
+    _, mu = pnp.plan(spec)
+    np.testing.assert_allclose(mu, oracle.bulk_mu(R, rb, fmt=fmt), rtol=1e-13)
+
+
+@pytest.mark.parametrize("shape,bc", [((128, 128, 128), ("N", "N", "D")), ((20, 10, 12), ("N", "N", "D")),
+                                      ((32, 32, 32), ("P", "P", "D")), ((86, 20, 5), ("N", "N", "D")),
+                                      ((96, 96, 96), ("P", "P", "D")), ((13, 11, 9), ("N", "N", "D"))])
+def test_padded_lengths_follow_the_rule(pnp, shape, bc):
+    spec, _ = mu_microbench(shape=(8, 8, 8))
+    spec = dataclasses.replace(spec, nx=shape[0], ny=shape[1], nz=shape[2], bc=bc)
+    info, _ = pnp.plan(spec)
+    need = int(np.ceil(max(spec.R))) + 1
+    for c in range(3):
+        assert info["fft_len"][c] == expected_length(shape[c], need, bc[c] == "P", c == 0), (c, info)
+    assert info["stencil_halfwidth"] == need and info["device_bytes"] > 0
+
+
+def test_wells_widen_the_padding(pnp):
+    spec = film_gummel(32, 32, 32)
+    info, _ = pnp.plan(spec)
+    assert info["well_halfwidth"] == int(np.ceil(spec.well_outer)) + 1
+    need = max(info["stencil_halfwidth"], info["well_halfwidth"])
+    assert info["fft_len"] == (32, 32, expected_length(32, need, False, False))
+
+
+def test_rejected_descriptors(pnp):
+    spec, _ = mu_microbench(shape=(12, 10, 10))
+    bad = [
+        dataclasses.replace(spec, bc=("P", "N", "D"), nx=13),        # periodic x must be even
+        dataclasses.replace(spec, fft_len=(14, 0, 0)),              # shorter than n + S
+        dataclasses.replace(spec, fft_len=(34, 0, 0)),              # 34 = 2 x 17 is not 2^a 3^b 5^c
+        dataclasses.replace(spec, fmt=2),
+        dataclasses.replace(spec, rho_mix=5),
+        dataclasses.replace(spec, eq_tol=-1.0),
+        dataclasses.replace(spec, rho_b=(0.2, 0.2, 0.2)),            # bulk packing above 1
+    ]
+    for s in bad:
+        with pytest.raises(pnp.PnpError) as e:
+            pnp.plan(s)
+        assert e.value.code == pnp.ERR_INVALID
