@@ -178,6 +178,7 @@ typedef struct {
     int tile[3];                   /* CTA tiles of the register-FFT kernels (x lines, y and z
                                       columns per CTA) fixed by the autotuner; 0 = built-in rule */
     double tuned_ms;               /* mu_ex time the autotuner measured for the chosen plan, 0 if untuned */
+    double bjerrum_h;              /* Bjerrum length e^2 / (4 pi eps0 eps_r kT) in units of h */
 } pnp_problem_info;
 
 typedef struct pnp_problem pnp_problem;

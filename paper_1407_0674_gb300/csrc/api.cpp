@@ -224,6 +224,7 @@ int pnp_get_problem_info(const pnp_problem *h, pnp_problem_info *info) {
     info->mg_levels = p->mg_levels;
     for (int c = 0; c < 3; ++c) info->tile[c] = p->tile[c];
     info->tuned_ms = p->tuned_ms;
+    info->bjerrum_h = p->lB;
     return PNP_OK;
 }
 
@@ -238,6 +239,7 @@ int pnp_plan_problem(const pnp_problem_desc *desc, pnp_problem_info *info, doubl
     info->stencil_halfwidth = p.S;
     info->well_halfwidth = p.Ssw;
     info->device_bytes = estimate_device_bytes(p);
+    info->bjerrum_h = p.lB;
     if (mu_reservoir)
         for (int i = 0; i < p.s; ++i) mu_reservoir[i] = p.mu_bulk[i];
     return PNP_OK;

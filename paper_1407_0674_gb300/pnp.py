@@ -82,7 +82,7 @@ class Stats(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("fft_len", ctypes.c_int * 3), ("stencil_halfwidth", ctypes.c_int),
                 ("well_halfwidth", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("mg_levels", ctypes.c_int),
-                ("tile", ctypes.c_int * 3), ("tuned_ms", ctypes.c_double)]
+                ("tile", ctypes.c_int * 3), ("tuned_ms", ctypes.c_double), ("bjerrum_h", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -224,7 +224,7 @@ def plan(spec, precision="fp64"):
     mu = np.zeros(len(spec.R))
     _check(lib().pnp_plan_problem(ctypes.byref(dh.desc), ctypes.byref(i), _ptr(mu)), "pnp_plan_problem")
     return ({"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
-             "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes}, mu)
+             "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "bjerrum_h": i.bjerrum_h}, mu)
 
 
 def selftest_bounded_wait(limit_ms):
@@ -276,7 +276,7 @@ class Problem:
         _check(lib().pnp_get_problem_info(self.h, ctypes.byref(i)), "pnp_get_problem_info")
         return {"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
                 "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "mg_levels": i.mg_levels,
-                "tile": tuple(i.tile), "tuned_ms": i.tuned_ms}
+                "tile": tuple(i.tile), "tuned_ms": i.tuned_ms, "bjerrum_h": i.bjerrum_h}
 
     def excess_mu(self, rho, precision=None):
         """pnp_excess_mu on host arrays; returns mu_ex [s, nz, ny, nx]."""

@@ -89,3 +89,22 @@ def test_rejected_descriptors(pnp):
         with pytest.raises(pnp.PnpError) as e:
             pnp.plan(s)
         assert e.value.code == pnp.ERR_INVALID
+
+
+def test_bjerrum_length_reproduces_table1(pnp):
+    """The library's unit conversion (SI constants) against the values the
+    paper prints in Table 1: l_B = 4.514 nm at 223 K with eps_r = 16.6."""
+    import os
+    g = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_units.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                g[k] = float(v)
+    spec, _ = mu_microbench(shape=(8, 8, 8))
+    spec = dataclasses.replace(spec, temperature_K=g["temperature_K"], eps_r=g["eps_r"], h_nm=1.0)
+    info, _ = pnp.plan(spec)
+    assert info["bjerrum_h"] == pytest.approx(g["bjerrum_length_nm"], rel=1e-4)
+    # in grid units h = 0.5 nm the same length is twice as many h
+    info2, _ = pnp.plan(dataclasses.replace(spec, h_nm=0.5))
+    assert info2["bjerrum_h"] == pytest.approx(2 * info["bjerrum_h"], rel=1e-14)
