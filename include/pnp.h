@@ -331,6 +331,17 @@ int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
  * boundaries), PNP_ERR_PACKING, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
 int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double *rho, double *flux);
 
+/* Host-only diagnostic: the discrete weight stencil K[m] the library builds
+ * at set-up (Sec 2.3.1 weights by the quadrature of Sec 3.5, each node
+ * deposited trilinearly on the grid; Sec 2.3.2 well shell).  kind 0: shell
+ * delta(|r| - r_out) (w2); 1: ball |r| <= r_out (w3); 2, 3, 4: x, y, z
+ * components of the vector shell (vec w2); 5: thick shell r_in <= |r| <= r_out
+ * (the square well).  nmu, ntheta, nr: quadrature counts (0 = defaults).  out
+ * gets (2S+1)^3 values, out[((mz+S)(2S+1) + my+S)(2S+1) + mx+S] for offsets
+ * |m| <= S in units of h; S must reach the support (ceil(r_out) + 1).
+ * Errors: PNP_ERR_INVALID. */
+int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, double *out);
+
 /* Failure-path self-test with no counterpart in the paper: launches one
  * kernel that waits on an mbarrier nothing ever completes, with the same
  * globally-timed bounded wait the tensor-core kernels use, limited to

@@ -245,6 +245,22 @@ int pnp_plan_problem(const pnp_problem_desc *desc, pnp_problem_info *info, doubl
     return PNP_OK;
 }
 
+int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, double *out) {
+    if (!out || kind < 0 || kind > 5 || !(r_out > 0) || nmu < 0 || ntheta < 0 || nr < 0 || S < 1 || S > 64)
+        return PNP_ERR_INVALID;
+    if ((int)std::ceil(r_out) + 1 > S || (kind == 5 && !(r_in >= 0 && r_in < r_out))) return PNP_ERR_INVALID;
+    Stencil st;
+    if (kind == 5) {
+        build_well_stencil(r_in, r_out, nmu, ntheta, nr, S, st);
+    } else {
+        Stencil fmt[kNumKernels];
+        build_fmt_stencils(r_out, nmu, ntheta, nr, S, fmt);
+        st = fmt[kind];
+    }
+    std::memcpy(out, st.K.data(), sizeof(double) * st.K.size());
+    return PNP_OK;
+}
+
 int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precision) {
     if (!h || !rho || !mu_ex) return PNP_ERR_INVALID;
     Problem *p = h->impl;

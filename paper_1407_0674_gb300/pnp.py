@@ -131,6 +131,8 @@ def lib():
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
+        L.pnp_weight_stencil.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -225,6 +227,16 @@ def plan(spec, precision="fp64"):
     _check(lib().pnp_plan_problem(ctypes.byref(dh.desc), ctypes.byref(i), _ptr(mu)), "pnp_plan_problem")
     return ({"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
              "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "bjerrum_h": i.bjerrum_h}, mu)
+
+
+def weight_stencil(kind, r_out, r_in=0.0, nmu=0, ntheta=0, nr=0, S=None):
+    """pnp_weight_stencil: the library's discrete weight stencil, [mz][my][mx]."""
+    if S is None:
+        S = int(np.ceil(r_out)) + 1
+    out = np.zeros((2 * S + 1,) * 3)
+    _check(lib().pnp_weight_stencil(int(kind), float(r_in), float(r_out), int(nmu), int(ntheta), int(nr), int(S),
+                                    _ptr(out)), "pnp_weight_stencil")
+    return out
 
 
 def selftest_bounded_wait(limit_ms):

@@ -108,3 +108,35 @@ def test_bjerrum_length_reproduces_table1(pnp):
     # in grid units h = 0.5 nm the same length is twice as many h
     info2, _ = pnp.plan(dataclasses.replace(spec, h_nm=0.5))
     assert info2["bjerrum_h"] == pytest.approx(2 * info["bjerrum_h"], rel=1e-14)
+
+
+@pytest.mark.parametrize("R", [1.0, 1.5, 2.0, 3.0, 2.37])
+def test_weight_stencils_match_independent_tables(pnp, R):
+    """The library's set-up stencils (row a1: quadrature of Sec 3.5, trilinear
+    deposit) against the brute-force module's tables, built independently from
+    numpy's Gauss-Legendre nodes and hat functions."""
+    import brute
+    S = int(np.ceil(R)) + 1
+    ps, ws, us = brute.nodes("shell", R)
+    pb, wb, ub = brute.nodes("ball", R)
+    shell = brute.kernel_table(ps, ws, us, S)
+    ball = brute.kernel_table(pb, wb, ub, S)
+    vec = brute.kernel_table(ps, ws, us, S, vector=True)
+    np.testing.assert_allclose(pnp.weight_stencil(0, R), shell, rtol=0, atol=1e-13 * shell.max())
+    np.testing.assert_allclose(pnp.weight_stencil(1, R), ball, rtol=0, atol=1e-13 * ball.max())
+    for c in range(3):
+        np.testing.assert_allclose(pnp.weight_stencil(2 + c, R), vec[..., c], rtol=0, atol=1e-13 * shell.max())
+    # exact moments of the quadrature: surface 4 pi R^2, volume 4/3 pi R^3
+    assert pnp.weight_stencil(0, R).sum() == pytest.approx(4 * np.pi * R * R, rel=1e-13)
+    assert pnp.weight_stencil(1, R).sum() == pytest.approx(4 / 3 * np.pi * R ** 3, rel=1e-13)
+
+
+def test_well_stencil_matches_independent_table(pnp):
+    import brute
+    r_in, r_out = 4.0, 5.0
+    S = int(np.ceil(r_out)) + 1
+    p, w, u = brute.nodes("thick", r_out, r_in)
+    ref = brute.kernel_table(p, w, u, S)
+    got = pnp.weight_stencil(5, r_out, r_in=r_in)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * ref.max())
+    assert got.sum() == pytest.approx(4 / 3 * np.pi * (r_out ** 3 - r_in ** 3), rel=1e-13)
