@@ -342,6 +342,15 @@ int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double 
  * Errors: PNP_ERR_INVALID. */
 int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, double *out);
 
+/* Host-only diagnostic: the real octant of that stencil's DFT on an
+ * Lx x Ly x Lz periodic grid, as the set-up stores it: out[kz][ky][kx]
+ * (k <= L/2, x fastest) = sum_m K[m] f(kx mx) f(ky my) f(kz mz), f = cos on
+ * even axes and sin on the vector component's own axis (odd), so the DFT is
+ * out (even kernels) or -i out (vector components).  Every L must be at least
+ * 2S + 1.  Errors: PNP_ERR_INVALID. */
+int pnp_weight_spectrum(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, int Lx, int Ly,
+                        int Lz, double *out);
+
 /* Failure-path self-test with no counterpart in the paper: launches one
  * kernel that waits on an mbarrier nothing ever completes, with the same
  * globally-timed bounded wait the tensor-core kernels use, limited to

@@ -261,6 +261,23 @@ int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta,
     return PNP_OK;
 }
 
+int pnp_weight_spectrum(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, int Lx, int Ly,
+                        int Lz, double *out) {
+    if (!out || Lx < 2 * S + 1 || Ly < 2 * S + 1 || Lz < 2 * S + 1 || Lx > 4096 || Ly > 4096 || Lz > 4096)
+        return PNP_ERR_INVALID;
+    const int W = 2 * S + 1;
+    std::vector<double> k((size_t)W * W * W);
+    const int rc = pnp_weight_stencil(kind, r_in, r_out, nmu, ntheta, nr, S, k.data());
+    if (rc) return rc;
+    Stencil st;
+    st.S = S;
+    st.K = k;
+    const int L[3] = {Lx, Ly, Lz};
+    const bool odd[3] = {kind == 2, kind == 3, kind == 4};
+    octant_transform(st, L, odd, 1.0, out);
+    return PNP_OK;
+}
+
 int pnp_excess_mu(pnp_problem *h, const double *rho, double *mu_ex, int precision) {
     if (!h || !rho || !mu_ex) return PNP_ERR_INVALID;
     Problem *p = h->impl;

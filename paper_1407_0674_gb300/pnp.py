@@ -133,6 +133,8 @@ def lib():
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_weight_stencil.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, _dp]
+        L.pnp_weight_spectrum.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_stage_timing.argtypes = [vp, ctypes.c_int]
         L.pnp_stage_times.argtypes = [vp, _dp, _ip, ctypes.c_int]
         L.pnp_stage_name.argtypes = [ctypes.c_int]
@@ -236,6 +238,17 @@ def weight_stencil(kind, r_out, r_in=0.0, nmu=0, ntheta=0, nr=0, S=None):
     out = np.zeros((2 * S + 1,) * 3)
     _check(lib().pnp_weight_stencil(int(kind), float(r_in), float(r_out), int(nmu), int(ntheta), int(nr), int(S),
                                     _ptr(out)), "pnp_weight_stencil")
+    return out
+
+
+def weight_spectrum(kind, r_out, L, r_in=0.0, S=None):
+    """pnp_weight_spectrum: the stored real octant of a stencil's DFT on an L grid."""
+    if S is None:
+        S = int(np.ceil(r_out)) + 1
+    Lx, Ly, Lz = L
+    out = np.zeros((Lz // 2 + 1, Ly // 2 + 1, Lx // 2 + 1))
+    _check(lib().pnp_weight_spectrum(int(kind), float(r_in), float(r_out), 0, 0, 0, int(S), Lx, Ly, Lz, _ptr(out)),
+           "pnp_weight_spectrum")
     return out
 
 

@@ -140,3 +140,27 @@ def test_well_stencil_matches_independent_table(pnp):
     got = pnp.weight_stencil(5, r_out, r_in=r_in)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * ref.max())
     assert got.sum() == pytest.approx(4 / 3 * np.pi * (r_out ** 3 - r_in ** 3), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4, 5])
+def test_weight_spectra_match_numpy_fft(pnp, kind):
+    """The set-up spectra (a separable real transform over the stored octant)
+    against numpy's FFT of the stencil embedded periodically in the grid: the
+    DFT is the octant (even kernels) or -i times it (vector components)."""
+    R, r_in = (5.0, 4.0) if kind == 5 else (2.0, 0.0)
+    S = int(np.ceil(R)) + 1
+    L = (16, 14, 18)
+    K = pnp.weight_stencil(kind, R, r_in=r_in, S=S)
+    grid = np.zeros((L[2], L[1], L[0]))
+    m = np.arange(-S, S + 1)
+    zz, yy, xx = np.meshgrid(m % L[2], m % L[1], m % L[0], indexing="ij")
+    np.add.at(grid, (zz, yy, xx), K)
+    F = np.fft.fftn(grid)[: L[2] // 2 + 1, : L[1] // 2 + 1, : L[0] // 2 + 1]
+    oct_ = pnp.weight_spectrum(kind, R, L, r_in=r_in, S=S)
+    scale = np.abs(F).max()
+    if kind in (2, 3, 4):
+        np.testing.assert_allclose(F.imag, -oct_, rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(F.real, 0.0, rtol=0, atol=1e-12 * scale)
+    else:
+        np.testing.assert_allclose(F.real, oct_, rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(F.imag, 0.0, rtol=0, atol=1e-12 * scale)
