@@ -55,3 +55,31 @@ def test_matches_numpy(check, n):
 
 def test_empty_is_valid(check):
     assert check(np.zeros(0), 1) is True
+
+
+def test_tf32_split_dft16_matrices():
+    """The operands of the tensor-core y pass: the real form of the 16-point
+    DFT (forward and inverse) split into TF32 hi and lo parts.  Each part must
+    be exactly representable in TF32 (low 13 mantissa bits zero), and hi + lo
+    must be the matrix to 2^-22 relative -- the accuracy the 3-term product
+    relies on."""
+    L = ctypes.CDLL(LIB)
+    f = getattr(L, "_ZN3pnp17ypass_tc_matricesEPf")
+    f.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    f.restype = None
+    out = np.zeros(4 * 32 * 32, dtype=np.float32)
+    f(out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    M = out.reshape(2, 2, 32, 32)               # [direction][hi, lo][j][k]
+    bits = M.view(np.uint32)
+    assert not np.any(bits & np.uint32(0x1FFF))
+    n = np.arange(16)
+    for d, sign in ((0, -1.0), (1, 1.0)):
+        W = np.exp(sign * 2j * np.pi * np.outer(n, n) / 16)   # W[k_out, n_in]
+        ref = np.zeros((32, 32))
+        ref[0::2, 0::2] = W.real      # out re <- in re
+        ref[0::2, 1::2] = -W.imag     # out re <- in im
+        ref[1::2, 0::2] = W.imag      # out im <- in re
+        ref[1::2, 1::2] = W.real      # out im <- in im
+        total = M[d, 0].astype(np.float64) + M[d, 1].astype(np.float64)
+        assert np.abs(total - ref).max() <= 2.0 ** -22
+        assert np.abs(M[d, 0] - ref).max() <= 2.0 ** -10
