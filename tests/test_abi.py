@@ -90,3 +90,22 @@ def test_desc_init_defaults(L):
     assert L.pnp_desc_init(ctypes.byref(d)) == 0
     assert d.lambda_phi == 0.3 and d.max_iter == 500 and d.sw_half == 1 and d.eps_r == 16.6
     assert L.pnp_desc_init(None) == pnp.ERR_INVALID
+
+
+@pytest.mark.parametrize("ctype,cname", [(pnp.Stats, "pnp_stats"), (pnp.Info, "pnp_problem_info"),
+                                          (pnp.ServerOpts, "pnp_server_opts"),
+                                          (pnp.ServerStats, "pnp_server_stats")])
+def test_struct_field_offsets_match_header(L, ctype, cname):
+    fields = [f for f, _ in ctype._fields_]
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"pnp.h\"\nint main(void){\n"
+    for f in fields:
+        prog += f'printf("%zu\\n", offsetof({cname}, {f}));\n'
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    for f, off in zip(fields, out):
+        assert getattr(ctype, f).offset == off, (cname, f)
