@@ -15,7 +15,9 @@ composition on tiny grids, started from arbitrary states:
 mu_ex and the Poisson right-hand side take the densities the sweep starts
 from; the NP solves take the relaxed phi.  The oracle's iteration applies this
 sweep repeatedly, so pinning it from arbitrary states pins every iterate of
-its trajectory up to the linear-solver tolerance.
+its trajectory up to the linear-solver tolerance.  The equilibrium stage's
+steps (Newton step of Poisson-Boltzmann, clamp, density relaxation) are
+pinned the same way.
 """
 import math
 
@@ -180,3 +182,49 @@ def test_adaptive_factors_halve_where_the_step_flips():
     for _ in range(4):
         phi, rho, _ = G(phi, rho)
     assert (G.lam < spec.lambda_rho * 0.99).any() and (G.lam == spec.lambda_rho).any()
+
+
+def dense_equilibrium(spec, steps, lam):
+    """The equilibrium stage (Sec 3.2, choice of initial guess) by the dense
+    parts: from the linear phi profile and the bulk densities, each step takes
+    c_i = rho_b,i exp(mu_b,i - mu_ex,i[rho]), one Newton step of the
+    Poisson-Boltzmann equation with Boltzmann densities c_i exp(-q_i phi)
+    (update clamped to +-1 kT/e), then the step-limited geometric relaxation
+    of rho towards c_i exp(-q_i phi).  Returns phi, rho, residual, clamped."""
+    G = DenseSweep(spec)
+    z = np.arange(1, spec.nz + 1)[:, None, None]
+    phi = np.broadcast_to(spec.phi_lo + (spec.phi_hi - spec.phi_lo) * z / (spec.nz + 1), spec.shape).copy()
+    rho = np.stack([np.full(spec.shape, spec.rho_b[i]) for i in range(spec.s)])
+    res, clamped = 0.0, False
+    for _ in range(steps):
+        mu = G.mu_ex(rho)
+        c = np.stack([spec.rho_b[i] * np.exp(G.mu_b[i] - mu[i]) for i in range(spec.s)])
+        r = np.stack([c[i] * np.exp(-spec.q[i] * phi) for i in range(spec.s)])
+        b = 4 * np.pi * G.lB * (spec.rho_f + sum(spec.q[i] * r[i] for i in range(spec.s)))
+        b[0] += spec.phi_lo
+        b[-1] += spec.phi_hi
+        shift = 4 * np.pi * G.lB * sum(spec.q[i] ** 2 * r[i] for i in range(spec.s))
+        d = np.linalg.solve(G.A + np.diag(shift.reshape(-1)), b.reshape(-1) - G.A @ phi.reshape(-1))
+        clamped |= bool((np.abs(d) > 1).any())
+        d = np.clip(d, -1.0, 1.0).reshape(spec.shape)
+        phi = phi + d
+        res = np.abs(d).max()
+        for i in range(spec.s):
+            step = np.clip(lam * np.log(c[i] * np.exp(-spec.q[i] * phi) / rho[i]), -0.2, 0.2)
+            v = rho[i] * np.exp(step)
+            res = max(res, np.abs(v - rho[i]).max() / spec.rho_b[i])
+            rho[i] = v
+    return phi, rho, res, clamped
+
+
+@pytest.mark.parametrize("bias,steps,clamps", [(0.5, 3, False), (6.0, 2, True)])
+def test_equilibrium_steps_match_dense_composition(bias, steps, clamps):
+    spec = make_spec(0, False, 0, 1)
+    spec.phi_hi = bias
+    r = oracle.equilibrium(spec, lam=0.5, tol=0.0, max_iter=steps)
+    assert r["status"] == 1 and r["iters"] == steps
+    phi, rho, res, clamped = dense_equilibrium(spec, steps, 0.5)
+    assert clamped == clamps
+    np.testing.assert_allclose(r["phi"], phi, rtol=0, atol=1e-11 * np.abs(phi).max())
+    np.testing.assert_allclose(r["rho"], rho, rtol=1e-11, atol=0)
+    assert r["residual"] == pytest.approx(res, rel=1e-9)
