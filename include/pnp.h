@@ -317,7 +317,6 @@ int pnp_poll(pnp_server *s, uint64_t ticket, double *phi_out, double *rho_out, p
 
 int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
 
-/* Static message for an error code. */
 /* Nernst-Planck current of species `species` through every z face (Sec 2.1,
  * Sec 3.1; the paper's conductivity is the current over the applied field):
  * flux[k+1] = sum over the x-y plane of Dbar_face (rhobar_k - rhobar_k+1)
@@ -359,6 +358,7 @@ int pnp_weight_spectrum(int kind, double r_in, double r_out, int nmu, int ntheta
  * limit, PNP_ERR_CUDA on a runtime error.  The device stays usable. */
 int pnp_selftest_bounded_wait(double limit_ms);
 
+/* Static message for an error code. */
 const char *pnp_error_string(int code);
 
 #ifdef __cplusplus

@@ -311,6 +311,26 @@ def np_flux(spec, i, phi, mu, mu_b, rhobar):
     return out
 
 
+def conductivity(spec, flux, D_m2_per_s=0.0):
+    """Ionic conductivity (Sec 4, size dependency of the conductivity): the
+    current density along the transport axis averaged over its length, over
+    the applied field.  flux [s][nz+1] are the species' currents through the
+    z faces (np_flux: reduced units, h = 1, each summed over the nx*ny faces of
+    a plane).  The charge current density is sum_i q_i flux_i / (nx ny); its
+    mean over the nz+1 faces stands for (1/L) int J dz; the field is the applied
+    one, E = -(phi_hi - phi_lo) / (nz+1) in kT/e per h.  Returns (sigma in units
+    of e^2 D / (kT h^3), sigma in S/cm for the diffusion scale D_m2_per_s and the
+    spec's T and h; 0 when D_m2_per_s is 0)."""
+    flux = np.asarray(flux, dtype=np.float64).reshape(spec.s, spec.nz + 1)
+    current = sum(spec.q[i] * flux[i] for i in range(spec.s)) / (spec.nx * spec.ny)
+    field = -(spec.phi_hi - spec.phi_lo) / (spec.nz + 1)
+    sigma = current.mean() / field
+    # e^2 D / (kT h^3) = e [C] * beta [1/V] * D [m^2/s] / h^3 [m^3]  (S/m), /100 for S/cm
+    h_m = spec.h_nm * 1e-9
+    si = sigma * units.E_CHARGE_C * units.beta_per_ev(spec.temperature_K) * D_m2_per_s / h_m ** 3 / 100.0
+    return float(sigma), float(si)
+
+
 def gummel(spec, phi0=None, rho0=None, lin_tol=1e-13):
     """Relaxed Gummel iteration of Sec 3.2.  Returns a dict with phi, rho,
     status (0 converged, 1 not converged, 2 packing), iters, hist."""

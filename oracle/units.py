@@ -7,6 +7,7 @@ Potentials are in kT/e and lengths in grid spacings h.
 """
 COULOMB_EV_NM = 1.43996454784     # e^2 / (4 pi eps0) in eV nm
 KB_EV_PER_K = 8.617333262e-5      # Boltzmann constant in eV / K
+E_CHARGE_C = 1.602176634e-19     # elementary charge in C (exact in the SI)
 
 
 def beta_per_ev(temperature_K: float) -> float:
