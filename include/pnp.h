@@ -330,6 +330,21 @@ int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
  * boundaries), PNP_ERR_PACKING, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
 int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double *rho, double *flux);
 
+/* Host-only: ionic conductivity from plane currents (Sec 4, size dependency
+ * of the conductivity: the current density along the transport axis averaged
+ * over its length, divided by the field).  flux [nspecies][nz+1] holds each
+ * species' currents through the z faces as pnp_plane_flux returns them
+ * (reduced units, h = 1, the desc's relative diffusivities).  With the charge
+ * current density c_k = sum_i q_i flux_i[k] / (nx ny), its mean over the
+ * nz+1 faces standing for the length average, and the applied field
+ * E = -(phi_hi - phi_lo) / (nz+1) (kT/e per h):
+ *   sigma[0] = mean_k c_k / E, in units of e^2 D / (k_B T h^3);
+ *   sigma[1] = the same in S/cm for the diffusion scale D_m2_per_s (m^2/s;
+ *              the paper's 1e-6 cm^2/s is 1e-10) and the desc's T and h_nm.
+ * Needs a Dirichlet z axis and phi_hi != phi_lo.  Errors: PNP_ERR_INVALID
+ * (descriptor rejected, zero bias, non-finite flux, D_m2_per_s < 0). */
+int pnp_conductivity(const pnp_problem_desc *desc, const double *flux, double D_m2_per_s, double *sigma);
+
 /* Host-only diagnostic: the discrete weight stencil K[m] the library builds
  * at set-up (Sec 2.3.1 weights by the quadrature of Sec 3.5, each node
  * deposited trilinearly on the grid; Sec 2.3.2 well shell).  kind 0: shell

@@ -245,6 +245,30 @@ int pnp_plan_problem(const pnp_problem_desc *desc, pnp_problem_info *info, doubl
     return PNP_OK;
 }
 
+int pnp_conductivity(const pnp_problem_desc *desc, const double *flux, double D_m2_per_s, double *sigma) {
+    if (!desc || !flux || !sigma || !(D_m2_per_s >= 0.0) || !std::isfinite(D_m2_per_s)) return PNP_ERR_INVALID;
+    Problem p;
+    std::string why;
+    const int rc = validate_and_copy(desc, &p, &why);
+    if (rc) return rc;
+    const double dphi = p.phi_hi - p.phi_lo;
+    if (p.bc[2] != PNP_BC_DIRICHLET || dphi == 0.0) return PNP_ERR_INVALID;
+    const int faces = p.nz + 1;
+    if (!host_values_ok(flux, (size_t)p.s * faces, 0)) return PNP_ERR_INVALID;
+    // mean over the faces of the charge current through a plane
+    double sum = 0.0;
+    for (int k = 0; k < faces; ++k) {
+        double c = 0.0;
+        for (int i = 0; i < p.s; ++i) c += p.q[i] * flux[(size_t)i * faces + k];
+        sum += c;
+    }
+    const double current = sum / faces / ((double)p.nx * p.ny);   // per unit area (h^2)
+    const double field = -dphi / faces;                           // kT/e per h
+    sigma[0] = current / field;
+    sigma[1] = sigma[0] * conductivity_unit_S_per_cm(p.temperature_K, p.h_nm, D_m2_per_s);
+    return PNP_OK;
+}
+
 int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, double *out) {
     if (!out || kind < 0 || kind > 5 || !(r_out > 0) || nmu < 0 || ntheta < 0 || nr < 0 || S < 1 || S > 64)
         return PNP_ERR_INVALID;

@@ -251,14 +251,22 @@ void octant_transform(const Stencil &st, const int L[3], const bool odd[3], doub
     for (auto &th : pool) th.join();
 }
 
+// SI constants (CODATA 2018; e and k_B exact).
+static const double kCharge = 1.602176634e-19;   // C
+static const double kEps0 = 8.8541878128e-12;    // F/m
+static const double kBoltzmann = 1.380649e-23;   // J/K
+
 // Bjerrum length e^2 / (4 pi eps0 eps_r k_B T) (Sec 2.3.3) from SI constants,
 // expressed in grid spacings.
 double bjerrum_length_h(double T, double eps_r, double h_nm) {
-    const double e = 1.602176634e-19;       // C
-    const double eps0 = 8.8541878128e-12;   // F/m
-    const double kB = 1.380649e-23;         // J/K
-    double lB_m = e * e / (4.0 * M_PI * eps0 * eps_r * kB * T);
+    double lB_m = kCharge * kCharge / (4.0 * M_PI * kEps0 * eps_r * kBoltzmann * T);
     return lB_m * 1e9 / h_nm;
+}
+
+// The unit of the reduced conductivity, e^2 D / (k_B T h^3), in S/cm.
+double conductivity_unit_S_per_cm(double T, double h_nm, double D_m2_per_s) {
+    const double h = h_nm * 1e-9;
+    return kCharge * kCharge * D_m2_per_s / (kBoltzmann * T * h * h * h) / 100.0;
 }
 
 // Reservoir excess chemical potential: in a uniform fluid every weighted

@@ -127,6 +127,7 @@ void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil ou
 void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
 void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
 double bjerrum_length_h(double T, double eps_r, double h_nm);
+double conductivity_unit_S_per_cm(double T, double h_nm, double D_m2_per_s);
 void bulk_mu_fmt(const Problem &p, std::vector<double> &mu);
 
 // ypass_tc.cu: a kernel whose bounded mbarrier wait nothing completes

@@ -131,6 +131,7 @@ def lib():
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
+        L.pnp_conductivity.argtypes = [ctypes.POINTER(Desc), _dp, ctypes.c_double, _dp]
         L.pnp_weight_stencil.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_weight_spectrum.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -229,6 +230,17 @@ def plan(spec, precision="fp64"):
     _check(lib().pnp_plan_problem(ctypes.byref(dh.desc), ctypes.byref(i), _ptr(mu)), "pnp_plan_problem")
     return ({"fft_len": tuple(i.fft_len), "stencil_halfwidth": i.stencil_halfwidth,
              "well_halfwidth": i.well_halfwidth, "device_bytes": i.device_bytes, "bjerrum_h": i.bjerrum_h}, mu)
+
+
+def conductivity(spec, flux, D_m2_per_s=0.0):
+    """pnp_conductivity (host-only): (reduced sigma, sigma in S/cm) from the
+    species' plane currents flux [s][nz+1]."""
+    dh = DescHolder(spec)
+    f = _f64(flux)
+    assert f.shape == (len(spec.R), spec.nz + 1)
+    out = np.zeros(2)
+    _check(lib().pnp_conductivity(ctypes.byref(dh.desc), _ptr(f), float(D_m2_per_s), _ptr(out)), "pnp_conductivity")
+    return float(out[0]), float(out[1])
 
 
 def weight_stencil(kind, r_out, r_in=0.0, nmu=0, ntheta=0, nr=0, S=None):
@@ -340,6 +352,12 @@ class Problem:
         out = np.empty(self.shape[0] + 1)
         _check(lib().pnp_plane_flux(self.h, int(species), _ptr(p), _ptr(r), _ptr(out)), "pnp_plane_flux")
         return out
+
+    def conductivity(self, phi, rho, D_m2_per_s=0.0):
+        """Plane currents of every species (pnp_plane_flux), then
+        pnp_conductivity: (reduced sigma, sigma in S/cm)."""
+        flux = np.stack([self.plane_flux(i, phi, rho) for i in range(self.s)])
+        return conductivity(self.spec, flux, D_m2_per_s)
 
     def gummel_solve(self, phi0=None, rho0=None, raise_on_error=True):
         """pnp_gummel_solve; returns (phi, rho, stats dict)."""

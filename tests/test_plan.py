@@ -164,3 +164,29 @@ def test_weight_spectra_match_numpy_fft(pnp, kind):
     else:
         np.testing.assert_allclose(F.real, oct_, rtol=0, atol=1e-12 * scale)
         np.testing.assert_allclose(F.imag, 0.0, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("bias,T,h", [(0.5, 300.0, 1.0), (-1.3, 223.0, 0.5), (1e-3, 400.0, 0.25)])
+def test_conductivity_matches_oracle(pnp, bias, T, h):
+    """pnp_conductivity (host-only arithmetic on plane currents) against the
+    oracle's conductivity, on arbitrary currents: reduced and S/cm."""
+    spec = film_gummel(6, 5, 9)
+    spec.phi_hi, spec.temperature_K, spec.h_nm = bias, T, h
+    rng = np.random.default_rng(3)
+    flux = rng.normal(0.0, 1.0, (spec.s, spec.nz + 1))
+    got = pnp.conductivity(spec, flux, D_m2_per_s=1e-10)
+    ref = oracle.conductivity(spec, flux, D_m2_per_s=1e-10)
+    assert got[0] == pytest.approx(ref[0], rel=1e-13)
+    # the oracle's k_B in eV/K carries 10 digits (1.7e-11 from k_B/e)
+    assert got[1] == pytest.approx(ref[1], rel=1e-10)
+
+
+def test_conductivity_rejections(pnp):
+    spec = film_gummel(6, 5, 9)
+    flux = np.ones((spec.s, spec.nz + 1))
+    for s, f, D in [(dataclasses.replace(spec, phi_hi=spec.phi_lo), flux, 0.0),    # no applied field
+                    (spec, np.where(np.arange(flux.size).reshape(flux.shape) == 4, np.nan, flux), 0.0),
+                    (spec, flux, -1.0)]:
+        with pytest.raises(pnp.PnpError) as e:
+            pnp.conductivity(s, f, D)
+        assert e.value.code == pnp.ERR_INVALID
