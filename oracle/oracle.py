@@ -251,6 +251,21 @@ def mu_sh(spec, rho_s):
     return out
 
 
+def square_well_energy(spec, rho):
+    """Square-well free energy F_sh of Sec 2.3.2 (kT), the mobile-site part:
+    the printed double sum over pairs (alpha, beta) with the factor 1/2 counts
+    the pair (i, s) and (s, i), so with the site density held fixed
+    F_sh = sum_i int rho_i(r) int rho_s(r') Phi_is(|r - r'|) dr' dr
+    (h^3 = 1).  Site-site pairs are a constant and mobile-mobile wells are
+    absent (Sec 2.3.2), so neither is included.  The inner integral is the
+    oracle's square-well sum without the 1/2 of mu_sh."""
+    import dataclasses
+    full = dataclasses.replace(spec, sw_half=False)
+    w = mu_sh(full, site_density(full))
+    r = _f64(rho).reshape(w.shape)
+    return float(sum((r[i] * w[i]).sum() for i in range(w.shape[0])))
+
+
 def excess_mu(spec, rho):
     """mu_ex = mu_hs + mu_sh (Sec 2.3).  Returns (mu[s, nz, ny, nx], bad)."""
     P = Problem(spec)
