@@ -330,6 +330,19 @@ int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out);
  * boundaries), PNP_ERR_PACKING, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
 int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double *rho, double *flux);
 
+/* Square-well free energy F_sh of Sec 2.3.2 (in kT), the mobile-site part:
+ * the printed pair sum with its factor 1/2 counts each pair (i, s) twice, so
+ * with the site density fixed
+ *   F_sh = sum_i sum_r rho_i(r) sum_r' rho_s(r') Phi_is(|r - r'|) h^3
+ *        = -sum_i eps_i sum_r rho_i(r) U(r),   U = K_sw (x) rho_s,
+ * the well field the library builds on the device at set-up (site-site pairs
+ * are a constant and mobile-mobile wells are absent).  Its derivative with
+ * respect to rho_i is -eps_i U, twice mu_sh,i when sw_half keeps the 1/2.
+ * rho [s][nz][ny][nx] (host, FP64, >= 0); *F_sh = 0 without wells.  U is
+ * copied to the host and the dot products summed there in a fixed order.
+ * Errors: PNP_ERR_INVALID, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
+int pnp_square_well_energy(pnp_problem *p, const double *rho, double *F_sh);
+
 /* Host-only: ionic conductivity from plane currents (Sec 4, size dependency
  * of the conductivity: the current density along the transport axis averaged
  * over its length, divided by the field).  flux [nspecies][nz+1] holds each

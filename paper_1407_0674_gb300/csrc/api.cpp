@@ -442,6 +442,35 @@ int pnp_plane_flux(pnp_problem *h, int species, const double *phi, const double 
     return rc ? rc : f;
 }
 
+int pnp_square_well_energy(pnp_problem *h, const double *rho, double *F_sh) {
+    if (!h || !rho || !F_sh) return PNP_ERR_INVALID;
+    Problem *p = h->impl;
+    const size_t N = p->npts();
+    if (!host_values_ok(rho, N * p->s, 1)) return PNP_ERR_INVALID;
+    *F_sh = 0.0;
+    if (!p->has_wells) return PNP_OK;
+    // the well field U = K_sw (x) rho_s was built on the device at set-up
+    std::vector<double> U;
+    try {
+        U.resize(N);
+    } catch (const std::bad_alloc &) {
+        return PNP_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpyAsync(U.data(), p->d_U, sizeof(double) * N, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    double F = 0.0;
+    for (int i = 0; i < p->s; ++i) {
+        if (p->depth[i] == 0.0) continue;
+        const double *r = rho + (size_t)i * N;
+        double acc = 0.0;
+        for (size_t k = 0; k < N; ++k) acc += r[k] * U[k];
+        F -= p->depth[i] * acc;
+    }
+    *F_sh = F;
+    return PNP_OK;
+}
+
 int pnp_selftest_bounded_wait(double limit_ms) { return bounded_wait_probe(limit_ms); }
 
 const char *pnp_error_string(int code) {

@@ -132,6 +132,7 @@ def lib():
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_conductivity.argtypes = [ctypes.POINTER(Desc), _dp, ctypes.c_double, _dp]
+        L.pnp_square_well_energy.argtypes = [vp, _dp, _dp]
         L.pnp_weight_stencil.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_weight_spectrum.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -352,6 +353,14 @@ class Problem:
         out = np.empty(self.shape[0] + 1)
         _check(lib().pnp_plane_flux(self.h, int(species), _ptr(p), _ptr(r), _ptr(out)), "pnp_plane_flux")
         return out
+
+    def square_well_energy(self, rho):
+        """pnp_square_well_energy: F_sh (kT) of the densities rho [s][nz][ny][nx]."""
+        r = _f64(rho)
+        assert r.shape == (self.s,) + self.shape
+        out = np.zeros(1)
+        _check(lib().pnp_square_well_energy(self.h, _ptr(r), _ptr(out)), "pnp_square_well_energy")
+        return float(out[0])
 
     def conductivity(self, phi, rho, D_m2_per_s=0.0):
         """Plane currents of every species (pnp_plane_flux), then

@@ -300,3 +300,22 @@ def test_conductivity_of_converged_state(pnp):
     assert sig[0] > 0
     assert sig[0] == pytest.approx(ref[0], rel=1e-8)
     assert sig[1] == pytest.approx(ref[1], rel=1e-8)
+
+
+@pytest.mark.parametrize("depth2", [0.0, 0.7])
+def test_square_well_energy_matches_oracle(pnp, depth2):
+    """pnp_square_well_energy (the device well field, summed against rho on
+    the host) against the oracle's direct-quadrature F_sh; a film without
+    wells gives exactly zero."""
+    spec = film_gummel(16, 12, 10, nsites=6)
+    spec.depth = (1.0, depth2)
+    rng = np.random.default_rng(12)
+    rho = np.stack([spec.rho_b[i] * rng.lognormal(0.0, 0.3, spec.shape) for i in range(spec.s)])
+    with pnp.Problem(spec) as P:
+        F = P.square_well_energy(rho)
+    ref = oracle.square_well_energy(spec, rho)
+    assert ref < 0
+    assert F == pytest.approx(ref, rel=1e-10)
+    spec.depth = (0.0, 0.0)
+    with pnp.Problem(spec) as P:
+        assert P.square_well_energy(rho) == 0.0
