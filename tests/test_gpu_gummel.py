@@ -282,40 +282,3 @@ def test_plane_flux_matches_oracle(pnp):
     # the cation and anion currents run in opposite directions
     assert flux[0].mean() * flux[1].mean() < 0
 
-
-def test_conductivity_of_converged_state(pnp):
-    """Problem.conductivity (device plane currents, then the host-only
-    pnp_conductivity) on a converged biased state against the oracle's
-    conductivity of the oracle's discrete currents, reduced and in S/cm."""
-    spec = dilute(0.0, 0.5, mix=1)
-    with pnp.Problem(spec) as P:
-        phi, rho, st = P.gummel_solve()
-        sig = P.conductivity(phi, rho, D_m2_per_s=1e-10)
-    assert st["status"] == 0
-    mu, _ = oracle.excess_mu(spec, rho)
-    mub = oracle.bulk_mu(spec.R, spec.rho_b)
-    flux = [oracle.np_flux(spec, i, phi, mu[i], mub[i], rho[i] * np.exp(spec.q[i] * phi + mu[i]))
-            for i in range(spec.s)]
-    ref = oracle.conductivity(spec, flux, D_m2_per_s=1e-10)
-    assert sig[0] > 0
-    assert sig[0] == pytest.approx(ref[0], rel=1e-8)
-    assert sig[1] == pytest.approx(ref[1], rel=1e-8)
-
-
-@pytest.mark.parametrize("depth2", [0.0, 0.7])
-def test_square_well_energy_matches_oracle(pnp, depth2):
-    """pnp_square_well_energy (the device well field, summed against rho on
-    the host) against the oracle's direct-quadrature F_sh; a film without
-    wells gives exactly zero."""
-    spec = film_gummel(16, 12, 10, nsites=6)
-    spec.depth = (1.0, depth2)
-    rng = np.random.default_rng(12)
-    rho = np.stack([spec.rho_b[i] * rng.lognormal(0.0, 0.3, spec.shape) for i in range(spec.s)])
-    with pnp.Problem(spec) as P:
-        F = P.square_well_energy(rho)
-    ref = oracle.square_well_energy(spec, rho)
-    assert ref < 0
-    assert F == pytest.approx(ref, rel=1e-10)
-    spec.depth = (0.0, 0.0)
-    with pnp.Problem(spec) as P:
-        assert P.square_well_energy(rho) == 0.0
