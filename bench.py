@@ -188,6 +188,24 @@ def stage_bytes(name, dims, cs, s):
     }[name]
 
 
+STAGES = ("x_fwd", "y_fwd", "z_mac", "y_inv", "x_fused", "y_fwd_psi", "z_back", "y_inv_mu", "x_inv")
+
+
+def path_bytes(dims, cs, s):
+    """Algorithmic bytes of one whole mu_ex: the nine stages' sum."""
+    return sum(stage_bytes(n, dims, cs, s) for n in STAGES)
+
+
+def pass_model_bytes(dims, s, w):
+    """Bytes of the unfused pass model of one mu_ex: T = s + 10 + min(10, 1 + 4s)
+    + s real 3D transforms (the densities, the ten weighted densities, the
+    non-zero derivative fields, the chemical potentials), each three axis
+    passes that read and write all Lx Ly Lz values of w bytes."""
+    nx, ny, nz, Lx, Ly, Lz = dims
+    T = s + 10 + min(10, 1 + 4 * s) + s
+    return T * 3 * 2 * Lx * Ly * Lz * w
+
+
 def stage_flops(name, dims, s):
     """Algorithmic floating-point operations of one launch of a stage: 5 L log2 L
     per complex transform of length L (a pair of real lines shares one), plus
@@ -403,6 +421,17 @@ def run_gpu(args, world, rank, local):
                 "share_of_step": share, "peak_source": peak_kind,
                 "fp32_tflops": f / (avg * 1e-3) / 1e12}
 
+    def path_roof(prec):
+        # the whole step against the copy bandwidth: this design's algorithmic
+        # bytes, and the unfused pass model of the same transforms
+        sec = results[prec]["ms"] * 1e-3
+        wide = prec in ("fp64", "df64")
+        b = path_bytes(dims, 16 if wide else 8, SPECIES)
+        m = pass_model_bytes(dims, SPECIES, 8 if wide else 4)
+        return {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": peak_kind,
+                "bytes_per_step": b, "achieved": b / sec / 1e9, "frac": b / sec / 1e9 / peak,
+                "pass_model_bytes": m, "pass_model_gbs": m / sec / 1e9, "pass_model_frac": m / sec / 1e9 / peak}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle
@@ -433,13 +462,15 @@ def run_gpu(args, world, rank, local):
                     "h2d_bytes_per_step": int(rho.nbytes), "d2h_bytes_per_step": int(rho.nbytes),
                     "ms_per_step": e2e_ms},
             "roofline": roof(head),
+            "path_roofline": path_roof(head),
             "max_rel_err_vs_fp64": errs.get(head), "error_bound_vs_oracle": ERROR_BOUND[head],
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": {VARIANT_NAME[p]: {
                 "value": vals[p], "unit": "Gpoints/s", "ms_per_step": results[p]["ms"],
-                "dtype": DTYPE[p], "roofline": roof(p), "max_rel_err_vs_fp64": errs.get(p),
+                "dtype": DTYPE[p], "roofline": roof(p), "path_roofline": path_roof(p),
+                "max_rel_err_vs_fp64": errs.get(p),
                 "error_bound_vs_oracle": ERROR_BOUND[p]}
                 for p in variants[1:]},
             "stages_ms": {p: {k: v[0] / max(v[1], 1) for k, v in results[p]["stages"].items()}
