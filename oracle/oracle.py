@@ -91,6 +91,7 @@ def _declare(L):
     L.oracle_mu_hs.argtypes = [P, _dp, _dp]
     L.oracle_site_density.argtypes = [P, _dp]
     L.oracle_mu_sh.argtypes = [P, _dp, _dp]
+    L.oracle_mu_el.argtypes = [P, _dp, _dp, _dp, ctypes.c_double, _dp]
     L.oracle_excess_mu.restype = ctypes.c_long
     L.oracle_excess_mu.argtypes = [P, _dp, _dp]
     L.oracle_bulk_mu.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -248,6 +249,22 @@ def mu_sh(spec, rho_s):
     rs = _f64(rho_s)
     out = np.zeros((P.s,) + P.shape)
     lib().oracle_mu_sh(P.ref, _ptr(rs), _ptr(out))
+    return out
+
+
+def mu_el(spec, rho=None, wave=None):
+    """Electrostatic-correlation chemical potential of Sec 2.3.4 (MSA), the
+    integral term: -sum_j int C_ij(|r - r'|) (rho_j(r') - rho_b,j) dr' over
+    Omega.  Returns [s, nz, ny, nx].  ``wave`` = (k[3], phase, amp[s]) replaces
+    rho_j - rho_b,j by amp_j cos(k.r + phase) evaluated at the nodes."""
+    P = Problem(spec)
+    out = np.zeros((P.s,) + P.shape)
+    if wave is None:
+        r = _f64(rho).reshape(P.s, -1)
+        lib().oracle_mu_el(P.ref, _ptr(r), _ptr(out), None, 0.0, None)
+    else:
+        k, ph, amp = wave
+        lib().oracle_mu_el(P.ref, None, _ptr(out), _ptr(_f64(k)), float(ph), _ptr(_f64(amp)))
     return out
 
 
