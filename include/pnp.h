@@ -369,6 +369,17 @@ int pnp_conductivity(const pnp_problem_desc *desc, const double *flux, double D_
  * Errors: PNP_ERR_INVALID. */
 int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, double *out);
 
+/* Host-only: the discrete MSA pair kernel of Sec 2.3.4 for species i, j of
+ * a descriptor, C_ij(r) = -q_i q_j l_B [2B/s - (B/s)^2 r - 1/r] on the ball
+ * r <= s = R_i + R_j, B = [xi + 1 - sqrt(1 + 2 xi)] / xi, xi = kappa s,
+ * kappa^2 = 4 pi l_B sum_k rho_b,k q_k^2 (l_B from the descriptor's T, eps_r
+ * and h_nm), by the ball quadrature of Sec 3.5 with the descriptor's counts,
+ * each node deposited trilinearly.  out gets (2S+1)^3 values in the layout
+ * of pnp_weight_stencil; S >= ceil(s) + 1.  The set-up stencil of the
+ * electrostatic-correlation term; the device pipeline does not apply it yet.
+ * Errors: PNP_ERR_INVALID. */
+int pnp_msa_stencil(const pnp_problem_desc *desc, int i, int j, int S, double *out);
+
 /* Host-only diagnostic: the real octant of that stencil's DFT on an
  * Lx x Ly x Lz periodic grid, as the set-up stores it: out[kz][ky][kx]
  * (k <= L/2, x fastest) = sum_m K[m] f(kx mx) f(ky my) f(kz mz), f = cos on

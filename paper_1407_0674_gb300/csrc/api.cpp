@@ -285,6 +285,24 @@ int pnp_weight_stencil(int kind, double r_in, double r_out, int nmu, int ntheta,
     return PNP_OK;
 }
 
+int pnp_msa_stencil(const pnp_problem_desc *desc, int i, int j, int S, double *out) {
+    if (!desc || !out) return PNP_ERR_INVALID;
+    Problem p;
+    std::string why;
+    const int rc = validate_and_copy(desc, &p, &why);
+    if (rc) return rc;
+    if (i < 0 || j < 0 || i >= p.s || j >= p.s) return PNP_ERR_INVALID;
+    const double sigma = p.R[i] + p.R[j];
+    if (S < (int)std::ceil(sigma) + 1 || S > 64) return PNP_ERR_INVALID;
+    double kappa2 = 0.0;
+    for (int k = 0; k < p.s; ++k) kappa2 += 4.0 * M_PI * p.lB * p.rho_b[k] * p.q[k] * p.q[k];
+    const double B = msa_B(std::sqrt(kappa2) * sigma);
+    Stencil st;
+    build_msa_stencil((double)p.q[i] * p.q[j] * p.lB, B, sigma, p.quad[0], p.quad[1], p.quad[2], S, st);
+    std::memcpy(out, st.K.data(), sizeof(double) * st.K.size());
+    return PNP_OK;
+}
+
 int pnp_weight_spectrum(int kind, double r_in, double r_out, int nmu, int ntheta, int nr, int S, int Lx, int Ly,
                         int Lz, double *out) {
     if (!out || Lx < 2 * S + 1 || Ly < 2 * S + 1 || Lz < 2 * S + 1 || Lx > 4096 || Ly > 4096 || Lz > 4096)

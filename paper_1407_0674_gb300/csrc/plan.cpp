@@ -181,6 +181,29 @@ void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, 
     for (const Node &n : nodes(false, r_in, r_out, nmu, ntheta, nr)) deposit(out, n.p, n.w);
 }
 
+// MSA pair kernel of Sec 2.3.4 on the ball |r| <= sigma, deposited like the
+// FMT weights: C(r) = -qq_lB [2B/sigma - (B/sigma)^2 r - 1/r], qq_lB = q_i q_j l_B.
+// The quadrature weight carries r^2, so C's 1/r stays finite at every node.
+void build_msa_stencil(double qq_lB, double B, double sigma, int nmu, int ntheta, int nr, int S, Stencil &out) {
+    reset(out, S);
+    for (const Node &n : nodes(false, 0.0, sigma, nmu, ntheta, nr)) {
+        const double r = std::sqrt(n.p[0] * n.p[0] + n.p[1] * n.p[1] + n.p[2] * n.p[2]);
+        const double C = -qq_lB * (2.0 * B / sigma - (B / sigma) * (B / sigma) * r - 1.0 / r);
+        deposit(out, n.p, n.w * C);
+    }
+}
+
+// MSA screening factor B = [xi + 1 - sqrt(1 + 2 xi)] / xi of Sec 2.3.4, taken
+// as 2 xi / (1 + sqrt(1 + 2 xi))^2 (the same number) where the printed form
+// cancels.
+double msa_B(double xi) {
+    if (xi < 1e-3) {
+        const double t = 1.0 + std::sqrt(1.0 + 2.0 * xi);
+        return 2.0 * xi / (t * t);
+    }
+    return (xi + 1.0 - std::sqrt(1.0 + 2.0 * xi)) / xi;
+}
+
 // out[kz][ky][kx] (kz <= Lz/2, ky <= Ly/2, kx <= Lx/2) =
 //   scale * sum_m K[m] f_x(kx mx) f_y(ky my) f_z(kz mz),  f = cos(2 pi k m / L)
 // on even axes and sin(...) on odd axes.  The stencil is even or odd in each

@@ -125,6 +125,8 @@ void length_candidates(const Problem *p, int axis, std::vector<int> *out);
 void gauss_legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w);
 void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil out[kNumKernels]);
 void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
+void build_msa_stencil(double qq_lB, double B, double sigma, int nmu, int ntheta, int nr, int S, Stencil &out);
+double msa_B(double xi);
 void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
 double bjerrum_length_h(double T, double eps_r, double h_nm);
 double conductivity_unit_S_per_cm(double T, double h_nm, double D_m2_per_s);

@@ -133,6 +133,7 @@ def lib():
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_conductivity.argtypes = [ctypes.POINTER(Desc), _dp, ctypes.c_double, _dp]
         L.pnp_square_well_energy.argtypes = [vp, _dp, _dp]
+        L.pnp_msa_stencil.argtypes = [ctypes.POINTER(Desc), ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_weight_stencil.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, _dp]
         L.pnp_weight_spectrum.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -251,6 +252,16 @@ def weight_stencil(kind, r_out, r_in=0.0, nmu=0, ntheta=0, nr=0, S=None):
     out = np.zeros((2 * S + 1,) * 3)
     _check(lib().pnp_weight_stencil(int(kind), float(r_in), float(r_out), int(nmu), int(ntheta), int(nr), int(S),
                                     _ptr(out)), "pnp_weight_stencil")
+    return out
+
+
+def msa_stencil(spec, i, j, S=None):
+    """pnp_msa_stencil: the MSA pair kernel C_ij on the grid, [mz][my][mx]."""
+    if S is None:
+        S = int(np.ceil(spec.R[i] + spec.R[j])) + 1
+    dh = DescHolder(spec)
+    out = np.zeros((2 * S + 1,) * 3)
+    _check(lib().pnp_msa_stencil(ctypes.byref(dh.desc), int(i), int(j), int(S), _ptr(out)), "pnp_msa_stencil")
     return out
 
 

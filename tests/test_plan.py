@@ -190,3 +190,56 @@ def test_conductivity_rejections(pnp):
         with pytest.raises(pnp.PnpError) as e:
             pnp.conductivity(s, f, D)
         assert e.value.code == pnp.ERR_INVALID
+
+
+def _msa_spec():
+    return ProblemSpec(nx=8, ny=6, nz=5, bc=("P", "P", "P"), R=(1.0, 1.5, 0.7), q=(1, -1, 2),
+                       rho_b=(0.004, 0.006, 0.001))
+
+
+@pytest.mark.parametrize("i,j", [(0, 0), (0, 1), (1, 2), (2, 2)])
+def test_msa_stencil_matches_independent_table(pnp, i, j):
+    """pnp_msa_stencil (row a1's set-up for the MSA term) against the brute
+    module's table from numpy's ball nodes, and its sum against the exact
+    ball integral of C_ij."""
+    import math
+    import brute
+    spec = _msa_spec()
+    lB = pnp.plan(spec)[0]["bjerrum_h"]          # the library's l_B (pinned to Table 1 above)
+    kap = math.sqrt(4 * math.pi * lB * sum(r * q * q for r, q in zip(spec.rho_b, spec.q)))
+    s = spec.R[i] + spec.R[j]
+    gs = 0.5 * (math.sqrt(1 + 2 * kap * s) - 1)
+    B = gs / (1 + gs)
+    qq = spec.q[i] * spec.q[j]
+    p, w, u = brute.nodes("ball", s)
+    r = np.linalg.norm(p, axis=1)
+    C = -qq * lB * (2 * B / s - (B / s) ** 2 * r - 1 / r)
+    S = int(np.ceil(s)) + 1
+    ref = brute.kernel_table(p, w * C, u, S)
+    got = pnp.msa_stencil(spec, i, j)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    exact = -4 * math.pi * qq * lB * s * s * (2 * B / 3 - B * B / 4 - 0.5)
+    assert got.sum() == pytest.approx(exact, rel=1e-12)
+
+
+def test_msa_stencil_convolution_equals_oracle(pnp):
+    """The library's stencils, applied as periodic correlations to rho - rho_b,
+    give the oracle's mu_el: both sides compute the same discrete operator."""
+    spec = _msa_spec()
+    rng = np.random.default_rng(6)
+    rho = np.stack([rb * rng.lognormal(0, 0.3, spec.shape) for rb in spec.rho_b])
+    ref = oracle.mu_el(spec, rho)
+    for i in range(spec.s):
+        got = np.zeros(spec.shape)
+        for j in range(spec.s):
+            K = pnp.msa_stencil(spec, i, j)
+            S = (K.shape[0] - 1) // 2
+            d = rho[j] - spec.rho_b[j]
+            for mz in range(-S, S + 1):
+                for my in range(-S, S + 1):
+                    for mx in range(-S, S + 1):
+                        k = K[mz + S, my + S, mx + S]
+                        if k != 0.0:
+                            got -= k * np.roll(d, (-mz, -my, -mx), axis=(0, 1, 2))
+        # the oracle's l_B comes from a 10-digit k_B in eV/K: 1.7e-11 from the SI value
+        np.testing.assert_allclose(got, ref[i], rtol=0, atol=1e-10 * np.abs(ref[i]).max())
