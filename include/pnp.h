@@ -343,7 +343,7 @@ int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double 
  * Errors: PNP_ERR_INVALID, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
 int pnp_square_well_energy(pnp_problem *p, const double *rho, double *F_sh);
 
-/* Host-only: ionic conductivity from plane currents (Sec 4, size dependency
+/* Host-only: ionic conductivity from plane currents (Sec 4.2.1, size dependency
  * of the conductivity: the current density along the transport axis averaged
  * over its length, divided by the field).  flux [nspecies][nz+1] holds each
  * species' currents through the z faces as pnp_plane_flux returns them

@@ -344,7 +344,7 @@ def np_flux(spec, i, phi, mu, mu_b, rhobar):
 
 
 def conductivity(spec, flux, D_m2_per_s=0.0):
-    """Ionic conductivity (Sec 4, size dependency of the conductivity): the
+    """Ionic conductivity (Sec 4.2.1, size dependency of the conductivity): the
     current density along the transport axis averaged over its length, over
     the applied field.  flux [s][nz+1] are the species' currents through the
     z faces (np_flux: reduced units, h = 1, each summed over the nx*ny faces of

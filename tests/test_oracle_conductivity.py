@@ -1,4 +1,4 @@
-"""Pins of the oracle's conductivity (Sec 4: current density averaged along
+"""Pins of the oracle's conductivity (Sec 4.2.1: current density averaged along
 the transport axis over the applied field).
 
 - Exact discrete steady state: with uniform densities rho_b, a linear phi
