@@ -78,6 +78,8 @@ def dist_init():
         import torch.distributed as dist
         import torch
         backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)     # one GPU per rank before NCCL sees a device
         dist.init_process_group(backend)
     return world, rank, local
 
