@@ -16,6 +16,15 @@
  *   delta-shell integrals by the (theta, phi) change of variables         Sec 3.5
  *   7-point harmonic-mean finite differences                              Sec 3.1
  *   relaxed Gummel iteration on the Slotboom form                         Sec 2.1, 3.2
+ *   White Bear (MFMT) derivatives, series near n3 = 0                     Sec 2.3.1
+ *   equilibrium cDFT initial guess (Poisson-Boltzmann Newton steps)       Sec 3.2.1
+ *   screened Poisson step, per-point adaptive relaxation (options)        Sec 3.2
+ *   Anderson-accelerated Gummel iteration (an extension)                  Sec 3.2
+ *   plane currents through the z faces                                    Sec 2.1, 3.1
+ *   MSA electrostatic-correlation term (integral part)                    Sec 2.3.4
+ *
+ * Every function is pinned by a CPU test against closed forms, brute force,
+ * independent library routines or invariants (see the tests named oracle_*).
  *
  * Every integral is evaluated as a DIRECT real-space sum over quadrature nodes
  * (no FFT).  The value at an off-grid node is trilinear in the 8 surrounding
