@@ -109,3 +109,10 @@ def test_struct_field_offsets_match_header(L, ctype, cname):
         out = [int(x) for x in subprocess.check_output([exe]).split()]
     for f, off in zip(fields, out):
         assert getattr(ctype, f).offset == off, (cname, f)
+
+
+def test_binding_declares_every_header_function(L):
+    """Every function of include/pnp.h has ctypes argument types in the
+    binding (without them ctypes would pass doubles as ints)."""
+    missing = [f for f in pnp.header_functions() if getattr(L, f).argtypes is None]
+    assert missing == []
