@@ -27,3 +27,9 @@ def test_path_bytes_are_the_stage_sum():
     # the z_back stage is the bench's dominant FP32 kernel: 568 MB per launch
     assert bench.stage_bytes("z_back", DIMS, 8, 3) == 568416828
     assert bench.path_bytes(DIMS, 8, 3) < 0.3 * bench.pass_model_bytes(DIMS, 3, 4)
+
+
+def test_kernels_per_step_of_the_bench_workload():
+    # nine stages, the derivative stage split into three kernels on a register length
+    assert sum(bench.kernels_per_stage(n, 256) for n in bench.STAGES) == 11
+    assert sum(bench.kernels_per_stage(n, 270) for n in bench.STAGES) == 9
