@@ -7,6 +7,7 @@ import os
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_1407_0674_gb300 import build, pnp
@@ -116,3 +117,58 @@ def test_binding_declares_every_header_function(L):
     binding (without them ctypes would pass doubles as ints)."""
     missing = [f for f in pnp.header_functions() if getattr(L, f).argtypes is None]
     assert missing == []
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "pnp.h"
+int main(void) {
+    pnp_problem_desc d;
+    if (pnp_desc_init(&d) != PNP_OK) return 1;
+    int q[2] = {1, -1};
+    double R[2] = {2.0, 2.0}, rb[2] = {0.006, 0.006}, mu[2];
+    d.nx = 32; d.ny = 32; d.nz = 30;
+    d.bc[0] = PNP_BC_PERIODIC; d.bc[1] = PNP_BC_PERIODIC; d.bc[2] = PNP_BC_DIRICHLET;
+    d.nspecies = 2; d.valence = q; d.radius = R; d.rho_bulk = rb;
+    d.phi_lo = 0.0; d.phi_hi = 0.5;
+    pnp_problem_info info;
+    if (pnp_plan_problem(&d, &info, mu) != PNP_OK) return 2;
+    printf("%d %d %d %d %.17g %.17g %.17g\n", info.fft_len[0], info.fft_len[1], info.fft_len[2],
+           info.stencil_halfwidth, mu[0], mu[1], info.bjerrum_h);
+    double flux[2 * 31];
+    for (int k = 0; k < 31; ++k) { flux[k] = -1.0; flux[31 + k] = 1.0; }
+    double sigma[2];
+    if (pnp_conductivity(&d, flux, 1e-10, sigma) != PNP_OK) return 3;
+    printf("%.17g %.17g\n", sigma[0], sigma[1]);
+    d.nspecies = 0;
+    printf("%d %s\n", pnp_plan_problem(&d, &info, NULL), pnp_error_string(PNP_ERR_INVALID));
+    return 0;
+}
+"""
+
+
+def test_plain_c_client_links_and_calls_host_entry_points(L):
+    """A C program built against include/pnp.h and linked to the shared
+    library calls the host-only entry points (no device needed): the plan
+    and reservoir mu match the Python binding's, the conductivity of unit
+    currents is the closed form, and a bad descriptor is refused."""
+    from workloads import ProblemSpec
+    lib_dir = os.path.dirname(pnp.LIB_PATH)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "client.c")
+        open(c, "w").write(C_CLIENT)
+        exe = os.path.join(d, "client")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe, "-L", lib_dir,
+                               "-lpnp_gb300", "-Wl,-rpath," + lib_dir])
+        lines = subprocess.check_output([exe], text=True).splitlines()
+    a = lines[0].split()
+    spec = ProblemSpec(nx=32, ny=32, nz=30, bc=("P", "P", "D"), R=(2.0, 2.0), q=(1, -1), rho_b=(0.006, 0.006),
+                       phi_hi=0.5)
+    info, mu = pnp.plan(spec)
+    assert tuple(int(x) for x in a[:3]) == info["fft_len"] and int(a[3]) == info["stencil_halfwidth"]
+    assert float(a[4]) == mu[0] and float(a[5]) == mu[1] and float(a[6]) == info["bjerrum_h"]
+    sig = [float(x) for x in lines[1].split()]
+    # charge current -2 per face over 32*32 faces, field -0.5/31
+    assert sig[0] == pytest.approx((-2.0 / 1024) / (-0.5 / 31), rel=1e-14)
+    assert sig == list(pnp.conductivity(spec, np.stack([-np.ones(31), np.ones(31)]), 1e-10))
+    assert lines[2].startswith(f"{pnp.ERR_INVALID} ")
