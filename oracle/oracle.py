@@ -75,6 +75,7 @@ class _Problem(ctypes.Structure):
         ("rho_mix", ctypes.c_int),
         ("screened", ctypes.c_int),
         ("fmt", ctypes.c_int),
+        ("msa", ctypes.c_int),
     ]
 
 
@@ -171,6 +172,7 @@ class Problem:
         st.rho_mix = int(getattr(spec, "rho_mix", 0))
         st.screened = 1 if getattr(spec, "screened_poisson", False) else 0
         st.fmt = int(getattr(spec, "fmt", 0))
+        st.msa = 1 if getattr(spec, "msa", False) else 0
         self.st = st
 
     @property
@@ -295,6 +297,8 @@ def excess_mu(spec, rho):
 def excess_mu_sampled(spec, rho, flat_idx):
     """mu_ex at the given flat grid indices only (same sums as excess_mu).
     Returns [s, nsamp]."""
+    if getattr(spec, "msa", False):
+        raise NotImplementedError("excess_mu_sampled evaluates mu_hs + mu_sh only")
     P = Problem(spec)
     r = _f64(rho)
     idx = np.ascontiguousarray(np.asarray(flat_idx, dtype=np.int64))

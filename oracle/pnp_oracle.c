@@ -231,6 +231,7 @@ typedef struct {
     int screened;              /* Gummel Poisson step: 0 linear solve, 1 one Newton step
                                   with the densities' Boltzmann dependence on phi */
     int fmt;                   /* 0 Rosenfeld (Sec 2.3.1), 1 White Bear (MFMT) */
+    int msa;                   /* 1: mu_ex also carries the MSA term of Sec 2.3.4 */
 } oracle_problem;
 
 static grid_t cdft_grid(const oracle_problem *p)
@@ -617,7 +618,8 @@ void oracle_mu_el(const oracle_problem *p, const double *rho, double *mu_el,
     free(drho);
 }
 
-/* mu_ex,i = mu_hs,i + mu_sh,i (Sec 2.3).  Returns the packing-error count. */
+/* mu_ex,i = mu_hs,i + mu_sh,i (Sec 2.3), plus mu_el,i (Sec 2.3.4) when the
+ * problem asks for it.  Returns the packing-error count. */
 long oracle_excess_mu(const oracle_problem *p, const double *rho, double *mu)
 {
     long N = (long)p->nx * p->ny * p->nz;
@@ -631,6 +633,10 @@ long oracle_excess_mu(const oracle_problem *p, const double *rho, double *mu)
     oracle_site_density(p, rs);
     oracle_mu_sh(p, rs, msh);
     for (long k = 0; k < p->s * N; ++k) mu[k] += msh[k];
+    if (p->msa) {
+        oracle_mu_el(p, rho, msh, 0, 0.0, 0);
+        for (long k = 0; k < p->s * N; ++k) mu[k] += msh[k];
+    }
     free(n); free(psi); free(rs); free(msh);
     return bad;
 }

@@ -177,6 +177,8 @@ class DescHolder:
     points to kept alive."""
 
     def __init__(self, spec, precision="fp64"):
+        if getattr(spec, "msa", False):
+            raise PnpError(ERR_INVALID, "the MSA term is not applied by the library yet")
         d = Desc()
         lib().pnp_desc_init(ctypes.byref(d))
         s = len(spec.R)

@@ -32,7 +32,7 @@ from workloads import ProblemSpec, bulk_density
 SHAPE = (7, 6, 6)   # (nz, ny, nx)
 
 
-def make_spec(rho_mix, screened, fmt, sweeps):
+def make_spec(rho_mix, screened, fmt, sweeps, msa=False):
     nz, ny, nx = SHAPE
     rng = np.random.default_rng(21)
     R = (1.5, 2.0)
@@ -42,7 +42,7 @@ def make_spec(rho_mix, screened, fmt, sweeps):
                        sites=rng.uniform(0, 1, (4, 3)) * np.array([nx, ny, nz]), site_alpha=0.8,
                        rho_f=rng.normal(0, 0.002, SHAPE), phi_lo=0.0, phi_hi=0.5,
                        lambda_phi=0.4, lambda_rho=0.3, rho_mix=rho_mix, tol=0.0, max_iter=sweeps,
-                       screened_poisson=screened, fmt=fmt)
+                       screened_poisson=screened, fmt=fmt, msa=msa)
 
 
 def start_state(spec, seed=5):
@@ -80,6 +80,24 @@ class DenseSweep:
                   + np.kron(lap1d(nz, "D"), np.eye(ny * nx)))
         self.lB = units.bjerrum_length_h(spec.temperature_K, spec.eps_r, spec.h_nm)
         self.mu_b = oracle.bulk_mu(spec.R, spec.rho_b, fmt=spec.fmt)
+        # MSA pair operators (Sec 2.3.4), B from the textbook screening parameter
+        self.msa = None
+        if getattr(spec, "msa", False):
+            kap = math.sqrt(4 * math.pi * self.lB * sum(r * q * q for r, q in zip(spec.rho_b, spec.q)))
+            self.msa = [[None] * spec.s for _ in range(spec.s)]
+            for i in range(spec.s):
+                for j in range(spec.s):
+                    qq = spec.q[i] * spec.q[j]
+                    if qq == 0:
+                        continue
+                    sg = spec.R[i] + spec.R[j]
+                    gs = 0.5 * (math.sqrt(1 + 2 * kap * sg) - 1)
+                    B = gs / (1 + gs)
+                    pb, wb, ub = brute.nodes("ball", sg)
+                    r = np.linalg.norm(pb, axis=1)
+                    C = -qq * self.lB * (2 * B / sg - (B / sg) ** 2 * r - 1 / r)
+                    rch = int(math.ceil(sg)) + 1
+                    self.msa[i][j] = brute.dense_operator(brute.kernel_table(pb, wb * C, ub, rch), rch, spec.shape, per)
         self.lam = np.full((spec.s,) + spec.shape, spec.lambda_rho)
         self.prev = np.zeros((spec.s,) + spec.shape)
 
@@ -102,6 +120,10 @@ class DenseSweep:
             m = M2.T @ (c0 * P[0] + c1 * P[1] + P[2]) + M3.T @ P[3]
             for c in range(3):
                 m += Mv[:, :, c].T @ (c1 * P[4 + c] + P[7 + c])
+            if self.msa is not None:
+                for j in range(spec.s):
+                    if self.msa[i][j] is not None:
+                        m = m - self.msa[i][j] @ (rho[j] - spec.rho_b[j]).reshape(-1)
             out.append((m + self.mu_sh[i]).reshape(spec.shape))
         return np.stack(out)
 
@@ -148,15 +170,16 @@ class DenseSweep:
         return phi_new, rho_new, res
 
 
-@pytest.mark.parametrize("rho_mix,screened,fmt,sweeps", [
-    (0, False, 0, 1),      # linear density relaxation, plain Poisson step
-    (1, False, 0, 2),      # geometric
-    (2, True, 0, 2),       # step-limited geometric, screened Newton step
-    (3, True, 0, 4),       # per-point adaptive: factors carried across sweeps
-    (1, False, 1, 2),      # White Bear functional
+@pytest.mark.parametrize("rho_mix,screened,fmt,sweeps,msa", [
+    (0, False, 0, 1, False),      # linear density relaxation, plain Poisson step
+    (1, False, 0, 2, False),      # geometric
+    (2, True, 0, 2, False),       # step-limited geometric, screened Newton step
+    (3, True, 0, 4, False),       # per-point adaptive: factors carried across sweeps
+    (1, False, 1, 2, False),      # White Bear functional
+    (2, True, 0, 2, True),        # with the MSA electrostatic correlations
 ])
-def test_sweeps_match_dense_composition(rho_mix, screened, fmt, sweeps):
-    spec = make_spec(rho_mix, screened, fmt, sweeps)
+def test_sweeps_match_dense_composition(rho_mix, screened, fmt, sweeps, msa):
+    spec = make_spec(rho_mix, screened, fmt, sweeps, msa)
     phi0, rho0 = start_state(spec)
     r = oracle.gummel(spec, phi0=phi0, rho0=rho0)
     assert r["status"] == 1 and r["iters"] == sweeps

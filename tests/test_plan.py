@@ -243,3 +243,12 @@ def test_msa_stencil_convolution_equals_oracle(pnp):
                             got -= k * np.roll(d, (-mz, -my, -mx), axis=(0, 1, 2))
         # the oracle's l_B comes from a 10-digit k_B in eV/K: 1.7e-11 from the SI value
         np.testing.assert_allclose(got, ref[i], rtol=0, atol=1e-10 * np.abs(ref[i]).max())
+
+
+def test_msa_problems_are_refused_by_the_binding(pnp):
+    """The device path does not apply the MSA term yet: a problem asking for
+    it is refused rather than solved without it."""
+    spec = dataclasses.replace(_msa_spec(), msa=True)
+    with pytest.raises(pnp.PnpError) as e:
+        pnp.plan(spec)
+    assert e.value.code == pnp.ERR_INVALID

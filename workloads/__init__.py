@@ -64,6 +64,7 @@ class ProblemSpec:
     eq_max_iter: int = 0                     # its iteration cap (0 = library default)
     screened_poisson: bool = False           # Gummel Poisson step as one screened Newton step
     fmt: int = 0                             # hard-sphere functional: 0 Rosenfeld, 1 White Bear (MFMT)
+    msa: bool = False                        # add the MSA electrostatic-correlation term (oracle only so far)
 
     @property
     def s(self) -> int:
