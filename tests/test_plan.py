@@ -252,3 +252,41 @@ def test_msa_problems_are_refused_by_the_binding(pnp):
     with pytest.raises(pnp.PnpError) as e:
         pnp.plan(spec)
     assert e.value.code == pnp.ERR_INVALID
+
+
+def test_msa_spectral_plan_on_zero_extended_axes(pnp):
+    """A numpy prototype of the planned device MSA term: zero-padded FFT
+    products of the library's stencils with rho_j, minus nothing for the bulk,
+    plus the fixed bulk field sum_j rho_b,j (C_ij conv 1_Omega), equals the
+    oracle's mu_el on a grid zero-extended on every axis."""
+    spec = dataclasses.replace(_msa_spec(), nx=9, ny=7, nz=6, bc=("N", "N", "D"))
+    rng = np.random.default_rng(11)
+    rho = np.stack([rb * rng.lognormal(0, 0.3, spec.shape) for rb in spec.rho_b])
+    ref = oracle.mu_el(spec, rho)
+    n = np.array(spec.shape)
+    Smax = max(int(np.ceil(spec.R[i] + spec.R[j])) + 1 for i in range(spec.s) for j in range(spec.s))
+    L = tuple(int(v) for v in n + Smax)
+
+    def embed(K):
+        S = (K.shape[0] - 1) // 2
+        g = np.zeros(L)
+        m = np.arange(-S, S + 1)
+        zz, yy, xx = np.meshgrid(m % L[0], m % L[1], m % L[2], indexing="ij")
+        np.add.at(g, (zz, yy, xx), K)
+        return np.fft.rfftn(g)
+
+    def pad(f):
+        g = np.zeros(L)
+        g[:n[0], :n[1], :n[2]] = f
+        return np.fft.rfftn(g)
+
+    one = pad(np.ones(spec.shape))
+    for i in range(spec.s):
+        acc = np.zeros(L[:2] + (L[2] // 2 + 1,), dtype=complex)
+        bulk = np.zeros_like(acc)
+        for j in range(spec.s):
+            Ck = embed(pnp.msa_stencil(spec, i, j))
+            acc += Ck * pad(rho[j])
+            bulk += spec.rho_b[j] * Ck * one
+        got = np.fft.irfftn(-acc + bulk, s=L, axes=(0, 1, 2))[:n[0], :n[1], :n[2]]
+        np.testing.assert_allclose(got, ref[i], rtol=0, atol=1e-10 * np.abs(ref[i]).max())
