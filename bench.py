@@ -501,6 +501,18 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
+def oracle_sweep_seconds(spec, sweeps):
+    """Mean wall time of one relaxed Gummel sweep of the CPU oracle on `spec`,
+    over its first `sweeps` sweeps from the default start (the oracle as it
+    stands, all host cores).  Returns (seconds per sweep, threads)."""
+    import dataclasses
+    from oracle import oracle
+    s = dataclasses.replace(spec, max_iter=sweeps, tol=0.0)
+    t0 = time.perf_counter()
+    oracle.gummel(s)
+    return (time.perf_counter() - t0) / sweeps, oracle.num_threads()
+
+
 def run_solves(args, world, rank, local):
     """Gummel workloads: film (one solve), batch (many solves through the
     server against the same solves one at a time), serve (Poisson arrivals)."""
@@ -526,6 +538,13 @@ def run_solves(args, world, rank, local):
                                        "64 sites, bias 0.1 kT/e) to residual 1e-8"},
                 "iterations": st["iterations"], "linear_iterations": st["linear_iterations"],
                 "residual": st["residual"]}
+        if rank == 0 and not args.no_cpu_baseline:
+            k = 2
+            per, threads = oracle_sweep_seconds(spec, k)
+            est = per * st["iterations"]
+            line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                                    "sample": f"first {k} Gummel sweeps of the same film ({per * k:.1f} s), "
+                                              f"extrapolated to the {st['iterations']} iterations of the GPU solve"}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -33,3 +33,11 @@ def test_kernels_per_step_of_the_bench_workload():
     # nine stages, the derivative stage split into three kernels on a register length
     assert sum(bench.kernels_per_stage(n, 256) for n in bench.STAGES) == 11
     assert sum(bench.kernels_per_stage(n, 270) for n in bench.STAGES) == 9
+
+
+def test_oracle_sweep_timing_helper():
+    """The film workload's CPU baseline: the oracle's per-sweep time on a small
+    film (timing only; the sweep itself is pinned elsewhere)."""
+    from workloads import film_gummel
+    per, threads = bench.oracle_sweep_seconds(film_gummel(8, 8, 8), 2)
+    assert per > 0 and threads >= 1
