@@ -450,15 +450,15 @@ def run_gpu(args, world, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        from oracle import oracle
         m = args.cpu_sample
-        s2, r2 = sub_box(spec, rho, m)
-        t0 = time.perf_counter()
-        oracle.excess_mu(s2, r2)
-        dt = time.perf_counter() - t0
-        cpu = {"value": m ** 3 / dt / 1e9, "unit": "Gpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+        v, used, dt = oracle_mu_rate(spec, rho, m)
+        m1 = max(8, m // 2)
+        v1, _, dt1 = oracle_mu_rate(spec, rho, m1, threads=1)
+        cpu = {"value": v, "unit": "Gpoints/s", "cores": used, "kind": "oracle",
                "sample": f"{m}^3 sub-box of the {N_EDGE}^3 workload (same radii and densities), one full mu_ex, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s",
+               "single_core": {"value": v1, "unit": "Gpoints/s", "cores": 1,
+                               "sample": f"{m1}^3 sub-box, one full mu_ex, {dt1:.1f} s"}}
 
     if rank == 0:
         head = variants[0]
@@ -499,6 +499,25 @@ def run_gpu(args, world, rank, local):
 def _pct(v, q):
     import numpy as np
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def oracle_mu_rate(spec, rho, m, threads=None):
+    """The CPU oracle's mu_ex rate (Gpoints/s) on an m^3 sub-box of the
+    workload, with `threads` OpenMP threads (None: as configured).  Returns
+    (rate, threads used, seconds)."""
+    from oracle import oracle
+    prev = oracle.num_threads()
+    if threads is not None:
+        oracle.set_num_threads(threads)
+    try:
+        s2, r2 = sub_box(spec, rho, m)
+        t0 = time.perf_counter()
+        oracle.excess_mu(s2, r2)
+        dt = time.perf_counter() - t0
+        used = oracle.num_threads()
+    finally:
+        oracle.set_num_threads(prev)
+    return m ** 3 / dt / 1e9, used, dt
 
 
 def oracle_sweep_seconds(spec, sweeps):

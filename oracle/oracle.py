@@ -115,6 +115,7 @@ def _declare(L):
     L.oracle_equilibrium.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp, _ip,
                                      ctypes.POINTER(ctypes.c_double)]
     L.oracle_num_threads.restype = ctypes.c_int
+    L.oracle_set_num_threads.argtypes = [ctypes.c_int]
 
 
 def _ptr(a):
@@ -409,6 +410,11 @@ def gummel_anderson(spec, m=3, lin_tol=1e-13):
     hist = np.zeros(max(spec.max_iter, 1))
     st = lib().oracle_gummel_anderson(P.ref, int(m), _ptr(phi), _ptr(rho), ctypes.byref(it), _ptr(hist))
     return {"phi": phi, "rho": rho, "status": st, "iters": it.value, "hist": hist[:it.value]}
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (n <= 0: one per processor)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def num_threads() -> int:

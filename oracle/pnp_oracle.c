@@ -1450,6 +1450,16 @@ int oracle_equilibrium(const oracle_problem *p, double lam, double tol, int max_
     return status;
 }
 
+/* Thread count of the OpenMP loops (n <= 0: one per processor). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

@@ -41,3 +41,17 @@ def test_oracle_sweep_timing_helper():
     from workloads import film_gummel
     per, threads = bench.oracle_sweep_seconds(film_gummel(8, 8, 8), 2)
     assert per > 0 and threads >= 1
+
+
+def test_oracle_rate_helper_restores_threads():
+    """The CPU legs of the benchmark: the oracle's mu_ex rate on a sub-box, at
+    all cores and at one core, leaving the thread count as it found it."""
+    from oracle import oracle
+    from workloads import mu_microbench
+    spec, rho = mu_microbench(16)
+    before = oracle.num_threads()
+    v, used, dt = bench.oracle_mu_rate(spec, rho, 6, threads=1)
+    assert v > 0 and used == 1 and dt > 0
+    assert oracle.num_threads() == before
+    v2, used2, _ = bench.oracle_mu_rate(spec, rho, 6)
+    assert v2 > 0 and used2 == before
