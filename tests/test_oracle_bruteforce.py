@@ -95,3 +95,23 @@ def test_invariants():
     np.testing.assert_allclose(ns / scale, np.roll(n1, (1, -2, 3), axis=(1, 2, 3)) / scale, rtol=0, atol=1e-13)
     # positivity of the packing fraction field
     assert n1[3].min() >= 0
+
+
+@pytest.mark.parametrize("bc", [("N", "N", "D"), ("P", "P", "D")])
+def test_sampled_mu_ex_equals_full_evaluation(bc):
+    """oracle.excess_mu_sampled (used for the full-size GPU checks) equals the
+    full evaluation at every sampled point, wells included, near faces and in
+    the interior."""
+    from workloads import film_gummel
+    spec = film_gummel(12, 10, 14, nsites=5)
+    spec.bc = bc
+    spec.well_inner, spec.well_outer = 2.0, 3.0
+    rng = np.random.default_rng(17)
+    rho = np.stack([spec.rho_b[i] * rng.lognormal(0.0, 0.3, spec.shape) for i in range(spec.s)])
+    full, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    N = spec.npoints
+    flat = np.unique(np.concatenate([rng.integers(0, N, 40), [0, N - 1, spec.nx * spec.ny]]))
+    got = oracle.excess_mu_sampled(spec, rho, flat)
+    ref = full.reshape(spec.s, -1)[:, flat]
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-15)
