@@ -301,6 +301,7 @@ def run_reference(args, world, rank):
         "config": {"workload": f"mu_ex {N_EDGE}^3 x {SPECIES} species (R 1.5/2/3 h), zero-padded {PAD}^3",
                    "sample": f"{m}^3 sub-box per step", "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": v, "unit": "Gpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"{m}^3 sub-box of the {N_EDGE}^3 workload, full mu_ex per step"},
         "e2e": {"value": v, "unit": "Gpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -454,7 +455,7 @@ def run_gpu(args, world, rank, local):
         v, used, dt = oracle_mu_rate(spec, rho, m)
         m1 = max(8, m // 2)
         v1, _, dt1 = oracle_mu_rate(spec, rho, m1, threads=1)
-        cpu = {"value": v, "unit": "Gpoints/s", "cores": used, "kind": "oracle",
+        cpu = {"value": v, "unit": "Gpoints/s", "cores": used, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"{m}^3 sub-box of the {N_EDGE}^3 workload (same radii and densities), one full mu_ex, "
                          f"{dt:.1f} s",
                "single_core": {"value": v1, "unit": "Gpoints/s", "cores": 1,
@@ -494,6 +495,25 @@ def run_gpu(args, world, rank, local):
         }
         print(json.dumps(line), flush=True)
     P.close()
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the
+    architecture), for the CPU baselines' records."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip() + f" ({os.uname().machine})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip() + f" ({os.uname().machine})"
+    except OSError:
+        pass
+    return os.uname().machine
 
 
 def _pct(v, q):
@@ -562,6 +582,7 @@ def run_solves(args, world, rank, local):
             per, threads = oracle_sweep_seconds(spec, k)
             est = per * st["iterations"]
             line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                                    "cpu_model": cpu_model(),
                                     "sample": f"first {k} Gummel sweeps of the same film ({per * k:.1f} s), "
                                               f"extrapolated to the {st['iterations']} iterations of the GPU solve"}
         if rank == 0:

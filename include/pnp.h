@@ -246,8 +246,13 @@ int pnp_excess_mu_device(pnp_problem *p, const double *d_rho, double *d_mu_ex, i
  * else PNP_ERR_TOO_LARGE.  The array is held by every GPU that loads the
  * library until the process exits.  The first call on a device looks up the
  * array's address while that device is current; make that call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race and must be serialised by the caller.
+ * stream capture.  All calls share the array, which keeps the last call's
+ * contents: twiddles and spectra are uploaded (one asynchronous copy on
+ * `stream`) only when the padded lengths, radii, quadrature counts or stencil
+ * reach differ from the last successful call on the device.  Calls on one
+ * device are serialised by a lock inside the library, and every call returns
+ * only after its work on `stream` has finished, on error as well; work that
+ * overlaps a call on the GPU by any other route races on the array.
  * Errors: PNP_ERR_INVALID, PNP_ERR_TOO_LARGE, PNP_ERR_PACKING, PNP_ERR_CUDA. */
 int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double *d_rho, double *d_mu_ex, void *stream);
 
@@ -396,6 +401,14 @@ int pnp_weight_spectrum(int kind, double r_in, double r_out, int nmu, int ntheta
  * gave up and reported it (the expected result), PNP_ERR_INVALID for a bad
  * limit, PNP_ERR_CUDA on a runtime error.  The device stays usable. */
 int pnp_selftest_bounded_wait(double limit_ms);
+
+/* Failure-path test hook with no counterpart in the paper.  Arms a host-side
+ * fault: counting from this call, the k-th device allocation the library
+ * makes (1-based) reports PNP_ERR_NOMEM without calling CUDA; k <= 0 disarms.
+ * Lets a test drive every allocation site's error path without exhausting or
+ * faulting a GPU.  Nothing else arms it (no environment variable is read).
+ * Process-wide; not for production callers.  Returns PNP_OK. */
+int pnp_test_fail_alloc_at(long k);
 
 /* Static message for an error code. */
 const char *pnp_error_string(int code);

@@ -22,18 +22,18 @@ int cuda_status(cudaError_t e) {
     return PNP_ERR_CUDA;
 }
 
-// Test hook: with PNP_FAULT_ALLOC_AT=k in the environment the k-th device
-// allocation of the process (1-based) reports cudaErrorMemoryAllocation on the
-// host without calling CUDA, so the error paths of every allocation site can
-// be driven without exhausting or faulting a GPU.  Inert when unset.
+// Test hook, armed only through the test entry point pnp_test_fail_alloc_at:
+// the k-th device allocation after arming (1-based) reports
+// cudaErrorMemoryAllocation on the host without calling CUDA, so the error
+// paths of every allocation site can be driven without exhausting or faulting
+// a GPU.  Inert unless a caller arms it explicitly.
+static std::atomic<long> g_fail_alloc_at{0};
+static std::atomic<long> g_alloc_count{0};
+
 static bool injected_alloc_failure() {
-    static const long fail_at = [] {
-        const char *v = std::getenv("PNP_FAULT_ALLOC_AT");
-        return v ? std::atol(v) : 0L;
-    }();
-    static std::atomic<long> count{0};
-    if (fail_at <= 0) return false;
-    return count.fetch_add(1) + 1 == fail_at;
+    const long at = g_fail_alloc_at.load();
+    if (at <= 0) return false;
+    return g_alloc_count.fetch_add(1) + 1 == at;
 }
 
 cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t st) {
@@ -490,6 +490,12 @@ int pnp_square_well_energy(pnp_problem *h, const double *rho, double *F_sh) {
 }
 
 int pnp_selftest_bounded_wait(double limit_ms) { return bounded_wait_probe(limit_ms); }
+
+int pnp_test_fail_alloc_at(long k) {
+    pnp::g_alloc_count.store(0);
+    pnp::g_fail_alloc_at.store(k > 0 ? k : 0);
+    return PNP_OK;
+}
 
 const char *pnp_error_string(int code) {
     switch (code) {

@@ -404,17 +404,26 @@ void mu_ex_free(Problem *p) {
 // with cudaGetSymbolAddress on the first call made while that device is
 // current; make that first call before any stream capture.  Every call shares
 // the array and it keeps the previous call's contents: the status word is
-// cleared by each call, everything else is fully overwritten before it is
-// read.  Calls whose work overlaps on the GPU (other streams, other host
-// threads) race on the array; serialise them.
+// cleared by each call; the twiddles and spectra are uploaded again whenever
+// the padded lengths, species radii, quadrature counts or stencil reach differ
+// from the last successful call on that device (a per-device key, dropped on
+// any error); the workspace is fully overwritten before it is read.  Calls on
+// one device are serialised by a per-device lock for their whole duration, and
+// each returns only after its work is done, on success and on error alike.
+// Calls whose work overlaps on the GPU (from code that shares the array by
+// other routes) race on it.
 namespace pnp {
 
 constexpr size_t kNoAllocBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-std::mutex g_noalloc_mutex;
-void *g_noalloc_addr[64] = {nullptr};
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mutex[kNoAllocDevices];
+void *g_noalloc_addr[kNoAllocDevices] = {nullptr};
+// what the array's twiddles and spectra were built for, per device (empty:
+// nothing valid)
+std::vector<double> g_noalloc_key[kNoAllocDevices];
 
 size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -429,8 +438,16 @@ size_t noalloc_bytes(const Problem &p) {
     return b;
 }
 
-void twiddles_host(int L, std::vector<double> &h) {
-    h.assign(2 * (size_t)L, 0.0);
+// everything the twiddle tables, the spectra and their places in the array
+// depend on
+std::vector<double> noalloc_key(const Problem &p) {
+    std::vector<double> k = {(double)p.L[0], (double)p.L[1], (double)p.L[2], (double)p.s, (double)p.S,
+                             (double)p.quad[0], (double)p.quad[1], (double)p.quad[2]};
+    for (int i = 0; i < p.s; ++i) k.push_back(p.R[i]);
+    return k;
+}
+
+void twiddles_host(int L, double *h) {
     for (int m = 0; m < L; ++m) {
         if ((4 * (long)m) % L == 0) {
             const double cs[4][2] = {{1, 0}, {0, -1}, {-1, 0}, {0, 1}};
@@ -461,8 +478,8 @@ extern "C" int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 0 || dev >= 64) return PNP_ERR_INVALID;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (dev < 0 || dev >= kNoAllocDevices) return PNP_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex[dev]);
     if (!g_noalloc_addr[dev]) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
@@ -471,49 +488,64 @@ extern "C" int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double 
     }
     unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
     cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> &key = g_noalloc_key[dev];
+    // after the first enqueue every exit waits for the stream (the lock is
+    // still held, so no later call can write the array under work in flight)
+    // and drops the key, since the array's contents are then unknown
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        key.clear();
+        return code;
+    };
+    const std::vector<double> want = noalloc_key(p);
+    const bool fresh = key != want;
+    key.clear();
     // carve: status word | twiddles x, y, z | spectra | workspace
     size_t off = 256;
     DeviceBuffers db;
     db.prec = PNP_PREC_FP64;
-    std::vector<double> h;
-    for (int c = 0; c < 3; ++c) {
-        db.tw[c] = base + off;
-        twiddles_host(p.L[c], h);
-        e = cudaMemcpyAsync(db.tw[c], h.data(), 16 * (size_t)p.L[c], cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_status(e);
-        off += round256(16 * (size_t)p.L[c]);
-    }
     const Dims d = make_dims(&p);
     const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
-    db.spec = base + off;
-    const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
-    const bool odd[kNumKernels][3] = {{false, false, false}, {false, false, false}, {true, false, false},
-                                      {false, true, false}, {false, false, true}};
-    h.assign(oct, 0.0);
-    for (int i = 0; i < p.s; ++i) {
-        Stencil stn[kNumKernels];
-        build_fmt_stencils(p.R[i], p.quad[0], p.quad[1], p.quad[2], p.S, stn);
-        for (int k = 0; k < kNumKernels; ++k) {
-            octant_transform(stn[k], p.L, odd[k], scale, h.data());
-            // synchronous copy: the host table is reused for the next kernel
-            e = cudaMemcpy((double *)db.spec + (size_t)(i * kNumKernels + k) * oct, h.data(), sizeof(double) * oct,
-                           cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) return cuda_status(e);
-        }
+    size_t tw_off[3];
+    for (int c = 0; c < 3; ++c) {
+        tw_off[c] = off;
+        db.tw[c] = base + off;
+        off += round256(16 * (size_t)p.L[c]);
     }
+    db.spec = base + off;
     off += round256(sizeof(double) * oct * kNumKernels * p.s);
+    if (fresh) {
+        // one host image of the twiddles and spectra, one copy
+        std::vector<double> h((off - 256) / sizeof(double), 0.0);
+        for (int c = 0; c < 3; ++c) twiddles_host(p.L[c], h.data() + (tw_off[c] - 256) / sizeof(double));
+        double *hs = h.data() + ((unsigned char *)db.spec - base - 256) / sizeof(double);
+        const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
+        const bool odd[kNumKernels][3] = {{false, false, false}, {false, false, false}, {true, false, false},
+                                          {false, true, false}, {false, false, true}};
+        for (int i = 0; i < p.s; ++i) {
+            Stencil stn[kNumKernels];
+            build_fmt_stencils(p.R[i], p.quad[0], p.quad[1], p.quad[2], p.S, stn);
+            for (int k = 0; k < kNumKernels; ++k)
+                octant_transform(stn[k], p.L, odd[k], scale, hs + (size_t)(i * kNumKernels + k) * oct);
+        }
+        // from pageable memory the copy has read `h` when the call returns
+        e = cudaMemcpyAsync(base + 256, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(cuda_status(e));
+    }
     p.d_work = base + off;
     p.d_flag = (int *)base;
     e = cudaMemsetAsync(p.d_flag, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail(cuda_status(e));
     rc = run_pipeline_fp64(&p, &db, d_rho, d_mu_ex, st);
-    if (rc) return rc;
+    if (rc) return fail(rc);
     int flag = 0;
     e = cudaMemcpyAsync(&flag, p.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return fail(cuda_status(e));
     p.d_work = nullptr;
     p.d_flag = nullptr;
+    key = want;
     return (flag & (kFlagPacking | kFlagNonFinite)) ? PNP_ERR_PACKING : PNP_OK;
 }
 

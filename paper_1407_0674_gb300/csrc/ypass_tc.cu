@@ -1,5 +1,5 @@
 // Split-precision DFT stage on the 5th-generation tensor cores: the y pass of
-// the FP32 pipeline (Sec 3.2: one axis of the zero-padded 3D transforms) with
+// the FP32 pipeline (Sec 3.4: one axis of the zero-padded 3D transforms) with
 // its two radix-16 DFT stages written as dense matrix products.
 //
 // A length-256 line is x[n1 + 16 n2].  Stage A forms, for every (column c, n1),

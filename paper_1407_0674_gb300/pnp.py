@@ -129,6 +129,7 @@ def lib():
         L.pnp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
+        L.pnp_test_fail_alloc_at.argtypes = [ctypes.c_long]
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_conductivity.argtypes = [ctypes.POINTER(Desc), _dp, ctypes.c_double, _dp]

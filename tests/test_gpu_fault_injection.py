@@ -1,5 +1,5 @@
-"""Allocation failures injected on the host (PNP_FAULT_ALLOC_AT=k makes the
-k-th device allocation of the process report out-of-memory without calling
+"""Allocation failures injected on the host (pnp_test_fail_alloc_at(k) makes
+the k-th device allocation after it report out-of-memory without calling
 CUDA): for every k the failing call returns PNP_ERR_NOMEM, leaves nothing
 half-built behind, the same call then succeeds, and the results are bit for
 bit those of a run without the fault.  Covers problem creation (workspace,
@@ -26,6 +26,7 @@ import numpy as np
 from paper_1407_0674_gb300 import pnp
 from workloads import film_gummel, lognormal_density
 
+pnp.lib().pnp_test_fail_alloc_at(int(sys.argv[3]))
 spec = film_gummel(8, 8, 8, max_iter=3, tol=1e-30)
 spec.lin_tol = 1e-13
 rho = lognormal_density(spec, 3, sigma=0.2)
@@ -62,12 +63,8 @@ def built():
 
 
 def run_child(k, out, tmp_path):
-    env = dict(os.environ)
-    env.pop("PNP_FAULT_ALLOC_AT", None)
-    if k:
-        env["PNP_FAULT_ALLOC_AT"] = str(k)
-    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(out)], capture_output=True, text=True, timeout=120,
-                       env=env, cwd=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT, str(out), str(k)], capture_output=True, text=True,
+                       timeout=120, cwd=ROOT)
     assert r.returncode == 0, (k, r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 

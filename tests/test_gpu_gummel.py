@@ -78,6 +78,17 @@ def test_dense_film_trajectory_matches_oracle(pnp):
     compare(spec, pnp)
 
 
+def test_full_size_film_trajectory_matches_oracle(pnp):
+    """The 32^3 film workload itself (2 ions, R 2h, packing 0.2 each, 1 kT
+    wells on 64 sites, fixed charge, bias 0.1 kT/e, geometric relaxation
+    0.05): its first three Gummel iterates against the oracle's, iterate by
+    iterate (the oracle takes about half a minute)."""
+    spec = film_gummel(32, 32, 32, tol=1e-30, max_iter=3)
+    spec.lin_tol = 1e-13
+    phi, rho, st, ref = compare(spec, pnp)
+    assert st["iterations"] == 3 and st["status"] == pnp.ERR_NOT_CONVERGED
+
+
 def test_deep_wells_step_limited_trajectory(pnp):
     """Batch-workload physics at 12^3: wells 12 kT deep, packing 0.3, step-
     limited geometric relaxation; six iterations match the oracle (the step

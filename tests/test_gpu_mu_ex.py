@@ -20,6 +20,10 @@ pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-10
 FP32_TOL = 2e-5
 TF32SPLIT_TOL = 5e-5
+# whole-field error against the FP64 path on the 128^3 -> 256^3 workload:
+# 3x the observed 8.5e-7 (FP32) and 4.1e-6 (3xTF32)
+FP32_FIELD_BOUND = 2.5e-6
+TF32SPLIT_FIELD_BOUND = 1.2e-5
 
 
 @pytest.fixture(scope="module")
@@ -266,8 +270,11 @@ def test_full_size_sampled(pnp):
         assert np.abs(mu32[i, flat] - ref[i]).max() / scale <= FP32_TOL
         assert np.abs(mudd[i, flat] - ref[i]).max() / scale <= FP64_TOL
         assert np.abs(mutc[i, flat] - ref[i]).max() / scale <= TF32SPLIT_TOL
-    # whole field of the tensor-core variant against the FP64 path
-    assert normwise(mutc, mu) <= TF32SPLIT_TOL
+    # whole fields of the reduced-precision variants against the FP64 path,
+    # at 3x the error observed at this size (FP32 8.5e-7, 3xTF32 4.1e-6);
+    # the looser oracle bars above cover every other shape
+    assert normwise(mu32, mu) <= FP32_FIELD_BOUND
+    assert normwise(mutc, mu) <= TF32SPLIT_FIELD_BOUND
     # whole-field agreement of the two FP64-accuracy paths
     assert np.abs(mudd - mu).max() / np.abs(mu).max() <= FP64_TOL
 

@@ -83,6 +83,35 @@ def test_results_same_alone_and_in_the_mix(pnp):
     srv.close()
 
 
+def test_served_solves_match_oracle(pnp):
+    """Two solves of the eight-solve mix (different grids and temperatures),
+    served concurrently with the other six, against the oracle's converged
+    states at 1e-8, and bitwise against the same solves run alone."""
+    from oracle import oracle
+    specs = mix()
+    for s in specs:
+        s.lin_tol = 1e-13
+    srv = pnp.Server(max_slots=8)
+    tickets = []
+    for s in specs:
+        rc, t = srv.submit(s)
+        assert rc == 0
+        tickets.append(t)
+    res = drain(srv, tickets)
+    srv.close()
+    for k in (0, 2):
+        rc, phi, rho, st = res[tickets[k]]
+        assert rc == 0 and st["status"] == 0
+        ref = oracle.gummel(specs[k])
+        assert ref["status"] == 0 and st["iterations"] == ref["iters"]
+        assert np.abs(phi - ref["phi"]).max() / max(np.abs(ref["phi"]).max(), 1.0) <= 1e-8
+        for i in range(specs[k].s):
+            assert np.abs(rho[i] - ref["rho"][i]).max() / np.abs(ref["rho"][i]).max() <= 1e-8
+        phi1, rho1, _ = alone(pnp, specs[k])
+        np.testing.assert_array_equal(phi, phi1)
+        np.testing.assert_array_equal(rho, rho1)
+
+
 def test_budget_admission_and_busy(pnp):
     specs = mix()[:4]
     # a budget that holds about one of these problems at a time
