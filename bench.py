@@ -6,12 +6,17 @@ lognormal(0, 0.1), seed 2), zero-padded to 256^3, through the C ABI
 (pnp_excess_mu_device) with inputs resident in device memory.
 
 Prints one JSON line (rank 0).  Metric: mu_ex Gpoints/s = output grid points /
-time, against the HBM roofline.  The headline is the FP32-FFT path with the
-singular terms of the FMT derivatives in FP64 (error against the FP64 path
-stated in the line, below 1e-6 on this workload); the plain FP64 form, the double-float FFT (FP64 accuracy) and
-the 3xTF32 tensor-core variant are reported beside it, each with its error.
+time.  The headline is the FP64-accuracy path: FFT arithmetic in double-float
+(pairs of FP32, ~48 bits; within 1e-10 of the FP64 oracle like plain FP64),
+FMT derivatives in FP64; its dominant kernel is bound by the FP32 pipes and is
+reported against their peak.  Beside it: the FP32-FFT variant (singular terms
+of the derivatives in FP64) and the 3xTF32 tensor-core variant against the HBM
+roofline, and the plain FP64 form, each with its error against the FP64 path.
 `e2e` times pnp_excess_mu with host buffers (pinned), host->device and
-device->host copies inside the timed region.
+device->host copies inside the timed region.  `solves` (after the timed
+region) serves `--solves` independent Gummel solves of the batch recipe
+concurrently and runs the same solves one at a time in plain FP64: solves/s,
+speed-up, p50/p99 latency and the largest density difference.
 
 `--impl reference` times the FP64 CPU oracle (direct real-space quadrature
 sums) on a bounded sample of the same workload; it is the reference arm.
@@ -58,7 +63,10 @@ def parse():
     ap.add_argument("--solve-prec", default="df64", choices=["fp64", "df64", "fp32", "tf32split"],
                     help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune the batched / served problems' plans")
-    ap.add_argument("--variants", default="fp32,fp64,df64,tf32split", help="precisions to time, headline first")
+    ap.add_argument("--variants", default="df64,fp32,tf32split,fp64", help="precisions to time, headline first")
+    ap.add_argument("--solves", type=int, default=16,
+                    help="mu_ex workload: solves of the batch recipe served concurrently, against the same solves "
+                         "one at a time in plain FP64, reported beside the mu_ex line (0: none)")
     ap.add_argument("--workload", default="mu_ex", choices=["mu_ex", "film", "film3", "batch", "serve"],
                     help="mu_ex (headline), film (one 32^3 Gummel solve), film3 (128x128x256 bias sweep), "
                          "batch (64 solves), serve (arrivals)")
@@ -253,6 +261,19 @@ def stage_flops(name, dims, s):
 PROFILED_TRAFFIC = {
     ("fp64", "z_back"): 1.1299e9,     # k_zback_p_fp64_120_pad256.md
     ("fp32", "z_back"): 5.559e8,      # k_zback_p_fp32_120_pad256.md
+    # k_z_dd_120_pad256.md: 1057.1 / 1068.4 MB at 120^3, x (algorithmic bytes
+    # at 128^3 / at 120^3) = 1137 / 1082 MB
+    ("df64", "z_mac"): 1.1108e9,
+    ("df64", "z_back"): 1.1227e9,
+}
+# FP32-pipe instructions (thread-level FADD + FMUL + FFMA) one launch of a
+# double-float kernel executes, from ncu's per-opcode counts (profiles/): the
+# work its number format costs the FP32 pipes.  A z kernel transforms every
+# one of the Ly x Wx columns over the full length Lz whatever nz is, so the
+# 120^3 capture holds for 128^3 as it is.  None for a kernel changed since.
+PROFILED_FP32_INST = {
+    ("df64", "z_mac"): 4.1144e10,      # k_z_dd_120_pad256.md
+    ("df64", "z_back"): 4.1144e10,
 }
 
 DTYPE = {"fp64": "f64",
@@ -268,6 +289,7 @@ ERROR_BOUND = {"fp64": 1e-10, "df64": 1e-10, "fp32": 2e-5, "tf32split": 5e-5}
 # per clock x 2 flops x 2.07 GHz (an FMA-chain probe measured 1.195 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 
 
 def run_reference(args, world, rank):
@@ -421,11 +443,19 @@ def run_gpu(args, world, rank, local):
         hbm = {"achieved_gbs": b / (avg * 1e-3) / 1e9, "bytes_per_launch": b}
         hbm["frac"] = hbm["achieved_gbs"] / peak
         if prec == "df64":
-            ach = f / (avg * 1e-3) / 1e12
-            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s (FP64-equivalent flops on the FP32 pipes)", "frac": ach / FP32_PEAK_TFLOPS,
-                    "traffic": None, "flops_per_launch": f, "avg_launch_ms": avg, "share_of_step": share,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "hbm": hbm}
+            # FP32-pipe instructions the double-float kernel executes (ncu
+            # count) per second against the pipes' issue rate; without a count
+            # for the current kernel no fraction is claimed
+            ni = PROFILED_FP32_INST.get((prec, name))
+            ach = ni / (avg * 1e-3) / 1e12 if ni else None
+            return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TINST,
+                    "unit": "T FP32-pipe instructions/s (FADD+FMUL+FFMA of the double-float arithmetic)",
+                    "frac": ach / FP32_PEAK_TINST if ach else None,
+                    "traffic": PROFILED_TRAFFIC.get((prec, name)), "fp32_inst_per_launch": ni,
+                    "fp64_equivalent_flops_per_launch": f, "fp64_equivalent_tflops": f / (avg * 1e-3) / 1e12,
+                    "avg_launch_ms": avg, "share_of_step": share,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz, one instruction per lane "
+                                   "per clock", "hbm": hbm}
         if prec == "fp64":
             ach = f / (avg * 1e-3) / 1e12
             return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -493,8 +523,14 @@ def run_gpu(args, world, rank, local):
             "stages_ms": {p: {k: v[0] / max(v[1], 1) for k, v in results[p]["stages"].items()}
                           for p in results},
         }
-        print(json.dumps(line), flush=True)
     P.close()
+    torch.cuda.synchronize()
+    if rank == 0 and args.solves > 0:
+        from workloads import batch_specs
+        line["solves"] = batch_record(batch_specs(args.solves), args.solve_prec, args.autotune, args.solves)
+    barrier(world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def cpu_model():
@@ -550,6 +586,70 @@ def oracle_sweep_seconds(spec, sweeps):
     t0 = time.perf_counter()
     oracle.gummel(s)
     return (time.perf_counter() - t0) / sweeps, oracle.num_threads()
+
+
+def batch_record(specs, solve_prec, autotune, seq_count, log=sys.stderr):
+    """Independent Gummel solves of the batch recipe served concurrently
+    (mu_ex in `solve_prec`, FP64 Gummel update and linear solves) against the
+    first `seq_count` of the same solves one at a time in plain FP64.
+    Latency of a served solve = submission (all at t = 0) to poll-ready."""
+    import numpy as np
+    from paper_1407_0674_gb300 import pnp
+    served = [dataclasses.replace(s, autotune=autotune) for s in specs]
+    seq = []
+    seq_res = {}
+    for k, s in enumerate(specs[:seq_count]):
+        with pnp.Problem(s) as P:
+            t0 = time.perf_counter()
+            phi, rho, st = P.gummel_solve(raise_on_error=False)
+            seq.append(time.perf_counter() - t0)
+            seq_res[k] = (rho, st)
+        print(f"sequential fp64 {k} ({s.nx}x{s.ny}x{s.nz}): status {st['status']} it {st['iterations']} "
+              f"{seq[-1]:.1f} s", file=log, flush=True)
+    srv = pnp.Server(max_slots=64)
+    t0 = time.perf_counter()
+    tickets = []
+    for s in served:
+        rc, t = srv.submit(s, precision=solve_prec)
+        if rc != 0:
+            raise RuntimeError(f"submit {rc}")
+        tickets.append(t)
+    done = {}
+    while len(done) < len(tickets):
+        for k, t in enumerate(tickets):
+            if k in done:
+                continue
+            rc, phi, rho, st = srv.poll(t)
+            if rc != pnp.PENDING:
+                done[k] = (rc, rho, st, time.perf_counter() - t0)
+                print(f"served {k}: status {rc} it {st['iterations']} at {done[k][3]:.1f} s", file=log, flush=True)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    srv.close()
+    # solves that converged in both runs
+    both = [k for k in seq_res if seq_res[k][1]["status"] == 0 and done[k][0] == 0]
+    errs = [max(float(np.abs(done[k][1][i] - seq_res[k][0][i]).max() / np.abs(seq_res[k][0][i]).max())
+                for i in range(specs[k].s)) for k in both]
+    lat = [v[3] for v in done.values()]
+    grids = sorted({(s.nx, s.ny, s.nz) for s in specs})
+    return {
+        "workload": f"{len(specs)} independent Gummel solves of the batch recipe (seed 4): grids "
+                    + ", ".join(f"{a}x{b}x{c}" for a, b, c in grids)
+                    + ", T U(250,400) K, wells 0.3 eV/kT, packing U(0.1,0.35), residual 1e-8; served "
+                      "concurrently (one CUDA graph per solve) vs one at a time in plain FP64",
+        "mu_ex_precision": solve_prec,
+        "served": {"solves": len(specs), "solves_per_s": len(specs) / wall, "wall_s": wall,
+                   "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+                   "converged": sum(1 for v in done.values() if v[0] == 0),
+                   "status": [done[k][0] for k in range(len(specs))],
+                   "iterations": [done[k][2]["iterations"] for k in range(len(specs))]},
+        "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq) if seq else None,
+                            "wall_s": sum(seq), "converged": sum(1 for k in seq_res if seq_res[k][1]["status"] == 0),
+                            "iterations": [seq_res[k][1]["iterations"] for k in seq_res]},
+        "speedup_vs_sequential_fp64": (len(specs) / wall) / (len(seq) / sum(seq)) if seq else None,
+        "max_rel_err_rho_vs_fp64": max(errs) if errs else None, "compared_solves": len(both),
+        "error_bar": 1e-6,
+    }
 
 
 def run_solves(args, world, rank, local):
@@ -638,59 +738,14 @@ def run_solves(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
     if args.workload == "batch":
-        specs = batch_specs(args.batch)
-        served = [dataclasses.replace(s, autotune=args.autotune) for s in specs]
-        # sequential baseline: the plain FP64 form, one solve at a time
-        seq = []
-        seq_res = {}
-        for k, s in enumerate(specs[:args.seq]):
-            with pnp.Problem(s) as P:
-                t0 = time.perf_counter()
-                phi, rho, st = P.gummel_solve(raise_on_error=False)
-                seq.append(time.perf_counter() - t0)
-                seq_res[k] = (rho, st)
-        srv = pnp.Server(max_slots=64)
-        t0 = time.perf_counter()
-        tickets = []
-        for s in served:
-            rc, t = srv.submit(s, precision=args.solve_prec)
-            if rc != 0:
-                raise RuntimeError(f"submit {rc}")
-            tickets.append(t)
-        done = {}
-        while len(done) < len(tickets):
-            for k, t in enumerate(tickets):
-                if k in done:
-                    continue
-                rc, phi, rho, st = srv.poll(t)
-                if rc != pnp.PENDING:
-                    done[k] = (rc, rho, st, time.perf_counter() - t0)
-                    print(f"batch {k}: status {rc} it {st['iterations']} at {done[k][3]:.1f} s", file=sys.stderr,
-                          flush=True)
-            time.sleep(0.002)
-        wall = time.perf_counter() - t0
-        srv.close()
-        # solves that converged in both runs
-        both = [k for k in seq_res if seq_res[k][1]["status"] == 0 and done[k][0] == 0]
-        errs = [float(np.abs(done[k][1] - seq_res[k][0]).max() / np.abs(seq_res[k][0]).max()) for k in both]
-        seq_ok = sum(1 for k in seq_res if seq_res[k][1]["status"] == 0)
-        ok = sum(1 for v in done.values() if v[0] in (0,))
-        lat = [v[3] for v in done.values()]
-        line = {"metric": "PNP solves/s", "value": world * len(specs) / wall, "unit": "solves/s", "n_gpus": world,
-                "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
-                "config": {"workload": f"{len(specs)} independent Gummel solves, grids from "
-                                       "{32^3,48^3,64^3,80x80x96,96^3}, T U(250,400) K, wells 0.3 eV/kT, packing "
-                                       "U(0.1,0.35), served concurrently (one CUDA graph per solve)",
-                           "mu_ex_precision": args.solve_prec, "autotune": bool(args.autotune)},
-                "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq),
-                                    "mean_s": float(np.mean(seq)), "converged": seq_ok,
-                                    "iterations": [seq_res[k][1]["iterations"] for k in seq_res]},
-                "speedup_vs_sequential": (len(specs) / wall) / (len(seq) / sum(seq)),
-                "max_rel_err_vs_sequential": max(errs) if errs else None,
-                "converged": ok, "status": [done[k][0] for k in range(len(specs))],
-                "compared_solves": len(both), "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
-                "iterations_mean": float(np.mean([v[2]["iterations"] for v in done.values()]))}
+        rec = batch_record(batch_specs(args.batch), args.solve_prec, args.autotune, args.seq)
+        line = {"metric": "PNP solves/s", "value": world * rec["served"]["solves_per_s"], "unit": "solves/s",
+                "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": rec["served"]["wall_s"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[args.solve_prec] + " / f64 Gummel", "data": "synthetic",
+                "config": {"workload": rec["workload"], "mu_ex_precision": args.solve_prec,
+                           "autotune": bool(args.autotune)}}
+        line.update({k: v for k, v in rec.items() if k != "workload"})
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -105,6 +105,22 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * as lambda_phi lambda_rho kappa^2 / k^2), the screened one is not. */
 #define PNP_FLAG_SCREENED_POISSON 4u
 
+/* PNP_FLAG_MSA: mu_ex also carries the electrostatic correlations of the mean
+ * spherical approximation (Sec 2.3.4):
+ *   mu_el,i(r) = - sum_j int_Omega C_ij(|r - r'|) (rho_j(r') - rho_b,j) dr',
+ *   C_ij(r) = -q_i q_j l_B [2B/s - (B/s)^2 r - 1/r] for r <= s, 0 beyond,
+ *   s = R_i + R_j, B = [xi + 1 - sqrt(1 + 2 xi)] / xi, xi = kappa s,
+ *   kappa^2 = 4 pi l_B sum_k rho_b,k q_k^2,
+ * with the printed prefactor e^2/(k_B T eps) read as l_B.  The integral is
+ * the ball quadrature of radius s (the FMT counts) deposited trilinearly on
+ * the grid like the FMT weights, rho_j - rho_b,j zero off the domain.  The
+ * bulk constant mu_el^bulk is not printed and is left out (a constant shift of
+ * mu_i and of its reservoir value cancels in the Slotboom form).  Padded
+ * lengths then also cover the MSA reach, ceil(2 max R) + 1.  Applied by every
+ * mu_ex call and every Gummel iteration of the problem; not available through
+ * pnp_excess_mu_noalloc (PNP_ERR_INVALID). */
+#define PNP_FLAG_MSA 8u
+
 /* hard-sphere functional (Sec 2.3.1): Rosenfeld's, whose derivatives the
  * paper prints, or the White Bear (modified FMT) form it names beside it, in
  * which the n2^3 term carries phi3(n3) / (36 pi),
@@ -157,6 +173,9 @@ typedef struct {
                                       (0 -> 1e-6) */
     int eq_max_iter;               /* and its iteration cap (0 -> 1000) */
     int fmt;                       /* hard-sphere functional, PNP_FMT_* */
+    int anderson_depth;            /* 0: the relaxed Gummel iteration as printed (Sec 3.2); 1..6: that
+                                      iteration accelerated by Anderson mixing of this depth (see
+                                      pnp_gummel_solve); not with PNP_MIX_ADAPTIVE */
 } pnp_problem_desc;
 
 typedef struct {

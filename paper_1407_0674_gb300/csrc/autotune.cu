@@ -31,13 +31,13 @@ struct Tuned {
     int tile[3];
     double ms;
 };
-using Key = std::array<int, 13>;
+using Key = std::array<int, 14>;
 
 std::mutex g_mu;
 std::map<Key, Tuned> g_cache;
 
 Key key_of(const Problem *p, const pnp_problem_desc *d) {
-    return Key{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->bc[2], p->s, p->S, p->Ssw, p->precision,
+    return Key{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->bc[2], p->s, p->S, p->Ssw, p->Smsa, p->precision,
                d->fft_len[0], d->fft_len[1], d->fft_len[2]};
 }
 

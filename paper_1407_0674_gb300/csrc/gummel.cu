@@ -62,6 +62,20 @@ struct DevStats {
     double eq_residual;    // its last residual
 };
 
+// control block of the Anderson mixing (see the kernels further down)
+constexpr int kAaMaxDepth = 6;
+constexpr int kAaMaxK = kAaMaxDepth * (kAaMaxDepth + 1) / 2 + kAaMaxDepth;   // Gram entries + right-hand side
+struct AaCtl {
+    int m;             // depth
+    int head, hlen;    // ring of m + 1 entries: logical a -> physical (head + a) % (m + 1)
+    int slot;          // physical entry of this iteration
+    int redo;          // 1: this sweep is repeated from the restored plain iterate
+    int skip;          // 1: no extrapolation this iteration (converged or failed)
+    int rslot;         // entry whose X + F is restored on a redo
+    int kd;            // differences in the history this iteration
+    double gamma[kAaMaxDepth];
+};
+
 struct GummelState {
     std::vector<Level> lv;
     double *mu = nullptr, *rho_new = nullptr;
@@ -76,6 +90,11 @@ struct GummelState {
     double *partial = nullptr;     // kRedBlocks
     double *lam = nullptr, *prev = nullptr;   // PNP_MIX_ADAPTIVE: per-point factor and last step
     double *scal = nullptr;        // device scalars
+    // Anderson mixing (depth m > 0): history of m + 1 iterates x = (phi, ln rho)
+    // and residuals f = G(x) - x, [m+1][(1+s) N] each, a control block and the
+    // Gram reduction's block partials
+    double *aa_X = nullptr, *aa_F = nullptr, *aa_part = nullptr;
+    struct AaCtl *aa = nullptr;
     unsigned long long *dmax = nullptr;
     size_t bytes = 0;
     bool poisson_ready = false;
@@ -738,9 +757,14 @@ __global__ void k_pcg_check(const double *scal, int maxit, DevStats *st, int *fl
 
 // end of a Gummel iteration: residual, status, continue or stop
 __global__ void k_gummel_check(const unsigned long long *dmax, const int *flag, double tol, int max_iter,
-                               DevStats *st, cudaGraphConditionalHandle h) {
+                               DevStats *st, cudaGraphConditionalHandle h, const AaCtl *aa) {
     const unsigned long long bits = *dmax;
     const double res = __longlong_as_double((long long)bits);
+    if (aa && aa->redo) {
+        // the sweep is repeated from the restored plain iterate: same iteration
+        cudaGraphSetConditional(h, 1u);
+        return;
+    }
     const int it = ++st->iters;
     st->residual = res;
     const int f = *flag;
@@ -793,6 +817,227 @@ __global__ void k_stats_reset(DevStats *st, int eq_enable) {
     st->eq_enable = eq_enable;
     st->eq_iters = 0;
     st->eq_residual = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Anderson mixing of the relaxed Gummel iteration (an extension; the paper
+// relaxes only).  G is one sweep of the loop body acting on x = (phi, ln rho);
+// with the last k <= m differences dX_a, dF_a of iterates and residuals
+// f = G(x) - x,
+//   gamma = argmin || f - dF gamma ||_2   (normal equations, ridge 1e-12 tr),
+//   x <- x + f - sum_a gamma_a (dX_a + dF_a).
+// If the sweep from an extrapolated state is unphysical (packing, overflow,
+// non-finite) the history is dropped and the sweep repeated from the last
+// plain iterate G(x_prev) = X + F of the newest entry, in the same iteration.
+// The stopping test is on the plain sweep's residual, so the fixed point is
+// the relaxed iteration's.
+__global__ void k_aa_reset(AaCtl *a, int m) {
+    a->m = m;
+    a->head = a->hlen = a->slot = a->redo = a->skip = a->rslot = a->kd = 0;
+}
+
+// start of an iteration: make room for the entry of the current state
+__global__ void k_aa_begin(AaCtl *a) {
+    const int R = a->m + 1;
+    if (a->hlen == R) {
+        a->head = (a->head + 1) % R;
+        a->hlen = a->m;
+    }
+    a->slot = (a->head + a->hlen) % R;
+    a->redo = 0;
+    a->skip = 0;
+}
+
+__device__ __forceinline__ double aa_state(const double *phi, const double *rho, size_t N, size_t e) {
+    return e < N ? phi[e] : log(rho[e - N]);
+}
+
+// X[slot] = x = (phi, ln rho) before the sweep
+__global__ void k_aa_save_x(const AaCtl *__restrict__ a, const double *__restrict__ phi,
+                            const double *__restrict__ rho, double *__restrict__ X, size_t N, size_t M) {
+    double *x = X + (size_t)a->slot * M;
+    GRID_LOOP(e, M) x[e] = aa_state(phi, rho, N, e);
+}
+
+// after the sweep: a failed sweep from an extrapolated state (history and
+// not the first iteration) is repeated from the last plain iterate; a
+// converged or failed one is not extrapolated
+__global__ void k_aa_post(AaCtl *a, const unsigned long long *dmax, int *flag, double tol, const DevStats *st) {
+    const double rr = __longlong_as_double((long long)*dmax);
+    const int bad = *flag & (kFlagPacking | kFlagOverflow | kFlagNonFinite);
+    if (bad && a->hlen > 0 && st->iters > 0) {
+        a->redo = 1;
+        a->skip = 1;
+        a->rslot = (a->head + a->hlen - 1) % (a->m + 1);
+        a->hlen = 0;
+        atomicAnd(flag, ~(kFlagPacking | kFlagOverflow | kFlagNonFinite));
+    } else if (bad || rr < tol) {
+        a->skip = 1;
+    }
+}
+
+// redo: (phi, rho) = the plain iterate X + F of the newest history entry
+__global__ void k_aa_restore(const AaCtl *__restrict__ a, const double *__restrict__ X,
+                             const double *__restrict__ F, double *__restrict__ phi, double *__restrict__ rho,
+                             size_t N, size_t M) {
+    if (!a->redo) return;
+    const double *x = X + (size_t)a->rslot * M, *f = F + (size_t)a->rslot * M;
+    GRID_LOOP(e, M) {
+        const double v = x[e] + f[e];
+        if (e < N) phi[e] = v;
+        else rho[e - N] = exp(v);
+    }
+}
+
+// F[slot] = G(x) - x, and block partials of the Gram entries
+// dF_a . dF_b (b <= a < kd) and dF_a . f, dF_a = F[a+1] - F[a] in logical
+// order, f = F[slot] (the newest entry)
+template <int KD>
+__device__ void aa_gram_body(const AaCtl &a, const double *__restrict__ phi, const double *__restrict__ rho,
+                             const double *__restrict__ X, double *__restrict__ F, size_t N, size_t M,
+                             double *__restrict__ part) {
+    constexpr int K = KD * (KD + 1) / 2 + KD;
+    double acc[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    const int R = a.m + 1;
+    const double *x = X + (size_t)a.slot * M;
+    double *fs = F + (size_t)a.slot * M;
+    GRID_LOOP(e, M) {
+        const double f = aa_state(phi, rho, N, e) - x[e];
+        fs[e] = f;
+        if constexpr (KD > 0) {
+            double Fv[KD + 1];
+#pragma unroll
+            for (int j = 0; j < KD; ++j) Fv[j] = F[(size_t)((a.head + j) % R) * M + e];
+            Fv[KD] = f;
+            double dF[KD];
+#pragma unroll
+            for (int j = 0; j < KD; ++j) dF[j] = Fv[j + 1] - Fv[j];
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < KD; ++i) {
+#pragma unroll
+                for (int j = 0; j <= i; ++j) acc[k++] += dF[i] * dF[j];
+                acc[k++] += dF[i] * f;
+            }
+        }
+    }
+    if constexpr (K > 0) {
+        __shared__ double sh[K][8];
+        const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (l == 0) sh[k][w] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < K) {
+            double v = 0.0;
+            for (int j = 0; j < 8; ++j) v += sh[threadIdx.x][j];
+            part[(size_t)threadIdx.x * kRedBlocks + blockIdx.x] = v;
+        }
+    }
+}
+
+// block of 256 threads; entries are ordered (a, b <= a, then rhs a) for a < kd
+__global__ void __launch_bounds__(256) k_aa_record(AaCtl *a, const double *__restrict__ phi,
+                                                   const double *__restrict__ rho, const double *__restrict__ X,
+                                                   double *__restrict__ F, size_t N, size_t M,
+                                                   double *__restrict__ part) {
+    if (a->skip) return;
+    const int kd = a->hlen;       // differences once this entry is in: hlen + 1 entries
+    switch (kd) {
+        case 0: aa_gram_body<0>(*a, phi, rho, X, F, N, M, part); break;
+        case 1: aa_gram_body<1>(*a, phi, rho, X, F, N, M, part); break;
+        case 2: aa_gram_body<2>(*a, phi, rho, X, F, N, M, part); break;
+        case 3: aa_gram_body<3>(*a, phi, rho, X, F, N, M, part); break;
+        case 4: aa_gram_body<4>(*a, phi, rho, X, F, N, M, part); break;
+        case 5: aa_gram_body<5>(*a, phi, rho, X, F, N, M, part); break;
+        default: aa_gram_body<6>(*a, phi, rho, X, F, N, M, part); break;
+    }
+}
+
+// sum the partials in a fixed order, enter the new entry into the history,
+// and solve the kd x kd normal equations in one thread (Gaussian elimination
+// with partial pivoting; gamma = 0, the plain iterate, if singular)
+__global__ void k_aa_solve(AaCtl *a, const double *__restrict__ part, int nb) {
+    __shared__ double tot[kAaMaxK];
+    if (a->skip) return;
+    const int kd = a->hlen;
+    const int K = kd * (kd + 1) / 2 + kd;
+    for (int k = 0; k < K; ++k) {
+        const double v = block_sum_partials(part + (size_t)k * kRedBlocks, nb);
+        if (threadIdx.x == 0) tot[k] = v;
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    a->hlen += 1;
+    a->kd = kd;
+    double A[kAaMaxDepth * kAaMaxDepth], b[kAaMaxDepth];
+    int k = 0;
+    for (int i = 0; i < kd; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            A[i * kd + j] = A[j * kd + i] = tot[k];
+            ++k;
+        }
+        b[i] = tot[k++];
+    }
+    double tr = 0.0;
+    for (int i = 0; i < kd; ++i) tr += A[i * kd + i];
+    for (int i = 0; i < kd; ++i) A[i * kd + i] += 1e-12 * tr + 1e-300;
+    bool ok = true;
+    for (int c = 0; c < kd && ok; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < kd; ++r)
+            if (fabs(A[r * kd + c]) > fabs(A[piv * kd + c])) piv = r;
+        if (A[piv * kd + c] == 0.0) {
+            ok = false;
+            break;
+        }
+        if (piv != c) {
+            for (int j = 0; j < kd; ++j) {
+                const double t = A[c * kd + j];
+                A[c * kd + j] = A[piv * kd + j];
+                A[piv * kd + j] = t;
+            }
+            const double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < kd; ++r) {
+            const double f = A[r * kd + c] / A[c * kd + c];
+            for (int j = c; j < kd; ++j) A[r * kd + j] -= f * A[c * kd + j];
+            b[r] -= f * b[c];
+        }
+    }
+    if (ok)
+        for (int c = kd - 1; c >= 0; --c) {
+            double v = b[c];
+            for (int j = c + 1; j < kd; ++j) v -= A[c * kd + j] * b[j];
+            b[c] = v / A[c * kd + c];
+        }
+    for (int i = 0; i < kAaMaxDepth; ++i) a->gamma[i] = (ok && i < kd) ? b[i] : 0.0;
+}
+
+// x_new = x + f - sum_a gamma_a (dX_a + dF_a); (phi, rho) = (x_new, exp x_new).
+// With no differences the state stays G(x), as computed by the sweep.
+__global__ void k_aa_update(const AaCtl *__restrict__ a, const double *__restrict__ X,
+                            const double *__restrict__ F, double *__restrict__ phi, double *__restrict__ rho,
+                            size_t N, size_t M) {
+    if (a->skip || a->kd == 0) return;
+    const int R = a->m + 1, kd = a->kd;
+    const double *x = X + (size_t)a->slot * M, *f = F + (size_t)a->slot * M;
+    GRID_LOOP(e, M) {
+        double v = x[e] + f[e];
+        for (int j = 0; j < kd; ++j) {
+            const size_t p0 = (size_t)((a->head + j) % R) * M + e, p1 = (size_t)((a->head + j + 1) % R) * M + e;
+            v -= a->gamma[j] * ((X[p1] - X[p0]) + (F[p1] - F[p0]));
+        }
+        if (e < N) phi[e] = v;
+        else rho[e - N] = exp(v);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -983,6 +1228,12 @@ int gummel_setup(Problem *p) {
          alloc(&g->z, N) && alloc(&g->pv, N) && alloc(&g->Ap, N) && alloc(&g->partial, kRedBlocks) &&
          alloc(&g->scal, S_COUNT);
     if (ok && p->rho_mix == PNP_MIX_ADAPTIVE) ok = alloc(&g->lam, N * p->s) && alloc(&g->prev, N * p->s);
+    if (ok && p->aa_depth > 0) {
+        const size_t M = (1 + (size_t)p->s) * N;
+        ok = alloc(&g->aa_X, (p->aa_depth + 1) * M) && alloc(&g->aa_F, (p->aa_depth + 1) * M) &&
+             alloc(&g->aa_part, (size_t)kAaMaxK * kRedBlocks);
+        if (ok && dmalloc((void **)&g->aa, sizeof(AaCtl), p->stream) != cudaSuccess) ok = false;
+    }
     if (ok) {
         if (dmalloc((void **)&g->dmax, sizeof(unsigned long long), p->stream) != cudaSuccess) ok = false;
         if (ok && dmalloc((void **)&g->stats, sizeof(DevStats), p->stream) != cudaSuccess) ok = false;
@@ -1021,8 +1272,9 @@ void gummel_free(Problem *p) {
     for (int k = 0; k < 2; ++k)
         if (g->cap[k]) cudaStreamDestroy(g->cap[k]);
     for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal, g->lam,
-                      g->prev})
+                      g->prev, g->aa_X, g->aa_F, g->aa_part})
         dfree(a, p->stream);
+    dfree(g->aa, p->stream);
     dfree(g->dmax, p->stream);
     dfree(g->stats, p->stream);
     dfree(g->keep_q, p->stream);
@@ -1101,7 +1353,14 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
     }
     if (e == cudaSuccess && rc == PNP_OK)
         e = cudaStreamBeginCaptureToGraph(sb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    const size_t M = (1 + (size_t)s) * N;
+    const int GM = grid_for(M), NBM = std::min(GM, kRedBlocks);
     if (e == cudaSuccess && rc == PNP_OK) {
+        if (g->aa) {
+            // Anderson: the history entry of the state this sweep starts from
+            k_aa_begin<<<1, 1, 0, sb>>>(g->aa);
+            k_aa_save_x<<<GM, 256, 0, sb>>>(g->aa, g->phi, g->rho, g->aa_X, N, M);
+        }
         // 1. mu_ex from rho^{n-1}
         rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
         cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
@@ -1147,8 +1406,17 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
                                            g->mu + i * N, g->x, g->rho + i * N, g->lam ? g->lam + i * N : nullptr,
                                            g->prev ? g->prev + i * N : nullptr, g->dmax, p->d_flag);
         }
+        if (g->aa) {
+            // Anderson extrapolation of the plain iterate (or a repeat of the
+            // sweep from the last plain iterate after an unphysical one)
+            k_aa_post<<<1, 1, 0, sb>>>(g->aa, g->dmax, p->d_flag, p->tol, g->stats);
+            k_aa_restore<<<GM, 256, 0, sb>>>(g->aa, g->aa_X, g->aa_F, g->phi, g->rho, N, M);
+            k_aa_record<<<NBM, 256, 0, sb>>>(g->aa, g->phi, g->rho, g->aa_X, g->aa_F, N, M, g->aa_part);
+            k_aa_solve<<<1, 256, 0, sb>>>(g->aa, g->aa_part, NBM);
+            k_aa_update<<<GM, 256, 0, sb>>>(g->aa, g->aa_X, g->aa_F, g->phi, g->rho, N, M);
+        }
         // 5. residual, status, continue?
-        k_gummel_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->tol, p->max_iter, g->stats, hg);
+        k_gummel_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->tol, p->max_iter, g->stats, hg, g->aa);
         cudaError_t e2 = cudaStreamEndCapture(sb, &body);
         if (e == cudaSuccess) e = e2;
     }
@@ -1219,6 +1487,7 @@ int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaSt
     }
     cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
     k_stats_reset<<<1, 1, 0, st>>>(g->stats, (p->eq_init && !d_phi0 && !d_rho0) ? 1 : 0);
+    if (g->aa) k_aa_reset<<<1, 1, 0, st>>>(g->aa, p->aa_depth);
     return cuda_status(cudaGraphLaunch(g->exec, st));
 }
 

@@ -153,7 +153,7 @@ static int build_fp64_into(Problem *p, DeviceBuffers *db) {
     if (rc) return rc;
     const Dims d = make_dims(p);
     const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
-    const size_t bytes = sizeof(double) * oct * kNumKernels * p->s;
+    const size_t bytes = sizeof(double) * oct * spec_kernels(p);
     if (dmalloc(&db->spec, bytes, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     db->bytes += bytes;
     const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
@@ -169,6 +169,21 @@ static int build_fp64_into(Problem *p, DeviceBuffers *db) {
                                        sizeof(double) * oct, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_status(e);
         }
+    }
+    if (p->msa) {
+        // MSA pair kernels (Sec 2.3.4), even in every axis, stored negated:
+        // the z-back kernels add spec * rho_j to mu_i
+        const bool even[3] = {false, false, false};
+        for (int i = 0; i < p->s; ++i)
+            for (int j = i; j < p->s; ++j) {
+                Stencil c;
+                build_msa_pair(*p, i, j, c);
+                octant_transform(c, p->L, even, -scale, h.data());
+                cudaError_t e = cudaMemcpy((double *)db->spec +
+                                               (size_t)(p->s * kNumKernels + msa_pair(i, j, p->s)) * oct,
+                                           h.data(), sizeof(double) * oct, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
     }
     p->device_bytes += db->bytes;
     return PNP_OK;
@@ -208,7 +223,7 @@ int mu_ex_prepare(Problem *p, int prec) {
     rc = upload_twiddles(p, db, prec);
     if (rc) return fail(rc);
     const Dims d = make_dims(p);
-    const size_t n = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p->s;
+    const size_t n = (size_t)d.Ox * d.Oy * d.Oz * spec_kernels(p);
     const size_t esz = prec == PNP_PREC_FP32 ? sizeof(float) : sizeof(dd);
     if (dmalloc(&db->spec, esz * n, p->stream) != cudaSuccess) return fail(PNP_ERR_NOMEM);
     db->bytes += esz * n;
@@ -223,13 +238,98 @@ int mu_ex_prepare(Problem *p, int prec) {
     return PNP_OK;
 }
 
-// Workspace, FP64 spectra and the square-well field U = K_sw (x) rho_s.
+static __global__ void k_set(double *__restrict__ a, double v, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// out = K (x) in for one real field on the problem's grid (zero extension on
+// the padded axes) with the FP64 Stockham kernels: x R2C, y, z multiply by the
+// even real spectrum octant `d_spec` (1/(Lx Ly Lz) folded in), y, x C2R.  Uses
+// the workspace; set-up only.
+static int conv_even_field(Problem *p, const double *d_in, const double *d_spec, double *d_out) {
+    int rc = set_smem_attrs<double>();
+    if (rc == PNP_OK)
+        rc = cuda_status(cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    if (rc) return rc;
+    const Dims d = make_dims(p);
+    const size_t N = p->npts();
+    const Launch l = launch_shape(p, PNP_PREC_FP64);
+    Work w = carve(p, PNP_PREC_FP64);
+    DeviceBuffers *db = p->buf[0];
+    double2 *A = (double2 *)w.A, *B = (double2 *)w.B10, *B2 = (double2 *)w.Bs;
+    SpeciesConst one{};
+    one.s = 1;
+    dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, 1);
+    k_xfwd<double><<<gx, 256, l.sm_x, p->stream>>>(d_in, N, A, d, p->ax[0], (const double2 *)db->tw[0], l.P_x);
+    dim3 gy((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, 1);
+    k_ypass<double, false><<<gy, 256, l.sm_y, p->stream>>>(A, B, d, d.ny, d.ny, d.Ly, d.Ly, p->ax[1],
+                                                           (const double2 *)db->tw[1], l.TX_y);
+    dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);
+    k_zconv<<<gz, 256, l.sm_zconv, p->stream>>>(B, B2, d, p->ax[2], (const double2 *)db->tw[2], d_spec, l.TX_z);
+    k_ypass<double, true><<<gy, 256, l.sm_y, p->stream>>>(B2, A, d, d.Ly, d.Ly, d.ny, d.ny, p->ax[1],
+                                                          (const double2 *)db->tw[1], l.TX_y);
+    k_xinv<double><<<gx, 256, l.sm_x, p->stream>>>(A, d_out, N, d, p->ax[0], (const double2 *)db->tw[0], nullptr,
+                                                   one, l.P_x, nullptr);
+    return cuda_status(cudaGetLastError());
+}
+
+// MSA bulk field E_i = sum_j rho_b,j (C_ij (x) 1_Omega) (Sec 2.3.4): with
+// mu_el,i = -sum_j C_ij (x) (rho_j - rho_b,j) on the domain, the density part
+// runs through the z-back kernels every call and this fixed part is added in
+// the last x pass.  One convolution of the indicator of the domain per species
+// with the combined stencil sum_j rho_b,j C_ij.
+static int build_msa_field(Problem *p) {
+    const Dims d = make_dims(p);
+    const size_t N = p->npts();
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    if (dmalloc((void **)&p->d_E, sizeof(double) * N * p->s, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
+    p->device_bytes += sizeof(double) * N * p->s;
+    double *d_one = nullptr, *d_spec = nullptr;
+    cudaError_t e = dmalloc((void **)&d_one, sizeof(double) * N, p->stream);
+    if (e == cudaSuccess) e = dmalloc((void **)&d_spec, sizeof(double) * oct, p->stream);
+    int rc = cuda_status(e);
+    if (rc == PNP_OK) k_set<<<1024, 256, 0, p->stream>>>(d_one, 1.0, N);
+    std::vector<double> h(oct);
+    const bool even[3] = {false, false, false};
+    const double scale = 1.0 / ((double)d.Lx * d.Ly * d.Lz);
+    for (int i = 0; i < p->s && rc == PNP_OK; ++i) {
+        Stencil K;
+        K.S = p->Smsa;
+        K.K.assign((size_t)(2 * K.S + 1) * (2 * K.S + 1) * (2 * K.S + 1), 0.0);
+        for (int j = 0; j < p->s; ++j) {
+            Stencil c;
+            build_msa_pair(*p, i, j, c);
+            for (int mz = -c.S; mz <= c.S; ++mz)
+                for (int my = -c.S; my <= c.S; ++my)
+                    for (int mx = -c.S; mx <= c.S; ++mx) K.at(mx, my, mz) += p->rho_b[j] * c.at(mx, my, mz);
+        }
+        octant_transform(K, p->L, even, scale, h.data());
+        // the previous convolution reads d_spec: copy in stream order
+        e = cudaMemcpyAsync(d_spec, h.data(), sizeof(double) * oct, cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        rc = cuda_status(e);
+        if (rc == PNP_OK) rc = conv_even_field(p, d_one, d_spec, p->d_E + (size_t)i * N);
+    }
+    if (rc == PNP_OK) rc = cuda_status(cudaStreamSynchronize(p->stream));
+    else cudaStreamSynchronize(p->stream);
+    dfree(d_one, p->stream);
+    dfree(d_spec, p->stream);
+    return rc;
+}
+
+// Workspace, FP64 spectra, the square-well field U = K_sw (x) rho_s and the
+// MSA bulk field.
 int mu_ex_setup(Problem *p) {
     p->work_bytes = workspace_bytes(p);
     if (dmalloc(&p->d_work, p->work_bytes, p->stream) != cudaSuccess) return PNP_ERR_NOMEM;
     p->device_bytes += p->work_bytes;
     int rc = build_fp64(p);
     if (rc) return rc;
+    if (p->msa) {
+        rc = build_msa_field(p);
+        if (rc) return rc;
+    }
     if (!p->has_wells) return PNP_OK;
 
     const Dims d = make_dims(p);
@@ -264,27 +364,9 @@ int mu_ex_setup(Problem *p) {
     octant_transform(sw, p->L, even, 1.0 / ((double)d.Lx * d.Ly * d.Lz), h.data());
     if (e == cudaSuccess) e = cudaMemcpy(d_spec, h.data(), sizeof(double) * oct, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        rc = set_smem_attrs<double>();
-        if (rc == PNP_OK)
-            rc = cuda_status(cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        const Launch l = launch_shape(p, PNP_PREC_FP64);
-        Work w = carve(p, PNP_PREC_FP64);
-        DeviceBuffers *db = p->buf[0];
-        double2 *A = (double2 *)w.A, *B = (double2 *)w.B10, *B2 = (double2 *)w.Bs;
-        SpeciesConst one{};
-        one.s = 1;
-        dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, 1);
-        k_xfwd<double><<<gx, 256, l.sm_x, p->stream>>>(d_rs, N, A, d, p->ax[0], (const double2 *)db->tw[0], l.P_x);
-        dim3 gy((d.Wx + l.TX_y - 1) / l.TX_y, d.nz, 1);
-        k_ypass<double, false><<<gy, 256, l.sm_y, p->stream>>>(A, B, d, d.ny, d.ny, d.Ly, d.Ly, p->ax[1],
-                                                               (const double2 *)db->tw[1], l.TX_y);
-        dim3 gz((d.Wx + l.TX_z - 1) / l.TX_z, d.Ly);
-        k_zconv<<<gz, 256, l.sm_zconv, p->stream>>>(B, B2, d, p->ax[2], (const double2 *)db->tw[2], d_spec, l.TX_z);
-        k_ypass<double, true><<<gy, 256, l.sm_y, p->stream>>>(B2, A, d, d.Ly, d.Ly, d.ny, d.ny, p->ax[1],
-                                                              (const double2 *)db->tw[1], l.TX_y);
-        k_xinv<double><<<gx, 256, l.sm_x, p->stream>>>(A, p->d_U, N, d, p->ax[0], (const double2 *)db->tw[0],
-                                                       nullptr, one, l.P_x);
-        e = cudaStreamSynchronize(p->stream);
+        rc = conv_even_field(p, d_rs, d_spec, p->d_U);
+        if (rc == PNP_OK) e = cudaStreamSynchronize(p->stream);
+        else cudaStreamSynchronize(p->stream);
     }
     dfree(d_sites, p->stream);
     dfree(d_rs, p->stream);
@@ -379,8 +461,10 @@ void mu_ex_free(Problem *p) {
     }
     dfree(p->d_work, p->stream);
     dfree(p->d_U, p->stream);
+    dfree(p->d_E, p->stream);
     p->d_work = nullptr;
     p->d_U = nullptr;
+    p->d_E = nullptr;
 }
 
 }  // namespace pnp
@@ -473,7 +557,7 @@ extern "C" int pnp_excess_mu_noalloc(const pnp_problem_desc *desc, const double 
     std::string why;
     int rc = validate_and_copy(desc, &p, &why);
     if (rc) return rc;
-    if (p.has_wells) return PNP_ERR_INVALID;        // hard-sphere part only
+    if (p.has_wells || p.msa) return PNP_ERR_INVALID;   // hard-sphere part only
     if (noalloc_bytes(p) > kNoAllocBytes) return PNP_ERR_TOO_LARGE;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -557,14 +641,16 @@ namespace pnp {
 size_t estimate_device_bytes(const Problem &p) {
     const Dims d = make_dims(&p);
     const size_t N = p.npts();
-    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz * kNumKernels * p.s;
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz * spec_kernels(&p);
     size_t b = workspace_bytes(&p) + oct * sizeof(double);
     if (p.precision == PNP_PREC_FP32 || p.precision == PNP_PREC_TF32SPLIT) b += oct * sizeof(float);
     if (p.precision == PNP_PREC_DF64) b += oct * sizeof(dd);
     if (p.has_wells) b += N * sizeof(double);
+    if (p.msa) b += N * p.s * sizeof(double);               // MSA bulk field
     b += sizeof(double) * (2 * N * p.s + N);                 // host-call staging
     b += sizeof(double) * N * 11 * 8 / 7;                    // multigrid levels
     b += sizeof(double) * N * (2 * (size_t)p.s + 7);         // solve state and CG vectors
+    if (p.aa_depth > 0) b += sizeof(double) * N * (1 + (size_t)p.s) * 2 * (p.aa_depth + 1);   // Anderson history
     return b + b / 16 + (1 << 20);
 }
 

@@ -46,6 +46,7 @@ struct Dims {
 
 struct SpeciesConst {
     int s;
+    int msa;           // 1: z-back also applies the MSA pair kernels (Sec 2.3.4)
     double c0[8];      // 1 / (4 pi R^2)
     double c1[8];      // 1 / (4 pi R)
     double sh[8];      // mu_sh coefficient
@@ -81,9 +82,16 @@ static Dims make_dims(const Problem *p) {
     return d;
 }
 
+// kernels whose octant spectra a problem stores: five FMT weights per
+// species, then the MSA pair kernels (packed upper triangle, negated)
+static int spec_kernels(const Problem *p) {
+    return kNumKernels * p->s + (p->msa ? p->s * (p->s + 1) / 2 : 0);
+}
+
 static SpeciesConst make_sc(const Problem *p) {
     SpeciesConst sc{};
     sc.s = p->s;
+    sc.msa = p->msa ? 1 : 0;
     for (int i = 0; i < p->s; ++i) {
         sc.c0[i] = 1.0 / (4.0 * M_PI * p->R[i] * p->R[i]);
         sc.c1[i] = 1.0 / (4.0 * M_PI * p->R[i]);
@@ -502,6 +510,37 @@ __global__ void k_zback(const typename vec2<T>::type *__restrict__ B10, typename
         }
         __syncthreads();
     }
+    if (sc.msa) {
+        // MSA correlations (Sec 2.3.4): Bs still holds the densities'
+        // y-spectra; mu_i -= sum_j C_ij rho_j (the stored spectra are -C_ij)
+        const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+        const int fy = ky <= d.Ly / 2 ? ky : d.Ly - ky;
+        for (int j = 0; j < sc.s; ++j) {
+            const C *src = Bs + (size_t)j * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
+            for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+                const int z = idx / TX, c = idx % TX, kx = kx0 + c;
+                C v = C{0, 0};
+                if (z < d.nz && kx < d.Wx) v = src[(size_t)z * d.Ly * d.Wx + kx];
+                work[idx] = v;
+            }
+            __syncthreads();
+            C *r = fft_lines<false>(work, scr, TX, ax, tw);
+            for (int idx = threadIdx.x; idx < col; idx += blockDim.x) {
+                const int kz = idx / TX, c = idx % TX, kx = kx0 + c;
+                if (kx >= d.Wx) continue;
+                const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+                const C v = r[idx];
+                for (int i = 0; i < sc.s; ++i) {
+                    const T g = ldgt(&spec[(size_t)(sc.s * kNumKernels + msa_pair(i, j, sc.s)) * oct +
+                                           ((size_t)fz * d.Oy + fy) * d.Ox + kx]);
+                    C &o = acc[(size_t)i * col + idx];
+                    o.x += g * v.x;
+                    o.y += g * v.y;
+                }
+            }
+            __syncthreads();
+        }
+    }
     for (int i = 0; i < sc.s; ++i) {
         C *r = fft_lines<true>(acc + (size_t)i * col, work, TX, ax, tw);
         C *dst = Bs + (size_t)i * d.nz * d.Ly * d.Wx + (size_t)ky * d.Wx;
@@ -519,7 +558,7 @@ __global__ void k_zback(const typename vec2<T>::type *__restrict__ B10, typename
 template <typename T>
 __global__ void k_xinv(const typename vec2<T>::type *__restrict__ A, double *__restrict__ out, size_t out_fstride,
                        Dims d, FftAxis ax, const typename vec2<T>::type *__restrict__ tw,
-                       const double *__restrict__ U, SpeciesConst sc, int P) {
+                       const double *__restrict__ U, SpeciesConst sc, int P, const double *__restrict__ E) {
     using C = typename vec2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *a = reinterpret_cast<C *>(smem_raw);
@@ -554,8 +593,14 @@ __global__ void k_xinv(const typename vec2<T>::type *__restrict__ A, double *__r
             u0 = coef * U[((size_t)z * d.ny + y0) * d.nx + x];
             if (y0 + 1 < d.ny) u1 = coef * U[((size_t)z * d.ny + y0 + 1) * d.nx + x];
         }
-        dst[(size_t)y0 * d.nx + x] = (double)v.x + u0;
-        if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (double)v.y + u1;
+        double r0 = (double)v.x + u0, r1 = (double)v.y + u1;
+        if (E) {
+            const double *e = E + f * out_fstride;
+            r0 += e[((size_t)z * d.ny + y0) * d.nx + x];
+            if (y0 + 1 < d.ny) r1 += e[((size_t)z * d.ny + y0 + 1) * d.nx + x];
+        }
+        dst[(size_t)y0 * d.nx + x] = r0;
+        if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = r1;
     }
 }
 
@@ -785,7 +830,10 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                                                                                         (2 * per_col))));
                 dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
                 const size_t sm = 2 * TX * per_col + (size_t)G * G * cs;   // + twiddle table
-                if (back) {
+                if (back && sc.msa) {
+                    ensure_smem<k_zback_p<T, N1, N2, true>>();
+                    k_zback_p<T, N1, N2, true><<<g, 2 * TX * G, sm, st>>>(B10, Bs, d, twz, spec, sc, TX);
+                } else if (back) {
                     ensure_smem<k_zback_p<T, N1, N2>>();
                     k_zback_p<T, N1, N2><<<g, 2 * TX * G, sm, st>>>(B10, Bs, d, twz, spec, sc, TX);
                 } else {
@@ -850,15 +898,16 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     // 9: x inverse + mu_sh
     tm.begin(8, st);
     const double *U = p->has_wells ? p->d_U : nullptr;
+    const double *E = p->msa ? p->d_E : nullptr;
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
             const int P = x_lines(p, G, Shape<N1, N2>::EX * (long)cs, d.npairs);
             ensure_smem<k_xinv_r<T, N1, N2>>();
             dim3 g((d.npairs + P - 1) / P, d.nz, s);
-            k_xinv_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(A, d_mu, N, d, twx, U, sc, P);
+            k_xinv_r<T, N1, N2><<<g, P * G, P * Shape<N1, N2>::EX * cs, st>>>(A, d_mu, N, d, twx, U, sc, P, E);
         })) {
         dim3 gx((d.npairs + l.P_x - 1) / l.P_x, d.nz, s);
-        k_xinv<T><<<gx, T256, l.sm_x, st>>>(A, d_mu, N, d, p->ax[0], twx, U, sc, l.P_x);
+        k_xinv<T><<<gx, T256, l.sm_x, st>>>(A, d_mu, N, d, p->ax[0], twx, U, sc, l.P_x, E);
     }
     tm.end(st);
     return cuda_status(cudaGetLastError());

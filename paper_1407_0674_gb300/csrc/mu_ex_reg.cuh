@@ -83,7 +83,8 @@ template <typename T, int N1, int N2>
 __global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__restrict__ A,
                                                  double *__restrict__ out, size_t out_fstride, Dims d,
                                                  const typename vec2<T>::type *__restrict__ tw,
-                                                 const double *__restrict__ U, SpeciesConst sc, int P) {
+                                                 const double *__restrict__ U, SpeciesConst sc, int P,
+                                                 const double *__restrict__ E) {
     using C = typename vec2<T>::type;
     constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX, L = N1 * N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -113,8 +114,14 @@ __global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__
                 u0 = coef * U[((size_t)z * d.ny + y0) * d.nx + x];
                 if (y0 + 1 < d.ny) u1 = coef * U[((size_t)z * d.ny + y0 + 1) * d.nx + x];
             }
-            dst[(size_t)y0 * d.nx + x] = (double)v[n2].x + u0;
-            if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = (double)v[n2].y + u1;
+            double r0 = (double)v[n2].x + u0, r1 = (double)v[n2].y + u1;
+            if (E) {
+                const double *e = E + f * out_fstride;
+                r0 += e[((size_t)z * d.ny + y0) * d.nx + x];
+                if (y0 + 1 < d.ny) r1 += e[((size_t)z * d.ny + y0 + 1) * d.nx + x];
+            }
+            dst[(size_t)y0 * d.nx + x] = r0;
+            if (y0 + 1 < d.ny) dst[(size_t)(y0 + 1) * d.nx + x] = r1;
         }
     }
 }
@@ -290,159 +297,6 @@ __global__ void __launch_bounds__(256) k_ypass_r(const typename vec2<T>::type *_
     }
 }
 
-// spectral multiply for output alpha at (kx, ky, kz) from the s density
-// spectra r_i: conj(K_alpha,i) r_i summed over species
-template <typename T, typename C>
-__device__ __forceinline__ C mac_forward(int alpha, const T *__restrict__ spec, const Dims &d, const SpeciesConst &sc,
-                                         int kx, int ky, int kz, const C *r, int rstride) {
-    C acc = C{0, 0};
-    for (int i = 0; i < sc.s; ++i) {
-        const C x = r[i * rstride];
-        if (alpha < 4) {
-            T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
-            if (alpha == 0) g *= sc_c0<T>(sc, i);
-            if (alpha == 1) g *= sc_c1<T>(sc, i);
-            acc.x += g * x.x;
-            acc.y += g * x.y;
-        } else {
-            T sv = spec_at(spec, d, i, 2 + (alpha - 4) % 3, kx, ky, kz);
-            if (alpha < 7) sv *= sc_c1<T>(sc, i);
-            acc.x -= sv * x.y;
-            acc.y += sv * x.x;
-        }
-    }
-    return acc;
-}
-
-// z: forward FFT of the s density columns, the ten weighted-density spectra,
-// inverse FFT, rows z < nz.  block TX*G, grid (ceil(Wx/TX), Ly).
-template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_zmac_r(const typename vec2<T>::type *__restrict__ Bs,
-                                                 typename vec2<T>::type *__restrict__ B10, Dims d,
-                                                 const typename vec2<T>::type *__restrict__ tw,
-                                                 const T *__restrict__ spec, SpeciesConst sc, int TX) {
-    using C = typename vec2<T>::type;
-    constexpr int G = Shape<N1, N2>::G, EX = Shape<N1, N2>::EX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = threadIdx.x / TX, c = threadIdx.x % TX;
-    C *slots = reinterpret_cast<C *>(smem_raw);     // [s][N1][G][TX]
-    C *ex = slots + (size_t)sc.s * N1 * G * TX + c;
-    const int rstride = N1 * G * TX;
-    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * TX + c]; };
-    const int ky = blockIdx.y, kx = blockIdx.x * TX + c;
-    const bool ok = kx < d.Wx;
-    const size_t plane = (size_t)d.Ly * d.Wx;
-    LaneTw<N1, N2, C> lt;
-    lt.load(tw, t);
-    C v[G];
-    for (int i = 0; i < sc.s; ++i) {
-        const C *src = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
-        if (t < N1) {
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) {
-                const int zz = t + N1 * n2;
-                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
-            }
-        }
-        fwd2<N1, N2>(v, lt, ex, t, TX);
-        if (t < N2) {
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = v[k1];
-        }
-    }
-    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
-        if (t < N2) {
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1)
-                v[k1] = ok ? mac_forward(alpha, spec, d, sc, kx, ky, t + N2 * k1, &slot(0, k1), rstride) : C{0, 0};
-        }
-        inv2<N1, N2>(v, lt, ex, t, TX);
-        if (t < N1 && ok) {
-            C *dst = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) {
-                const int zz = t + N1 * n2;
-                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
-            }
-        }
-    }
-}
-
-// z back: forward FFT of each Psi_alpha column, mu_i += K_alpha,i Psi_alpha,
-// inverse FFT of the s accumulators, rows z < nz.
-template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_zback_r(const typename vec2<T>::type *__restrict__ B10,
-                                                  typename vec2<T>::type *__restrict__ Bs, Dims d,
-                                                  const typename vec2<T>::type *__restrict__ tw,
-                                                  const T *__restrict__ spec, SpeciesConst sc, int TX) {
-    using C = typename vec2<T>::type;
-    constexpr int G = Shape<N1, N2>::G;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = threadIdx.x / TX, c = threadIdx.x % TX;
-    C *slots = reinterpret_cast<C *>(smem_raw);     // [s][N1][G][TX]
-    C *ex = slots + (size_t)sc.s * N1 * G * TX + c;
-    const int rstride = N1 * G * TX;
-    auto slot = [&](int i, int k1) -> C & { return slots[i * rstride + (k1 * G + t) * TX + c]; };
-    const int ky = blockIdx.y, kx = blockIdx.x * TX + c;
-    const bool ok = kx < d.Wx;
-    const size_t plane = (size_t)d.Ly * d.Wx;
-    LaneTw<N1, N2, C> lt;
-    lt.load(tw, t);
-    C v[G];
-    if (t < N2)
-        for (int i = 0; i < sc.s; ++i)
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) slot(i, k1) = C{0, 0};
-    for (int alpha = 0; alpha < kNumWeighted; ++alpha) {
-        const C *src = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
-        if (t < N1) {
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) {
-                const int zz = t + N1 * n2;
-                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
-            }
-        }
-        fwd2<N1, N2>(v, lt, ex, t, TX);
-        if (t < N2 && ok) {
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) {
-                const int kz = t + N2 * k1;
-                const C x = v[k1];
-                for (int i = 0; i < sc.s; ++i) {
-                    C &o = slot(i, k1);
-                    if (alpha < 4) {
-                        T g = spec_at(spec, d, i, alpha == 3 ? 1 : 0, kx, ky, kz);
-                        if (alpha == 0) g *= sc_c0<T>(sc, i);
-                        if (alpha == 1) g *= sc_c1<T>(sc, i);
-                        o.x += g * x.x;
-                        o.y += g * x.y;
-                    } else {
-                        T sv = spec_at(spec, d, i, 2 + (alpha - 4) % 3, kx, ky, kz);
-                        if (alpha < 7) sv *= sc_c1<T>(sc, i);
-                        o.x += sv * x.y;
-                        o.y -= sv * x.x;
-                    }
-                }
-            }
-        }
-    }
-    for (int i = 0; i < sc.s; ++i) {
-        if (t < N2) {
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) v[k1] = slot(i, k1);
-        }
-        inv2<N1, N2>(v, lt, ex, t, TX);
-        if (t < N1 && ok) {
-            C *dst = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) {
-                const int zz = t + N1 * n2;
-                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
-            }
-        }
-    }
-}
-
 }  // namespace pnp
 
 namespace pnp {
@@ -583,7 +437,7 @@ __global__ void __launch_bounds__(256) k_zmac_p(const typename vec2<T>::type *__
     }
 }
 
-template <typename T, int N1, int N2>
+template <typename T, int N1, int N2, bool MSA = false>
 __global__ void __launch_bounds__(256) k_zback_p(const typename vec2<T>::type *__restrict__ B10,
                                                   typename vec2<T>::type *__restrict__ Bs, Dims d,
                                                   const typename vec2<T>::type *__restrict__ tw,
@@ -656,6 +510,39 @@ __global__ void __launch_bounds__(256) k_zback_p(const typename vec2<T>::type *_
                                 acc.y -= gg * x.x;
                             }
                         }
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (MSA) {
+        // MSA correlations (Sec 2.3.4): Bs still holds the densities'
+        // y-spectra (written over only below); mu_i -= sum_j C_ij rho_j, the
+        // stored even spectra being -C_ij
+        const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+        const int fy = ky <= d.Ly / 2 ? ky : d.Ly - ky;
+        for (int j = 0; j < sc.s; ++j) {
+            const C *src = Bs + (size_t)j * d.nz * plane + (size_t)ky * d.Wx + kx;
+            if (t < N1) {
+#pragma unroll
+                for (int n2 = 0; n2 < N2; ++n2) {
+                    const int zz = t + N1 * n2;
+                    v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+                }
+            }
+            fwd2<N1, N2>(v, lt, ex, t, lanes);
+            if (t < N2) {
+                for (int i = 0; i < sc.s; ++i) {
+                    const T *base = spec + (size_t)(sc.s * kNumKernels + msa_pair(i, j, sc.s)) * oct +
+                                    (size_t)fy * d.Ox + kx;
+#pragma unroll
+                    for (int k1 = 0; k1 < N1; ++k1) {
+                        const int kz = t + N2 * k1;
+                        const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+                        const T gg = ok ? ldgt(&base[(size_t)fz * d.Oy * d.Ox]) : (T)0;
+                        C &acc = slot(i, k1);
+                        acc.x += gg * v[k1].x;
+                        acc.y += gg * v[k1].y;
                     }
                 }
             }

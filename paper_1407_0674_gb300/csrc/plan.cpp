@@ -193,6 +193,16 @@ void build_msa_stencil(double qq_lB, double B, double sigma, int nmu, int ntheta
     }
 }
 
+// C_ij of a problem on its own reach ceil(R_i + R_j) + 1 (Sec 2.3.4)
+void build_msa_pair(const Problem &p, int i, int j, Stencil &out) {
+    const double sigma = p.R[i] + p.R[j];
+    double kappa2 = 0.0;
+    for (int k = 0; k < p.s; ++k) kappa2 += 4.0 * M_PI * p.lB * p.rho_b[k] * p.q[k] * p.q[k];
+    const double B = msa_B(std::sqrt(kappa2) * sigma);
+    build_msa_stencil((double)p.q[i] * p.q[j] * p.lB, B, sigma, p.quad[0], p.quad[1], p.quad[2],
+                      (int)std::ceil(sigma) + 1, out);
+}
+
 // MSA screening factor B = [xi + 1 - sqrt(1 + 2 xi)] / xi of Sec 2.3.4, taken
 // as 2 xi / (1 + sqrt(1 + 2 xi))^2 (the same number) where the printed form
 // cancels.
@@ -420,6 +430,11 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->max_iter = d->max_iter;
     p->eq_init = eq;
     p->screened = (d->flags & PNP_FLAG_SCREENED_POISSON) != 0;
+    p->msa = (d->flags & PNP_FLAG_MSA) != 0;
+    if (d->anderson_depth < 0 || d->anderson_depth > 6) return bad("anderson_depth must be in 0..6");
+    if (d->anderson_depth > 0 && d->rho_mix == PNP_MIX_ADAPTIVE)
+        return bad("Anderson mixing needs a relaxation without per-point state (not PNP_MIX_ADAPTIVE)");
+    p->aa_depth = d->anderson_depth;
     p->eq_tol = d->eq_tol > 0 ? d->eq_tol : 1e-6;
     p->eq_max_iter = d->eq_max_iter > 0 ? d->eq_max_iter : 1000;
     p->quad[0] = d->quad_nmu; p->quad[1] = d->quad_ntheta; p->quad[2] = d->quad_nr;
@@ -445,7 +460,7 @@ void length_candidates(const Problem *p, int c, std::vector<int> *out) {
         return;
     }
     const bool even = (c == 0);
-    const int minL = n[c] + std::max(p->S, p->Ssw);
+    const int minL = n[c] + std::max(std::max(p->S, p->Ssw), p->Smsa);
     const int L0 = next_smooth(minL, even);
     out->push_back(L0);
     int extra = 0;
@@ -463,7 +478,9 @@ int plan_lengths(Problem *p, const int fft_len[3]) {
     for (double r : p->R) Rmax = std::max(Rmax, r);
     p->S = (int)std::ceil(Rmax) + 1;
     p->Ssw = p->has_wells ? (int)std::ceil(p->well_outer) + 1 : 0;
-    int need = std::max(p->S, p->Ssw);
+    // the MSA pair kernels reach R_i + R_j
+    p->Smsa = p->msa ? (int)std::ceil(2.0 * Rmax) + 1 : 0;
+    int need = std::max(std::max(p->S, p->Ssw), p->Smsa);
     const int n[3] = {p->nx, p->ny, p->nz};
     for (int c = 0; c < 3; ++c) {
         bool even = (c == 0);

@@ -88,10 +88,12 @@ struct Problem {
     int precision = 0;
     double lin_tol = 0.0;             // 0: adaptive inner tolerance
     bool has_wells = false;
+    bool msa = false;                 // mu_ex carries the MSA correlation term (Sec 2.3.4)
+    int aa_depth = 0;                 // Anderson mixing depth of the Gummel loop (0: relaxed only)
 
     // ---- plan ----
     int L[3] = {0, 0, 0};
-    int S = 0, Ssw = 0;
+    int S = 0, Ssw = 0, Smsa = 0;     // stencil half-widths: FMT, square well, MSA pair kernels
     FftAxis ax[3];
     std::vector<double> mu_bulk;      // reservoir mu_ex (bulk Rosenfeld)
 
@@ -102,6 +104,7 @@ struct Problem {
     int *d_flag = nullptr;            // device status bits
     double *d_U = nullptr;            // square-well field sum_m K_sw[m] rho_s(r+m)
     std::vector<double> sh_coef;      // mu_sh,i = sh_coef[i] * U
+    double *d_E = nullptr;            // [s][N] MSA bulk field sum_j rho_b,j (C_ij (x) 1_Omega)
     double *d_sh_coef = nullptr;
     DeviceBuffers *buf[3] = {nullptr, nullptr, nullptr};   // FP64, FP32, double-float
     void *d_work = nullptr;           // shared FFT workspace
@@ -127,6 +130,13 @@ void build_fmt_stencils(double R, int nmu, int ntheta, int nr, int S, Stencil ou
 void build_well_stencil(double r_in, double r_out, int nmu, int ntheta, int nr, int S, Stencil &out);
 void build_msa_stencil(double qq_lB, double B, double sigma, int nmu, int ntheta, int nr, int S, Stencil &out);
 double msa_B(double xi);
+// MSA pair kernels of a problem: pair index of (i, j), i <= j, in the packed
+// upper triangle; count s (s + 1) / 2
+__host__ __device__ inline int msa_pair(int i, int j, int s) {
+    if (i > j) { const int t = i; i = j; j = t; }
+    return i * s - i * (i - 1) / 2 + (j - i);
+}
+void build_msa_pair(const Problem &p, int i, int j, Stencil &out);   // C_ij on its own reach
 void octant_transform(const Stencil &st, const int L[3], const bool odd[3], double scale, double *out);
 double bjerrum_length_h(double T, double eps_r, double h_nm);
 double conductivity_unit_S_per_cm(double T, double h_nm, double D_m2_per_s);

@@ -38,6 +38,7 @@ BC = {"P": 0, "D": 1, "N": 2, 0: 0, 1: 1, 2: 2}
 FLAG_AUTOTUNE = 1
 FLAG_EQUILIBRIUM_INIT = 2
 FLAG_SCREENED_POISSON = 4
+FLAG_MSA = 8
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -70,6 +71,7 @@ class Desc(ctypes.Structure):
         ("eq_tol", ctypes.c_double),
         ("eq_max_iter", ctypes.c_int),
         ("fmt", ctypes.c_int),
+        ("anderson_depth", ctypes.c_int),
     ]
 
 
@@ -178,8 +180,6 @@ class DescHolder:
     points to kept alive."""
 
     def __init__(self, spec, precision="fp64"):
-        if getattr(spec, "msa", False):
-            raise PnpError(ERR_INVALID, "the MSA term is not applied by the library yet")
         d = Desc()
         lib().pnp_desc_init(ctypes.byref(d))
         s = len(spec.R)
@@ -219,10 +219,12 @@ class DescHolder:
         d.lin_tol = float(getattr(spec, "lin_tol", 0.0))
         d.flags = (FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0) | \
             (FLAG_EQUILIBRIUM_INIT if getattr(spec, "eq_init", False) else 0) | \
-            (FLAG_SCREENED_POISSON if getattr(spec, "screened_poisson", False) else 0)
+            (FLAG_SCREENED_POISSON if getattr(spec, "screened_poisson", False) else 0) | \
+            (FLAG_MSA if getattr(spec, "msa", False) else 0)
         d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         d.fmt = int(getattr(spec, "fmt", 0))
+        d.anderson_depth = int(getattr(spec, "anderson", 0))
         self.desc = d
 
 

@@ -245,13 +245,18 @@ def test_msa_stencil_convolution_equals_oracle(pnp):
         np.testing.assert_allclose(got, ref[i], rtol=0, atol=1e-10 * np.abs(ref[i]).max())
 
 
-def test_msa_problems_are_refused_by_the_binding(pnp):
-    """The device path does not apply the MSA term yet: a problem asking for
-    it is refused rather than solved without it."""
-    spec = dataclasses.replace(_msa_spec(), msa=True)
-    with pytest.raises(pnp.PnpError) as e:
-        pnp.plan(spec)
-    assert e.value.code == pnp.ERR_INVALID
+def test_msa_plan_covers_the_pair_reach(pnp):
+    """With the MSA term the padded lengths of the zero-extended axes cover the
+    pair kernels' reach ceil(R_i + R_j) + 1 (> the FMT reach), so the circular
+    convolution never wraps into the domain; periodic axes keep their length."""
+    base = dataclasses.replace(_msa_spec(), nx=9, ny=8, nz=7, bc=("N", "P", "D"))
+    plain, _ = pnp.plan(base)
+    msa, _ = pnp.plan(dataclasses.replace(base, msa=True))
+    reach = int(np.ceil(2 * max(base.R))) + 1
+    assert msa["fft_len"][0] >= base.nx + reach and msa["fft_len"][2] >= base.nz + reach
+    assert msa["fft_len"][1] == base.ny
+    assert plain["fft_len"][0] < base.nx + reach          # the FMT reach alone is shorter
+    assert msa["device_bytes"] > plain["device_bytes"]
 
 
 def test_msa_spectral_plan_on_zero_extended_axes(pnp):

@@ -71,3 +71,7 @@ def test_refuses_what_does_not_fit(env):
     assert pnp.excess_mu_noalloc(spec, dummy, dummy) == pnp.ERR_TOO_LARGE
     wells = film_gummel(16, 16, 16)
     assert pnp.excess_mu_noalloc(wells, dummy, dummy) == pnp.ERR_INVALID
+    # the MSA term is not part of this entry point's pipeline
+    msa, _ = mu_microbench(12)
+    msa.msa = True
+    assert pnp.excess_mu_noalloc(msa, dummy, dummy) == pnp.ERR_INVALID

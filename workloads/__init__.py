@@ -64,7 +64,8 @@ class ProblemSpec:
     eq_max_iter: int = 0                     # its iteration cap (0 = library default)
     screened_poisson: bool = False           # Gummel Poisson step as one screened Newton step
     fmt: int = 0                             # hard-sphere functional: 0 Rosenfeld, 1 White Bear (MFMT)
-    msa: bool = False                        # add the MSA electrostatic-correlation term (oracle only so far)
+    msa: bool = False                        # add the MSA electrostatic-correlation term (Sec 2.3.4)
+    anderson: int = 0                        # Anderson mixing depth of the Gummel iteration (0 = relaxed only)
 
     @property
     def s(self) -> int:
