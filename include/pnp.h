@@ -308,11 +308,24 @@ int pnp_gummel_solve(pnp_problem *p, const double *phi0, const double *rho0, dou
 /* Serving: a queue of independent Gummel solves that run concurrently on one
  * GPU.  Requests are admitted as slots and the device-memory budget allow;
  * each keeps its state resident until it finishes; finished results wait in
- * host memory until polled. */
+ * host memory until polled.
+ * Policies (no counterpart in the paper):
+ *   PNP_SERVE_FIFO: admission in arrival order; every solve runs on its
+ *     problem's stream at the default priority.
+ *   PNP_SERVE_SMALLEST_FIRST: the queued request with the fewest unknowns
+ *     (grid points x (species + 1)) is admitted first, and each solve runs on
+ *     a stream whose CUDA priority rises as its grid shrinks (one level per
+ *     factor 8 in grid points), so small solves' kernels are scheduled ahead
+ *     of large ones already running: short requests are not held behind long
+ *     ones, at the cost of the long ones' latency (a long request can wait as
+ *     long as shorter ones keep arriving).  Results are the same bits under
+ *     either policy. */
+enum { PNP_SERVE_FIFO = 0, PNP_SERVE_SMALLEST_FIRST = 1 };
 typedef struct {
     size_t hbm_budget_bytes;       /* device memory the server may hold, 0 -> 150 GB */
     int max_slots;                 /* concurrently resident solves, 0 -> 64 */
     int max_queue;                 /* waiting requests, 0 -> 4096 */
+    int policy;                    /* PNP_SERVE_* */
 } pnp_server_opts;
 
 typedef struct {
@@ -362,8 +375,9 @@ int pnp_plane_flux(pnp_problem *p, int species, const double *phi, const double 
  * the well field the library builds on the device at set-up (site-site pairs
  * are a constant and mobile-mobile wells are absent).  Its derivative with
  * respect to rho_i is -eps_i U, twice mu_sh,i when sw_half keeps the 1/2.
- * rho [s][nz][ny][nx] (host, FP64, >= 0); *F_sh = 0 without wells.  U is
- * copied to the host and the dot products summed there in a fixed order.
+ * rho [s][nz][ny][nx] (host, FP64, >= 0); *F_sh = 0 without wells.  The
+ * densities are copied to the device and the sum is a fixed-shape device
+ * reduction against U (the same bits every call).  Synchronises.
  * Errors: PNP_ERR_INVALID, PNP_ERR_NOMEM, PNP_ERR_CUDA. */
 int pnp_square_well_energy(pnp_problem *p, const double *rho, double *F_sh);
 

@@ -463,28 +463,30 @@ int pnp_plane_flux(pnp_problem *h, int species, const double *phi, const double 
 int pnp_square_well_energy(pnp_problem *h, const double *rho, double *F_sh) {
     if (!h || !rho || !F_sh) return PNP_ERR_INVALID;
     Problem *p = h->impl;
-    const size_t N = p->npts();
-    if (!host_values_ok(rho, N * p->s, 1)) return PNP_ERR_INVALID;
+    const size_t N = p->npts(), n = N * p->s;
+    if (!host_values_ok(rho, n, 1)) return PNP_ERR_INVALID;
     *F_sh = 0.0;
     if (!p->has_wells) return PNP_OK;
-    // the well field U = K_sw (x) rho_s was built on the device at set-up
-    std::vector<double> U;
-    try {
-        U.resize(N);
-    } catch (const std::bad_alloc &) {
-        return PNP_ERR_NOMEM;
+    if (!p->d_io) {
+        if (dmalloc((void **)&p->d_io, sizeof(double) * (2 * n + N), p->stream) != cudaSuccess)
+            return PNP_ERR_NOMEM;
+        p->device_bytes += sizeof(double) * (2 * n + N);
     }
-    cudaError_t e = cudaMemcpyAsync(U.data(), p->d_U, sizeof(double) * N, cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    cudaStream_t st = p->stream;
+    p->last_stream = st;
+    // densities staged, then a fixed-order reduction against the well field
+    // U = K_sw (x) rho_s built on the device at set-up
+    double *d_rho = p->d_io, *d_red = nullptr;
+    cudaError_t e = dmalloc((void **)&d_red, sizeof(double) * 520, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rho, rho, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    int rc = cuda_status(e);
+    if (rc == PNP_OK) rc = square_well_energy_enqueue(p, d_rho, d_red, d_red + 8, st);
     double F = 0.0;
-    for (int i = 0; i < p->s; ++i) {
-        if (p->depth[i] == 0.0) continue;
-        const double *r = rho + (size_t)i * N;
-        double acc = 0.0;
-        for (size_t k = 0; k < N; ++k) acc += r[k] * U[k];
-        F -= p->depth[i] * acc;
-    }
+    if (rc == PNP_OK) rc = cuda_status(cudaMemcpyAsync(&F, d_red, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (rc == PNP_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    else cudaStreamSynchronize(st);
+    dfree(d_red, st);
+    if (rc) return rc;
     *F_sh = F;
     return PNP_OK;
 }

@@ -375,6 +375,58 @@ int mu_ex_setup(Problem *p) {
     return cuda_status(e);
 }
 
+// ---------------------------------------------------------------------------
+// Square-well free energy F_sh = -sum_i eps_i sum_r rho_i(r) U(r) (Sec 2.3.2,
+// mobile-site part) as a fixed-shape device reduction: each thread sums its
+// points in grid-stride order (species inside, in order), each block a tree,
+// then one block sums the block partials in a tree; the same bits every call.
+constexpr int kFshBlocks = 512;
+
+static __global__ void __launch_bounds__(256) k_fsh_partial(const double *__restrict__ U,
+                                                            const double *__restrict__ rho, size_t N, int s,
+                                                            SpeciesConst sc, double *__restrict__ part) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int i = 0; i < s; ++i) v += sc.c0[i] * rho[(size_t)i * N + p];
+        acc += v * U[p];
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+static __global__ void __launch_bounds__(kFshBlocks) k_fsh_final(const double *__restrict__ part, int nb,
+                                                                double *__restrict__ out) {
+    __shared__ double sh[kFshBlocks];
+    sh[threadIdx.x] = (int)threadIdx.x < nb ? part[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int w = kFshBlocks / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// F_sh of the device densities d_rho [s][N] into d_out[0]; d_part holds
+// kFshBlocks doubles.  Problems without wells get 0.
+int square_well_energy_enqueue(Problem *p, const double *d_rho, double *d_out, double *d_part, cudaStream_t st) {
+    const size_t N = p->npts();
+    if (!p->has_wells || !p->d_U) return cuda_status(cudaMemsetAsync(d_out, 0, sizeof(double), st));
+    SpeciesConst c{};
+    c.s = p->s;
+    for (int i = 0; i < p->s; ++i) c.c0[i] = -p->depth[i];     // coefficient of rho_i U
+    const int nb = (int)std::min<size_t>(kFshBlocks, std::max<size_t>(1, (N + 255) / 256));
+    k_fsh_partial<<<nb, 256, 0, st>>>(p->d_U, d_rho, N, p->s, c, d_part);
+    k_fsh_final<<<1, kFshBlocks, 0, st>>>(d_part, nb, d_out);
+    return cuda_status(cudaGetLastError());
+}
+
 int mu_ex_enqueue(Problem *p, int prec, const double *d_rho, double *d_mu, cudaStream_t st) {
     int rc = mu_ex_prepare(p, prec);
     if (rc) return rc;

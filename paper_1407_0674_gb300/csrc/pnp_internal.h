@@ -153,6 +153,8 @@ int mu_ex_setup(Problem *p);                 // workspace, spectra, mu_sh
 int mu_ex_prepare(Problem *p, int prec);     // lazily build one precision's buffers
 int mu_ex_enqueue(Problem *p, int prec, const double *d_rho, double *d_mu, cudaStream_t st);
 void mu_ex_free(Problem *p);
+// F_sh (Sec 2.3.2) of device densities into d_out[0] (d_part: 512 doubles)
+int square_well_energy_enqueue(Problem *p, const double *d_rho, double *d_out, double *d_part, cudaStream_t st);
 
 // gummel.cu
 int gummel_setup(Problem *p);

@@ -1,8 +1,8 @@
 // Serving loop: a queue of independent Gummel solves running concurrently on
 // one GPU (pnp_server_* in include/pnp.h).
 //
-// A worker thread owns the device work.  It admits queued requests in arrival
-// order while a slot is free and the request's device footprint (estimated
+// A worker thread owns the device work.  It admits queued requests (in arrival
+// order, or smallest first with PNP_SERVE_SMALLEST_FIRST) while a slot is free and the request's device footprint (estimated
 // from its plan before anything is allocated) fits the memory budget, builds
 // the problem, and launches its whole solve -- one CUDA graph whose loops end
 // on the device -- on the problem's own stream, followed by copies of the
@@ -40,6 +40,7 @@ struct Request {
     int s = 0;
     // running state
     Problem *prob = nullptr;
+    cudaStream_t own_stream = nullptr;           // priority stream (PNP_SERVE_SMALLEST_FIRST)
     cudaEvent_t done_ev = nullptr;
     double *h_phi = nullptr, *h_rho = nullptr;   // pinned
     void *h_stats = nullptr;                     // pinned
@@ -132,6 +133,8 @@ static void deep_copy(const pnp_problem_desc *d, Request *r, const double *phi0,
 static void release(pnp_server *s, Request *r) {
     if (r->prob) destroy_problem_internal(r->prob);
     r->prob = nullptr;
+    if (r->own_stream) cudaStreamDestroy(r->own_stream);
+    r->own_stream = nullptr;
     if (r->done_ev) cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
     s->pinned.put(r->h_phi);
@@ -156,6 +159,18 @@ static int start(pnp_server *s, Request *r) {
     r->h_stats = s->pinned.get(gummel_stats_bytes());
     if (!r->h_phi || !r->h_rho || !r->h_stats) return PNP_ERR_NOMEM;
     cudaStream_t st = p->stream;
+    if (s->opts.policy == PNP_SERVE_SMALLEST_FIRST) {
+        // one priority level per factor 8 in grid points: 32^3 and smaller
+        // highest, up to the lowest level the device offers
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e != cudaSuccess) return cuda_status(e);
+        const int level = std::max(0, (int)std::floor(std::log2((double)std::max<size_t>(N, 1)) / 3.0) - 5);
+        const int prio = std::min(least, greatest + level);
+        e = cudaStreamCreateWithPriority(&r->own_stream, cudaStreamNonBlocking, prio);
+        if (e != cudaSuccess) return cuda_status(e);
+        st = r->own_stream;
+    }
     const double *d_phi0 = nullptr, *d_rho0 = nullptr;
     if (!r->phi0.empty() || !r->rho0.empty()) {
         const size_t n = N * r->s;
@@ -210,9 +225,15 @@ static void worker_main(pnp_server *s) {
                 s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
             if (s->stop) break;
             while (!s->queue.empty() && (int)(running.size() + admit.size()) < s->opts.max_slots) {
-                Request *r = s->queue.front();
+                auto it = s->queue.begin();
+                if (s->opts.policy == PNP_SERVE_SMALLEST_FIRST)
+                    it = std::min_element(s->queue.begin(), s->queue.end(), [](const Request *a, const Request *b) {
+                        const size_t wa = a->npts * (a->s + 1), wb = b->npts * (b->s + 1);
+                        return wa != wb ? wa < wb : a->ticket < b->ticket;
+                    });
+                Request *r = *it;
                 if (s->bytes_in_use + r->bytes > s->opts.hbm_budget_bytes) break;
-                s->queue.pop_front();
+                s->queue.erase(it);
                 s->bytes_in_use += r->bytes;
                 admit.push_back(r);
             }
@@ -261,6 +282,10 @@ int pnp_server_create(const pnp_server_opts *opts, pnp_server **out) {
     if (s->opts.hbm_budget_bytes == 0) s->opts.hbm_budget_bytes = (size_t)150 << 30;
     if (s->opts.max_slots <= 0) s->opts.max_slots = 64;
     if (s->opts.max_queue <= 0) s->opts.max_queue = 4096;
+    if (s->opts.policy != PNP_SERVE_FIFO && s->opts.policy != PNP_SERVE_SMALLEST_FIRST) {
+        delete s;
+        return PNP_ERR_INVALID;
+    }
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return PNP_ERR_CUDA;

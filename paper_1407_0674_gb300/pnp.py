@@ -39,6 +39,7 @@ FLAG_AUTOTUNE = 1
 FLAG_EQUILIBRIUM_INIT = 2
 FLAG_SCREENED_POISSON = 4
 FLAG_MSA = 8
+SERVE = {"fifo": 0, "smallest_first": 1}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -88,7 +89,8 @@ class Info(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int),
+                ("policy", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -403,8 +405,8 @@ class Problem:
 class Server:
     """Owns a pnp_server handle."""
 
-    def __init__(self, hbm_budget_bytes=0, max_slots=0, max_queue=0):
-        o = ServerOpts(hbm_budget_bytes, max_slots, max_queue)
+    def __init__(self, hbm_budget_bytes=0, max_slots=0, max_queue=0, policy="fifo"):
+        o = ServerOpts(hbm_budget_bytes, max_slots, max_queue, SERVE[policy])
         h = ctypes.c_void_p()
         _check(lib().pnp_server_create(ctypes.byref(o), ctypes.byref(h)), "pnp_server_create")
         self.h = h

@@ -41,17 +41,20 @@ def test_conductivity_of_converged_state(pnp):
     assert sig[1] == pytest.approx(ref[1], rel=1e-8)
 
 
-@pytest.mark.parametrize("depth2", [0.0, 0.7])
-def test_square_well_energy_matches_oracle(pnp, depth2):
-    """pnp_square_well_energy (the device well field, summed against rho on
-    the host) against the oracle's direct-quadrature F_sh; a film without
-    wells gives exactly zero."""
-    spec = film_gummel(16, 12, 10, nsites=6)
+@pytest.mark.parametrize("depth2,shape", [(0.0, (16, 12, 10)), (0.7, (16, 12, 10)), (0.7, (48, 40, 36))])
+def test_square_well_energy_matches_oracle(pnp, depth2, shape):
+    """pnp_square_well_energy (the device well field, summed against rho by a
+    fixed-shape device reduction; the largest grid spans 270 blocks) against
+    the oracle's direct-quadrature F_sh, the same bits on a repeat call; a
+    film without wells gives exactly zero."""
+    nx, ny, nz = shape
+    spec = film_gummel(nx, ny, nz, nsites=6)
     spec.depth = (1.0, depth2)
     rng = np.random.default_rng(12)
     rho = np.stack([spec.rho_b[i] * rng.lognormal(0.0, 0.3, spec.shape) for i in range(spec.s)])
     with pnp.Problem(spec) as P:
         F = P.square_well_energy(rho)
+        assert P.square_well_energy(rho) == F
     ref = oracle.square_well_energy(spec, rho)
     assert ref < 0
     assert F == pytest.approx(ref, rel=1e-10)

@@ -154,3 +154,59 @@ def test_warm_start_through_server(pnp):
     r = drain(srv, [t])[t]
     assert r[0] == 0 and r[3]["iterations"] <= 2
     srv.close()
+
+
+def completion_order(pnp, policy, specs):
+    """Submit `specs` in order to a one-slot server; return the tickets in the
+    order their results became ready."""
+    srv = pnp.Server(max_slots=1, policy=policy)
+    tickets = []
+    for s in specs:
+        rc, t = srv.submit(s)
+        assert rc == 0
+        tickets.append(t)
+    order, res = [], {}
+    t0 = time.time()
+    while len(order) < len(tickets):
+        for t in tickets:
+            if t in res:
+                continue
+            r = srv.poll(t)
+            if r[0] != 1:
+                res[t] = r
+                order.append(t)
+        assert time.time() - t0 < 300
+        time.sleep(0.002)
+    srv.close()
+    return tickets, order, res
+
+
+def test_smallest_first_lets_a_small_request_overtake(pnp):
+    """One slot, three 32^3 solves submitted ahead of an 8x8x10 one: first in,
+    first out the small one finishes last; smallest first it finishes right
+    after the solve that was already running, with the same bits."""
+    big = [small(0.1 * k, shape=(32, 32, 32), seed=10 + k) for k in range(3)]
+    little = small(0.3, seed=3)
+    specs = big + [little]
+    tk, order, res = completion_order(pnp, "fifo", specs)
+    assert order[-1] == tk[3]
+    tk2, order2, res2 = completion_order(pnp, "smallest_first", specs)
+    assert order2.index(tk2[3]) <= 1, order2
+    for a, b in zip(tk, tk2):
+        assert res[a][0] == 0 and res2[b][0] == 0
+        np.testing.assert_array_equal(res[a][2], res2[b][2])
+
+
+def test_priority_streams_keep_results_bitwise(pnp):
+    """Smallest first with every request admitted at once (priority streams
+    only): each result is the same bits as the solve run alone."""
+    specs = mix()
+    srv = pnp.Server(max_slots=8, policy="smallest_first")
+    tickets = [srv.submit(s)[1] for s in specs]
+    res = drain(srv, tickets)
+    srv.close()
+    for s, t in zip(specs, tickets):
+        rc, phi, rho, st = res[t]
+        assert rc == 0
+        phi1, rho1, _ = alone(pnp, s)
+        np.testing.assert_array_equal(rho, rho1)
