@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--solve-prec", default="df64", choices=["fp64", "df64", "fp32", "tf32split"],
                     help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
     ap.add_argument("--autotune", type=int, default=1, help="autotune the batched / served problems' plans")
+    ap.add_argument("--solve-aa", type=int, default=3,
+                    help="Anderson depth of the batched / served solves (0: the recipe's relaxation; > 0 with the "
+                         "step-limited geometric relaxation); the sequential FP64 baseline keeps the recipe's")
+    ap.add_argument("--policy", default="smallest_first", choices=["fifo", "smallest_first"],
+                    help="admission policy of the batched / served solves")
     ap.add_argument("--variants", default="df64,fp32,tf32split,fp64", help="precisions to time, headline first")
     ap.add_argument("--solves", type=int, default=16,
                     help="mu_ex workload: solves of the batch recipe served concurrently, against the same solves "
@@ -527,7 +532,8 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     if rank == 0 and args.solves > 0:
         from workloads import batch_specs
-        line["solves"] = batch_record(batch_specs(args.solves), args.solve_prec, args.autotune, args.solves)
+        line["solves"] = batch_record(batch_specs(args.solves), args.solve_prec, args.autotune, args.solves,
+                                      aa=args.solve_aa, policy=args.policy)
     barrier(world)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -588,14 +594,25 @@ def oracle_sweep_seconds(spec, sweeps):
     return (time.perf_counter() - t0) / sweeps, oracle.num_threads()
 
 
-def batch_record(specs, solve_prec, autotune, seq_count, log=sys.stderr):
+def served_variant(spec, autotune, aa):
+    """The served form of a request: autotuned plan and, with aa > 0, the
+    relaxed iteration accelerated by Anderson mixing of depth aa on the
+    step-limited geometric relaxation (same fixed point as the recipe's)."""
+    s = dataclasses.replace(spec, autotune=autotune)
+    if aa > 0:
+        s = dataclasses.replace(s, anderson=aa, rho_mix=2)
+    return s
+
+
+def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", log=sys.stderr):
     """Independent Gummel solves of the batch recipe served concurrently
-    (mu_ex in `solve_prec`, FP64 Gummel update and linear solves) against the
-    first `seq_count` of the same solves one at a time in plain FP64.
+    (mu_ex in `solve_prec`, FP64 Gummel update and linear solves, Anderson
+    depth `aa`, admission `policy`) against the first `seq_count` of the same
+    solves one at a time in plain FP64 with the recipe's relaxation.
     Latency of a served solve = submission (all at t = 0) to poll-ready."""
     import numpy as np
     from paper_1407_0674_gb300 import pnp
-    served = [dataclasses.replace(s, autotune=autotune) for s in specs]
+    served = [served_variant(s, autotune, aa) for s in specs]
     seq = []
     seq_res = {}
     for k, s in enumerate(specs[:seq_count]):
@@ -606,7 +623,7 @@ def batch_record(specs, solve_prec, autotune, seq_count, log=sys.stderr):
             seq_res[k] = (rho, st)
         print(f"sequential fp64 {k} ({s.nx}x{s.ny}x{s.nz}): status {st['status']} it {st['iterations']} "
               f"{seq[-1]:.1f} s", file=log, flush=True)
-    srv = pnp.Server(max_slots=64)
+    srv = pnp.Server(max_slots=64, policy=policy)
     t0 = time.perf_counter()
     tickets = []
     for s in served:
@@ -638,6 +655,9 @@ def batch_record(specs, solve_prec, autotune, seq_count, log=sys.stderr):
                     + ", T U(250,400) K, wells 0.3 eV/kT, packing U(0.1,0.35), residual 1e-8; served "
                       "concurrently (one CUDA graph per solve) vs one at a time in plain FP64",
         "mu_ex_precision": solve_prec,
+        "served_solver": (f"Anderson depth {aa} on the step-limited geometric relaxation (0.05)" if aa > 0 else
+                          "the recipe's relaxation") + f", policy {policy}",
+        "sequential_solver": "the recipe's relaxation (per-point adaptive, 0.05), plain FP64 mu_ex",
         "served": {"solves": len(specs), "solves_per_s": len(specs) / wall, "wall_s": wall,
                    "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
                    "converged": sum(1 for v in done.values() if v[0] == 0),
@@ -677,6 +697,18 @@ def run_solves(args, world, rank, local):
                                        "64 sites, bias 0.1 kT/e) to residual 1e-8"},
                 "iterations": st["iterations"], "linear_iterations": st["linear_iterations"],
                 "residual": st["residual"]}
+        if args.solve_aa > 0:
+            # the same solve with Anderson mixing (same fixed point)
+            sa = dataclasses.replace(spec, anderson=args.solve_aa)
+            with pnp.Problem(sa) as P:
+                P.gummel_solve()
+                t0 = time.perf_counter()
+                _, rho_a, sta = P.gummel_solve()
+                dta = time.perf_counter() - t0
+            line["anderson"] = {"depth": args.solve_aa, "solves_per_s": world / dta, "ms_per_solve": dta * 1e3,
+                                "iterations": sta["iterations"],
+                                "max_rel_err_rho_vs_plain": max(float(np.abs(rho_a[i] - rho[i]).max() /
+                                                                      np.abs(rho[i]).max()) for i in range(2))}
         if rank == 0 and not args.no_cpu_baseline:
             k = 2
             per, threads = oracle_sweep_seconds(spec, k)
@@ -738,7 +770,8 @@ def run_solves(args, world, rank, local):
             print(json.dumps(line), flush=True)
         return
     if args.workload == "batch":
-        rec = batch_record(batch_specs(args.batch), args.solve_prec, args.autotune, args.seq)
+        rec = batch_record(batch_specs(args.batch), args.solve_prec, args.autotune, args.seq, aa=args.solve_aa,
+                           policy=args.policy)
         line = {"metric": "PNP solves/s", "value": world * rec["served"]["solves_per_s"], "unit": "solves/s",
                 "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": rec["served"]["wall_s"] * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -752,7 +785,7 @@ def run_solves(args, world, rank, local):
     # serve
     arr = serving_arrivals(args.requests, rate=args.rate, hi=args.max_edge)
     specs = [serving_spec(n, bias, T) for (_, n, bias, T) in arr]
-    served = [dataclasses.replace(s, autotune=args.autotune) for s in specs]
+    served = [served_variant(s, args.autotune, args.solve_aa) for s in specs]
     seq = []
     for s in specs[:args.seq]:
         with pnp.Problem(s) as P:
@@ -761,7 +794,7 @@ def run_solves(args, world, rank, local):
             seq.append(time.perf_counter() - t0)
         print(f"serve sequential n {s.nx}: status {st['status']} it {st['iterations']} {seq[-1]:.1f} s",
               file=sys.stderr, flush=True)
-    srv = pnp.Server(max_slots=64)
+    srv = pnp.Server(max_slots=64, policy=args.policy)
     t0 = time.perf_counter()
     pending = {}
     lat = []

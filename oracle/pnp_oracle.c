@@ -1199,7 +1199,10 @@ int oracle_gummel(const oracle_problem *p, const double *phi0, const double *rho
  *   gamma = argmin || f - dF gamma ||_2   (normal equations, tiny ridge),
  *   x <- x + f - (dX + dF) gamma.
  * If the extrapolated state is unphysical (packing or a non-finite value in
- * the next sweep) the history is dropped and the plain iterate G(x) taken.
+ * the next sweep) the history is dropped and the plain iterate G(x) taken;
+ * if the sweep from that fails as well, the step from the last recorded
+ * iterate x is halved, x + f/2, x + f/4, ..., at most AA_BACKTRACK times (x
+ * swept cleanly, so a short enough step does too).
  * Stops on the residual of the base map, max(|dphi|, max_i |drho_i| / rho_b,i)
  * < tol, like the plain iteration; so the fixed point is the same.
  * Returns 0 converged, 1 not converged, 2 packing of a plain iterate.     */
@@ -1268,6 +1271,7 @@ static int small_solve(int k, double *A, double *b)
     return 0;
 }
 
+#define AA_BACKTRACK 8
 int oracle_gummel_anderson(const oracle_problem *p, int m, double *phi, double *rho, int *iters, double *hist)
 {
     long N = (long)p->nx * p->ny * p->nz, plane = (long)p->nx * p->ny;
@@ -1292,11 +1296,23 @@ int oracle_gummel_anderson(const oracle_problem *p, int m, double *phi, double *
     for (n = 1; n <= p->max_iter; ++n) {
         int rc = gummel_sweep(p, mub, phi, rho, phi_g, rho_g, mu, rb, &rr);
         if (rc && hlen > 0 && n > 1) {
-            /* the extrapolated state is unphysical: restart from the last plain iterate */
-            for (long k = 0; k < N; ++k) phi[k] = g[k];
-            for (long k = 0; k < s * N; ++k) rho[k] = exp(g[N + k]);
-            hlen = 0;
-            rc = gummel_sweep(p, mub, phi, rho, phi_g, rho_g, mu, rb, &rr);
+            /* the state is unphysical: restart from the last plain iterate
+             * g = x + f of the last recorded pair, and while the sweep from
+             * there fails too, halve the step: x + theta f, theta = 1/2,
+             * 1/4, ... down to 2^-AA_BACKTRACK (x itself swept cleanly) */
+            double theta = 1.0;
+            for (int bt = 0; rc && bt <= AA_BACKTRACK; ++bt) {
+                if (bt == 0) {
+                    for (long k = 0; k < N; ++k) phi[k] = g[k];
+                    for (long k = 0; k < s * N; ++k) rho[k] = exp(g[N + k]);
+                } else {
+                    for (long k = 0; k < N; ++k) phi[k] = x[k] + theta * f[k];
+                    for (long k = 0; k < s * N; ++k) rho[k] = exp(x[N + k] + theta * f[N + k]);
+                }
+                hlen = 0;
+                rc = gummel_sweep(p, mub, phi, rho, phi_g, rho_g, mu, rb, &rr);
+                theta *= 0.5;
+            }
         }
         if (rc) { status = 2; break; }
         if (hist) hist[n - 1] = rr;

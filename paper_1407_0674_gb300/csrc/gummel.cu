@@ -73,8 +73,11 @@ struct AaCtl {
     int skip;          // 1: no extrapolation this iteration (converged or failed)
     int rslot;         // entry whose X + F is restored on a redo
     int kd;            // differences in the history this iteration
+    int bt;            // backtracking level after a failed sweep (-1: none)
+    double theta;      // step factor of the state being retried
     double gamma[kAaMaxDepth];
 };
+constexpr int kAaBacktrack = 8;    // step halvings after the restart from the plain iterate
 
 struct GummelState {
     std::vector<Level> lv;
@@ -94,6 +97,7 @@ struct GummelState {
     // and residuals f = G(x) - x, [m+1][(1+s) N] each, a control block and the
     // Gram reduction's block partials
     double *aa_X = nullptr, *aa_F = nullptr, *aa_part = nullptr;
+    double *aa_xb = nullptr, *aa_fb = nullptr;   // base pair (x, f) of a backtrack
     struct AaCtl *aa = nullptr;
     unsigned long long *dmax = nullptr;
     size_t bytes = 0;
@@ -828,12 +832,16 @@ __global__ void k_stats_reset(DevStats *st, int eq_enable) {
 //   x <- x + f - sum_a gamma_a (dX_a + dF_a).
 // If the sweep from an extrapolated state is unphysical (packing, overflow,
 // non-finite) the history is dropped and the sweep repeated from the last
-// plain iterate G(x_prev) = X + F of the newest entry, in the same iteration.
+// plain iterate G(x_prev) = X + F of the newest entry, in the same iteration;
+// while that fails as well, the step from x_prev is halved (x_prev + F/2,
+// x_prev + F/4, ..., kAaBacktrack times at most).
 // The stopping test is on the plain sweep's residual, so the fixed point is
 // the relaxed iteration's.
 __global__ void k_aa_reset(AaCtl *a, int m) {
     a->m = m;
     a->head = a->hlen = a->slot = a->redo = a->skip = a->rslot = a->kd = 0;
+    a->bt = -1;
+    a->theta = 1.0;
 }
 
 // start of an iteration: make room for the entry of the current state
@@ -860,30 +868,54 @@ __global__ void k_aa_save_x(const AaCtl *__restrict__ a, const double *__restric
 }
 
 // after the sweep: a failed sweep from an extrapolated state (history and
-// not the first iteration) is repeated from the last plain iterate; a
-// converged or failed one is not extrapolated
+// not the first iteration) is repeated from the last plain iterate x + f of
+// the newest entry; while the repeat fails too, from x + theta f with theta
+// halved each time (x swept cleanly), at most kAaBacktrack times; a converged
+// or failed sweep is not extrapolated
 __global__ void k_aa_post(AaCtl *a, const unsigned long long *dmax, int *flag, double tol, const DevStats *st) {
     const double rr = __longlong_as_double((long long)*dmax);
     const int bad = *flag & (kFlagPacking | kFlagOverflow | kFlagNonFinite);
-    if (bad && a->hlen > 0 && st->iters > 0) {
-        a->redo = 1;
+    if (bad && st->iters > 0 && (a->hlen > 0 || a->bt >= 0)) {
+        if (a->hlen > 0) {
+            a->bt = 0;
+            a->rslot = (a->head + a->hlen - 1) % (a->m + 1);
+        } else {
+            a->bt += 1;
+        }
         a->skip = 1;
-        a->rslot = (a->head + a->hlen - 1) % (a->m + 1);
+        if (a->bt > kAaBacktrack) {
+            a->bt = -1;           // give up: the error ends the solve
+            return;
+        }
+        a->redo = 1;
+        a->theta = ldexp(1.0, -a->bt);
         a->hlen = 0;
         atomicAnd(flag, ~(kFlagPacking | kFlagOverflow | kFlagNonFinite));
-    } else if (bad || rr < tol) {
-        a->skip = 1;
+        return;
     }
+    if (!bad) a->bt = -1;
+    if (bad || rr < tol) a->skip = 1;
 }
 
-// redo: (phi, rho) = the plain iterate X + F of the newest history entry
+// redo: (phi, rho) = x + theta f of the base pair, taken from the newest
+// history entry at the first repeat (theta = 1: the plain iterate)
 __global__ void k_aa_restore(const AaCtl *__restrict__ a, const double *__restrict__ X,
-                             const double *__restrict__ F, double *__restrict__ phi, double *__restrict__ rho,
-                             size_t N, size_t M) {
+                             const double *__restrict__ F, double *__restrict__ xb, double *__restrict__ fb,
+                             double *__restrict__ phi, double *__restrict__ rho, size_t N, size_t M) {
     if (!a->redo) return;
     const double *x = X + (size_t)a->rslot * M, *f = F + (size_t)a->rslot * M;
+    const bool first = a->bt == 0;
+    const double th = a->theta;
     GRID_LOOP(e, M) {
-        const double v = x[e] + f[e];
+        double v;
+        if (first) {
+            const double xe = x[e], fe = f[e];
+            xb[e] = xe;
+            fb[e] = fe;
+            v = xe + fe;
+        } else {
+            v = xb[e] + th * fb[e];
+        }
         if (e < N) phi[e] = v;
         else rho[e - N] = exp(v);
     }
@@ -1231,7 +1263,7 @@ int gummel_setup(Problem *p) {
     if (ok && p->aa_depth > 0) {
         const size_t M = (1 + (size_t)p->s) * N;
         ok = alloc(&g->aa_X, (p->aa_depth + 1) * M) && alloc(&g->aa_F, (p->aa_depth + 1) * M) &&
-             alloc(&g->aa_part, (size_t)kAaMaxK * kRedBlocks);
+             alloc(&g->aa_part, (size_t)kAaMaxK * kRedBlocks) && alloc(&g->aa_xb, M) && alloc(&g->aa_fb, M);
         if (ok && dmalloc((void **)&g->aa, sizeof(AaCtl), p->stream) != cudaSuccess) ok = false;
     }
     if (ok) {
@@ -1272,7 +1304,7 @@ void gummel_free(Problem *p) {
     for (int k = 0; k < 2; ++k)
         if (g->cap[k]) cudaStreamDestroy(g->cap[k]);
     for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal, g->lam,
-                      g->prev, g->aa_X, g->aa_F, g->aa_part})
+                      g->prev, g->aa_X, g->aa_F, g->aa_part, g->aa_xb, g->aa_fb})
         dfree(a, p->stream);
     dfree(g->aa, p->stream);
     dfree(g->dmax, p->stream);
@@ -1410,7 +1442,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
             // Anderson extrapolation of the plain iterate (or a repeat of the
             // sweep from the last plain iterate after an unphysical one)
             k_aa_post<<<1, 1, 0, sb>>>(g->aa, g->dmax, p->d_flag, p->tol, g->stats);
-            k_aa_restore<<<GM, 256, 0, sb>>>(g->aa, g->aa_X, g->aa_F, g->phi, g->rho, N, M);
+            k_aa_restore<<<GM, 256, 0, sb>>>(g->aa, g->aa_X, g->aa_F, g->aa_xb, g->aa_fb, g->phi, g->rho, N, M);
             k_aa_record<<<NBM, 256, 0, sb>>>(g->aa, g->phi, g->rho, g->aa_X, g->aa_F, N, M, g->aa_part);
             k_aa_solve<<<1, 256, 0, sb>>>(g->aa, g->aa_part, NBM);
             k_aa_update<<<GM, 256, 0, sb>>>(g->aa, g->aa_X, g->aa_F, g->phi, g->rho, N, M);

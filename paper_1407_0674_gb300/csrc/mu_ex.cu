@@ -702,7 +702,7 @@ size_t estimate_device_bytes(const Problem &p) {
     b += sizeof(double) * (2 * N * p.s + N);                 // host-call staging
     b += sizeof(double) * N * 11 * 8 / 7;                    // multigrid levels
     b += sizeof(double) * N * (2 * (size_t)p.s + 7);         // solve state and CG vectors
-    if (p.aa_depth > 0) b += sizeof(double) * N * (1 + (size_t)p.s) * 2 * (p.aa_depth + 1);   // Anderson history
+    if (p.aa_depth > 0) b += sizeof(double) * N * (1 + (size_t)p.s) * 2 * (p.aa_depth + 2);   // Anderson history
     return b + b / 16 + (1 << 20);
 }
 
