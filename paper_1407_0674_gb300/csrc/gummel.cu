@@ -539,6 +539,127 @@ __global__ void k_coarse_smem(Op A, double *__restrict__ x_out, const double *__
     for (int p = threadIdx.x; p < n; p += blockDim.x) x_out[p] = x[p];
 }
 
+// ---------------------------------------------------------------------------
+// The coarse part of the V-cycle in one CTA.  From the first level with at
+// most kCtaVcycleMax points down to the coarsest, a V-cycle is a few hundred
+// tiny dependent steps; as separate kernels each costs a launch.  This kernel
+// runs the same steps -- the same per-point arithmetic in the same order, so
+// the same bits -- with a block barrier between them, the coarsest solve in
+// shared memory as k_coarse_smem does.
+constexpr int kCtaVcycleMax = 4096;
+constexpr int kCtaVcycleThreads = 1024;
+constexpr int kMaxChain = 16;
+struct VLevel {
+    int nx, ny, nz, fx, fy, fz;
+    const double *cx, *cy, *cz, *czlo, *dg;
+    double *x, *b;
+};
+struct VChain {
+    int n;                  // levels in the chain (the last is the coarsest)
+    double scale;
+    VLevel L[kMaxChain];
+};
+
+__device__ __forceinline__ Op vop(const VLevel &L) { return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo, L.dg}; }
+
+__device__ __forceinline__ void cta_color(const Op &A, double *x, const double *b, int color) {
+    const int n = A.nx * A.ny * A.nz;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+        if (((i + j + k) & 1) != color) continue;
+        x[p] = (b[p] + op_nbr(A, x, i, j, k, p)) / op_diag(A, i, j, k, p);
+    }
+    __syncthreads();
+}
+
+// x = M b on the chain's first level (x0, b0; the levels' own vectors below)
+__global__ void __launch_bounds__(kCtaVcycleThreads) k_vcycle_cta(VChain ch, double *__restrict__ x0,
+                                                                 const double *__restrict__ b0) {
+    extern __shared__ double csm[];
+    for (int q = 0; q + 1 < ch.n; ++q) {
+        const VLevel &L = ch.L[q], &C = ch.L[q + 1];
+        const Op A = vop(L);
+        double *x = q ? L.x : x0;
+        const double *b = q ? L.b : b0;
+        const int n = L.nx * L.ny * L.nz;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+            x[p] = ((i + j + k) & 1) ? 0.0 : b[p] / op_diag(A, i, j, k, p);
+        }
+        __syncthreads();
+        cta_color(A, x, b, 1);
+        cta_color(A, x, b, 0);
+        cta_color(A, x, b, 1);
+        const int cn = C.nx * C.ny * C.nz;
+        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
+            const int I = c % C.nx, J = (c / C.nx) % C.ny, K = c / (C.nx * C.ny);
+            double sum = 0;
+            for (int kk = 0; kk < L.fz; ++kk)
+                for (int bb = 0; bb < L.fy; ++bb)
+                    for (int a = 0; a < L.fx; ++a) {
+                        const int i = I * L.fx + a, j = J * L.fy + bb, k = K * L.fz + kk;
+                        const size_t pp = pidx(i, j, k, A.nx, A.ny);
+                        sum += b[pp] - (op_diag(A, i, j, k, pp) * x[pp] - op_nbr(A, x, i, j, k, pp));
+                    }
+            C.b[c] = sum;
+        }
+        __syncthreads();
+    }
+    {
+        // coarsest level in shared memory, as k_coarse_smem
+        const VLevel &L = ch.L[ch.n - 1];
+        const Op A = vop(L);
+        double *xo = ch.n > 1 ? L.x : x0;
+        const double *bi = ch.n > 1 ? L.b : b0;
+        const int n = L.nx * L.ny * L.nz;
+        double *x = csm, *b = csm + n, *dg = csm + 2 * n, *cx = csm + 3 * n, *cy = csm + 4 * n, *cz = csm + 5 * n,
+               *cl = csm + 6 * n;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            x[p] = 0.0;
+            b[p] = bi[p];
+            cx[p] = A.cx[p];
+            cy[p] = A.cy[p];
+            cz[p] = A.cz[p];
+            cl[p] = A.czlo[p];
+        }
+        __syncthreads();
+        const Op S{A.nx, A.ny, A.nz, cx, cy, cz, cl};
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+            dg[p] = op_diag(S, i, j, k, p) + (A.dg ? A.dg[p] : 0.0);
+        }
+        __syncthreads();
+        const int order[4] = {0, 1, 1, 0};
+        for (int sw = 0; sw < kCoarseSweeps; ++sw)
+            for (int c = 0; c < 4; ++c) {
+                for (int p = threadIdx.x; p < n; p += blockDim.x) {
+                    const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
+                    if (((i + j + k) & 1) != order[c]) continue;
+                    x[p] = (b[p] + op_nbr(S, x, i, j, k, p)) / dg[p];
+                }
+                __syncthreads();
+            }
+        for (int p = threadIdx.x; p < n; p += blockDim.x) xo[p] = x[p];
+        __syncthreads();
+    }
+    for (int q = ch.n - 2; q >= 0; --q) {
+        const VLevel &L = ch.L[q], &C = ch.L[q + 1];
+        const Op A = vop(L);
+        double *x = q ? L.x : x0;
+        const double *b = q ? L.b : b0;
+        const int n = L.nx * L.ny * L.nz;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = p % L.nx, j = (p / L.nx) % L.ny, k = p / (L.nx * L.ny);
+            x[p] += ch.scale * C.x[pidx(i / L.fx, j / L.fy, k / L.fz, C.nx, C.ny)];
+        }
+        __syncthreads();
+        cta_color(A, x, b, 1);
+        cta_color(A, x, b, 0);
+        cta_color(A, x, b, 1);
+        cta_color(A, x, b, 0);
+    }
+}
+
 // y = A x and the block partial sums of x . y
 __global__ void k_apply_dot(Op A, const double *__restrict__ x, double *__restrict__ y, double *__restrict__ partial) {
     __shared__ double sh[256];
@@ -1087,6 +1208,20 @@ static void vcycle(GummelState *g, int l, cudaStream_t st, double *x = nullptr, 
     if (!b) b = L.b;
     const Op A = op_of(L, g->shift);
     const int G = grid_for(L.n);
+    const int nl = (int)g->lv.size();
+    if (L.n <= (size_t)kCtaVcycleMax && nl - l <= kMaxChain && g->lv.back().n <= (size_t)kCoarseMax) {
+        // this level and every coarser one in a single CTA
+        VChain ch{};
+        ch.n = nl - l;
+        ch.scale = kCoarseScale;
+        for (int q = 0; q < ch.n; ++q) {
+            const Level &V = g->lv[l + q];
+            const Op o = op_of(V, g->shift);
+            ch.L[q] = VLevel{V.nx, V.ny, V.nz, V.fx, V.fy, V.fz, o.cx, o.cy, o.cz, o.czlo, o.dg, V.x, V.b};
+        }
+        k_vcycle_cta<<<1, kCtaVcycleThreads, 7 * g->lv.back().n * sizeof(double), st>>>(ch, x, b);
+        return;
+    }
     if (l + 1 == (int)g->lv.size()) {
         if (L.n <= (size_t)kCoarseMax)
             k_coarse_smem<<<1, 256, 7 * L.n * sizeof(double), st>>>(A, x, b);
@@ -1281,6 +1416,7 @@ int gummel_setup(Problem *p) {
     p->device_bytes += g->bytes;
     p->mg_levels = (int)g->lv.size();
     cudaFuncSetAttribute(k_coarse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
+    cudaFuncSetAttribute(k_vcycle_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
     // Poisson operator on every level (into the p* arrays)
     PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
     set_operator(g, true);
