@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--max-iter3", type=int, default=2000, help="film3: Gummel iteration cap per bias point")
     ap.add_argument("--solve-prec", default="df64", choices=["fp64", "df64", "fp32", "tf32split"],
                     help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
-    ap.add_argument("--autotune", type=int, default=1, help="autotune the batched / served problems' plans")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="autotune the batched / served problems' plans (timing candidates on a loaded GPU)")
     ap.add_argument("--solve-aa", type=int, default=3,
                     help="Anderson depth of the batched / served solves (0: the recipe's relaxation; > 0 with the "
                          "step-limited geometric relaxation); the sequential FP64 baseline keeps the recipe's")
@@ -265,11 +266,11 @@ def stage_flops(name, dims, s):
 # changes after the capture.
 PROFILED_TRAFFIC = {
     ("fp64", "z_back"): 1.1299e9,     # k_zback_p_fp64_120_pad256.md
-    ("fp32", "z_back"): 5.559e8,      # k_zback_p_fp32_120_pad256.md
-    # k_z_dd_120_pad256.md: 1057.1 / 1068.4 MB at 120^3, x (algorithmic bytes
-    # at 128^3 / at 120^3) = 1137 / 1082 MB
-    ("df64", "z_mac"): 1.1108e9,
-    ("df64", "z_back"): 1.1227e9,
+    ("fp32", "z_back"): None,
+    # k_zq4_dd_120_pad256.md: 1037.7 / 1072.3 MB at 120^3, x (algorithmic
+    # bytes at 128^3 / at 120^3) = 1137 / 1082 MB
+    ("df64", "z_mac"): 1.0904e9,
+    ("df64", "z_back"): 1.1268e9,
 }
 # FP32-pipe instructions (thread-level FADD + FMUL + FFMA) one launch of a
 # double-float kernel executes, from ncu's per-opcode counts (profiles/): the
@@ -277,8 +278,8 @@ PROFILED_TRAFFIC = {
 # one of the Ly x Wx columns over the full length Lz whatever nz is, so the
 # 120^3 capture holds for 128^3 as it is.  None for a kernel changed since.
 PROFILED_FP32_INST = {
-    ("df64", "z_mac"): 4.1144e10,      # k_z_dd_120_pad256.md
-    ("df64", "z_back"): 4.1144e10,
+    ("df64", "z_mac"): 4.3043e10,      # k_zq4_dd_120_pad256.md
+    ("df64", "z_back"): 4.3229e10,
 }
 
 DTYPE = {"fp64": "f64",
@@ -697,6 +698,13 @@ def run_solves(args, world, rank, local):
                                        "64 sites, bias 0.1 kT/e) to residual 1e-8"},
                 "iterations": st["iterations"], "linear_iterations": st["linear_iterations"],
                 "residual": st["residual"]}
+        # where an iteration's device time goes (the solve graph's phase marks)
+        sp = dataclasses.replace(spec, phase_timing=True)
+        with pnp.Problem(sp) as P:
+            P.gummel_solve()
+            _, _, stp = P.gummel_solve()
+            ph = P.gummel_phase_times()
+        line["phases_ms_per_iteration"] = {k: v / max(stp["iterations"], 1) for k, v in ph.items()}
         if args.solve_aa > 0:
             # the same solve with Anderson mixing (same fixed point)
             sa = dataclasses.replace(spec, anderson=args.solve_aa)

@@ -121,6 +121,14 @@ enum { PNP_PREC_DEFAULT = -1, PNP_PREC_FP64 = 0, PNP_PREC_FP32 = 1, PNP_PREC_DF6
  * pnp_excess_mu_noalloc (PNP_ERR_INVALID). */
 #define PNP_FLAG_MSA 8u
 
+/* PNP_FLAG_PHASE_TIMING (no counterpart in the paper): the solve graph also
+ * marks the boundaries of the phases of every Gummel iteration with the GPU's
+ * nanosecond global timer (one single-thread kernel per boundary) and sums
+ * the time spent in each phase; pnp_gummel_phase_times reads the sums of the
+ * last solve.  Results are unchanged; the marks add a few microseconds per
+ * iteration. */
+#define PNP_FLAG_PHASE_TIMING 16u
+
 /* hard-sphere functional (Sec 2.3.1): Rosenfeld's, whose derivatives the
  * paper prints, or the White Bear (modified FMT) form it names beside it, in
  * which the n2^3 term carries phi3(n3) / (36 pi),
@@ -304,6 +312,16 @@ const char *pnp_stage_name(int stage);
  * PNP_ERR_OVERFLOW, PNP_ERR_INVALID, PNP_ERR_CUDA. */
 int pnp_gummel_solve(pnp_problem *p, const double *phi0, const double *rho0, double *phi_out,
                      double *rho_out, pnp_stats *stats);
+
+/* Per-phase device time of the last pnp_gummel_solve of a problem created
+ * with PNP_FLAG_PHASE_TIMING, summed over its Gummel iterations: ms[0] mu_ex,
+ * ms[1] the Poisson step (right-hand side, multigrid-preconditioned CG, phi
+ * relaxation), ms[2] the Nernst-Planck solves and density updates of every
+ * species, ms[3] the end of the iteration (Anderson mixing when enabled, the
+ * residual and the loop decision).  Fills min(max_phases, 4) entries and
+ * returns 4; the equilibrium stage is not included.  Synchronises.  Errors:
+ * PNP_ERR_INVALID (no flag, no solve yet, bad arguments), PNP_ERR_CUDA. */
+int pnp_gummel_phase_times(pnp_problem *p, double *ms, int max_phases);
 
 /* Serving: a queue of independent Gummel solves that run concurrently on one
  * GPU.  Requests are admitted as slots and the device-memory budget allow;

@@ -491,6 +491,11 @@ int pnp_square_well_energy(pnp_problem *h, const double *rho, double *F_sh) {
     return PNP_OK;
 }
 
+int pnp_gummel_phase_times(pnp_problem *h, double *ms, int max_phases) {
+    if (!h || !ms) return PNP_ERR_INVALID;
+    return gummel_phase_times(h->impl, ms, max_phases);
+}
+
 int pnp_selftest_bounded_wait(double limit_ms) { return bounded_wait_probe(limit_ms); }
 
 int pnp_test_fail_alloc_at(long k) {

@@ -99,6 +99,7 @@ struct GummelState {
     double *aa_X = nullptr, *aa_F = nullptr, *aa_part = nullptr;
     double *aa_xb = nullptr, *aa_fb = nullptr;   // base pair (x, f) of a backtrack
     struct AaCtl *aa = nullptr;
+    double *phase = nullptr;          // PNP_FLAG_PHASE_TIMING: ns per phase, then the last mark
     unsigned long long *dmax = nullptr;
     size_t bytes = 0;
     bool poisson_ready = false;
@@ -537,127 +538,6 @@ __global__ void k_coarse_smem(Op A, double *__restrict__ x_out, const double *__
             __syncthreads();
         }
     for (int p = threadIdx.x; p < n; p += blockDim.x) x_out[p] = x[p];
-}
-
-// ---------------------------------------------------------------------------
-// The coarse part of the V-cycle in one CTA.  From the first level with at
-// most kCtaVcycleMax points down to the coarsest, a V-cycle is a few hundred
-// tiny dependent steps; as separate kernels each costs a launch.  This kernel
-// runs the same steps -- the same per-point arithmetic in the same order, so
-// the same bits -- with a block barrier between them, the coarsest solve in
-// shared memory as k_coarse_smem does.
-constexpr int kCtaVcycleMax = 4096;
-constexpr int kCtaVcycleThreads = 1024;
-constexpr int kMaxChain = 16;
-struct VLevel {
-    int nx, ny, nz, fx, fy, fz;
-    const double *cx, *cy, *cz, *czlo, *dg;
-    double *x, *b;
-};
-struct VChain {
-    int n;                  // levels in the chain (the last is the coarsest)
-    double scale;
-    VLevel L[kMaxChain];
-};
-
-__device__ __forceinline__ Op vop(const VLevel &L) { return Op{L.nx, L.ny, L.nz, L.cx, L.cy, L.cz, L.czlo, L.dg}; }
-
-__device__ __forceinline__ void cta_color(const Op &A, double *x, const double *b, int color) {
-    const int n = A.nx * A.ny * A.nz;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
-        if (((i + j + k) & 1) != color) continue;
-        x[p] = (b[p] + op_nbr(A, x, i, j, k, p)) / op_diag(A, i, j, k, p);
-    }
-    __syncthreads();
-}
-
-// x = M b on the chain's first level (x0, b0; the levels' own vectors below)
-__global__ void __launch_bounds__(kCtaVcycleThreads) k_vcycle_cta(VChain ch, double *__restrict__ x0,
-                                                                 const double *__restrict__ b0) {
-    extern __shared__ double csm[];
-    for (int q = 0; q + 1 < ch.n; ++q) {
-        const VLevel &L = ch.L[q], &C = ch.L[q + 1];
-        const Op A = vop(L);
-        double *x = q ? L.x : x0;
-        const double *b = q ? L.b : b0;
-        const int n = L.nx * L.ny * L.nz;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
-            x[p] = ((i + j + k) & 1) ? 0.0 : b[p] / op_diag(A, i, j, k, p);
-        }
-        __syncthreads();
-        cta_color(A, x, b, 1);
-        cta_color(A, x, b, 0);
-        cta_color(A, x, b, 1);
-        const int cn = C.nx * C.ny * C.nz;
-        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
-            const int I = c % C.nx, J = (c / C.nx) % C.ny, K = c / (C.nx * C.ny);
-            double sum = 0;
-            for (int kk = 0; kk < L.fz; ++kk)
-                for (int bb = 0; bb < L.fy; ++bb)
-                    for (int a = 0; a < L.fx; ++a) {
-                        const int i = I * L.fx + a, j = J * L.fy + bb, k = K * L.fz + kk;
-                        const size_t pp = pidx(i, j, k, A.nx, A.ny);
-                        sum += b[pp] - (op_diag(A, i, j, k, pp) * x[pp] - op_nbr(A, x, i, j, k, pp));
-                    }
-            C.b[c] = sum;
-        }
-        __syncthreads();
-    }
-    {
-        // coarsest level in shared memory, as k_coarse_smem
-        const VLevel &L = ch.L[ch.n - 1];
-        const Op A = vop(L);
-        double *xo = ch.n > 1 ? L.x : x0;
-        const double *bi = ch.n > 1 ? L.b : b0;
-        const int n = L.nx * L.ny * L.nz;
-        double *x = csm, *b = csm + n, *dg = csm + 2 * n, *cx = csm + 3 * n, *cy = csm + 4 * n, *cz = csm + 5 * n,
-               *cl = csm + 6 * n;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            x[p] = 0.0;
-            b[p] = bi[p];
-            cx[p] = A.cx[p];
-            cy[p] = A.cy[p];
-            cz[p] = A.cz[p];
-            cl[p] = A.czlo[p];
-        }
-        __syncthreads();
-        const Op S{A.nx, A.ny, A.nz, cx, cy, cz, cl};
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
-            dg[p] = op_diag(S, i, j, k, p) + (A.dg ? A.dg[p] : 0.0);
-        }
-        __syncthreads();
-        const int order[4] = {0, 1, 1, 0};
-        for (int sw = 0; sw < kCoarseSweeps; ++sw)
-            for (int c = 0; c < 4; ++c) {
-                for (int p = threadIdx.x; p < n; p += blockDim.x) {
-                    const int i = p % A.nx, j = (p / A.nx) % A.ny, k = p / (A.nx * A.ny);
-                    if (((i + j + k) & 1) != order[c]) continue;
-                    x[p] = (b[p] + op_nbr(S, x, i, j, k, p)) / dg[p];
-                }
-                __syncthreads();
-            }
-        for (int p = threadIdx.x; p < n; p += blockDim.x) xo[p] = x[p];
-        __syncthreads();
-    }
-    for (int q = ch.n - 2; q >= 0; --q) {
-        const VLevel &L = ch.L[q], &C = ch.L[q + 1];
-        const Op A = vop(L);
-        double *x = q ? L.x : x0;
-        const double *b = q ? L.b : b0;
-        const int n = L.nx * L.ny * L.nz;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            const int i = p % L.nx, j = (p / L.nx) % L.ny, k = p / (L.nx * L.ny);
-            x[p] += ch.scale * C.x[pidx(i / L.fx, j / L.fy, k / L.fz, C.nx, C.ny)];
-        }
-        __syncthreads();
-        cta_color(A, x, b, 1);
-        cta_color(A, x, b, 0);
-        cta_color(A, x, b, 1);
-        cta_color(A, x, b, 0);
-    }
 }
 
 // y = A x and the block partial sums of x . y
@@ -1194,6 +1074,19 @@ __global__ void k_aa_update(const AaCtl *__restrict__ a, const double *__restric
 }
 
 // ---------------------------------------------------------------------------
+// phase boundaries of a Gummel iteration (PNP_FLAG_PHASE_TIMING): the global
+// nanosecond timer at each mark; the time since the previous mark is added to
+// phase `slot` (slot < 0: only the mark).  rec[kPhases] holds the last mark.
+constexpr int kPhases = 4;
+__global__ void k_phase_mark(double *rec, int slot) {
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    unsigned long long *last = reinterpret_cast<unsigned long long *>(rec + kPhases);
+    if (slot >= 0) rec[slot] += (double)(now - *last);
+    *last = now;
+}
+
+// ---------------------------------------------------------------------------
 // host orchestration
 static int grid_for(size_t n) { return (int)std::min<size_t>(std::max<size_t>((n + 255) / 256, 1), 152 * 16); }
 
@@ -1208,20 +1101,6 @@ static void vcycle(GummelState *g, int l, cudaStream_t st, double *x = nullptr, 
     if (!b) b = L.b;
     const Op A = op_of(L, g->shift);
     const int G = grid_for(L.n);
-    const int nl = (int)g->lv.size();
-    if (L.n <= (size_t)kCtaVcycleMax && nl - l <= kMaxChain && g->lv.back().n <= (size_t)kCoarseMax) {
-        // this level and every coarser one in a single CTA
-        VChain ch{};
-        ch.n = nl - l;
-        ch.scale = kCoarseScale;
-        for (int q = 0; q < ch.n; ++q) {
-            const Level &V = g->lv[l + q];
-            const Op o = op_of(V, g->shift);
-            ch.L[q] = VLevel{V.nx, V.ny, V.nz, V.fx, V.fy, V.fz, o.cx, o.cy, o.cz, o.czlo, o.dg, V.x, V.b};
-        }
-        k_vcycle_cta<<<1, kCtaVcycleThreads, 7 * g->lv.back().n * sizeof(double), st>>>(ch, x, b);
-        return;
-    }
     if (l + 1 == (int)g->lv.size()) {
         if (L.n <= (size_t)kCoarseMax)
             k_coarse_smem<<<1, 256, 7 * L.n * sizeof(double), st>>>(A, x, b);
@@ -1395,6 +1274,7 @@ int gummel_setup(Problem *p) {
          alloc(&g->z, N) && alloc(&g->pv, N) && alloc(&g->Ap, N) && alloc(&g->partial, kRedBlocks) &&
          alloc(&g->scal, S_COUNT);
     if (ok && p->rho_mix == PNP_MIX_ADAPTIVE) ok = alloc(&g->lam, N * p->s) && alloc(&g->prev, N * p->s);
+    if (ok && p->phase_timing) ok = alloc(&g->phase, kPhases + 1);
     if (ok && p->aa_depth > 0) {
         const size_t M = (1 + (size_t)p->s) * N;
         ok = alloc(&g->aa_X, (p->aa_depth + 1) * M) && alloc(&g->aa_F, (p->aa_depth + 1) * M) &&
@@ -1416,7 +1296,6 @@ int gummel_setup(Problem *p) {
     p->device_bytes += g->bytes;
     p->mg_levels = (int)g->lv.size();
     cudaFuncSetAttribute(k_coarse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
-    cudaFuncSetAttribute(k_vcycle_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, 7 * kCoarseMax * 8);
     // Poisson operator on every level (into the p* arrays)
     PhysConst c{p->nx, p->ny, p->nz, p->bc[0], p->bc[1], p->lB, p->phi_lo, p->phi_hi};
     set_operator(g, true);
@@ -1440,7 +1319,7 @@ void gummel_free(Problem *p) {
     for (int k = 0; k < 2; ++k)
         if (g->cap[k]) cudaStreamDestroy(g->cap[k]);
     for (double *a : {g->mu, g->phi, g->rho, g->rhs, g->x, g->r, g->z, g->pv, g->Ap, g->partial, g->scal, g->lam,
-                      g->prev, g->aa_X, g->aa_F, g->aa_part, g->aa_xb, g->aa_fb})
+                      g->prev, g->aa_X, g->aa_F, g->aa_part, g->aa_xb, g->aa_fb, g->phase})
         dfree(a, p->stream);
     dfree(g->aa, p->stream);
     dfree(g->dmax, p->stream);
@@ -1524,6 +1403,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
     const size_t M = (1 + (size_t)s) * N;
     const int GM = grid_for(M), NBM = std::min(GM, kRedBlocks);
     if (e == cudaSuccess && rc == PNP_OK) {
+        if (g->phase) k_phase_mark<<<1, 1, 0, sb>>>(g->phase, -1);
         if (g->aa) {
             // Anderson: the history entry of the state this sweep starts from
             k_aa_begin<<<1, 1, 0, sb>>>(g->aa);
@@ -1531,6 +1411,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
         }
         // 1. mu_ex from rho^{n-1}
         rc = mu_ex_enqueue(p, p->precision, g->rho, g->mu, sb);
+        if (g->phase) k_phase_mark<<<1, 1, 0, sb>>>(g->phase, 0);
         cudaMemsetAsync(g->dmax, 0, sizeof(unsigned long long), sb);
         // 2. Poisson for phi*, starting from phi; 3. relax phi
         set_operator(g, true);
@@ -1556,6 +1437,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
             set_operator(g, true);
             k_relax_phi<<<G, 256, 0, sb>>>(g->phi, g->x, p->lambda_phi, N, g->dmax);
         }
+        if (g->phase) k_phase_mark<<<1, 1, 0, sb>>>(g->phase, 1);
         // 4. Nernst-Planck per species
         for (int i = 0; i < s && e == cudaSuccess; ++i) {
             NpConst nc;
@@ -1574,6 +1456,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
                                            g->mu + i * N, g->x, g->rho + i * N, g->lam ? g->lam + i * N : nullptr,
                                            g->prev ? g->prev + i * N : nullptr, g->dmax, p->d_flag);
         }
+        if (g->phase) k_phase_mark<<<1, 1, 0, sb>>>(g->phase, 2);
         if (g->aa) {
             // Anderson extrapolation of the plain iterate (or a repeat of the
             // sweep from the last plain iterate after an unphysical one)
@@ -1585,6 +1468,7 @@ static int build_graph(Problem *p, int *d_q, double *d_rhof) {
         }
         // 5. residual, status, continue?
         k_gummel_check<<<1, 1, 0, sb>>>(g->dmax, p->d_flag, p->tol, p->max_iter, g->stats, hg, g->aa);
+        if (g->phase) k_phase_mark<<<1, 1, 0, sb>>>(g->phase, 3);
         cudaError_t e2 = cudaStreamEndCapture(sb, &body);
         if (e == cudaSuccess) e = e2;
     }
@@ -1656,6 +1540,7 @@ int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaSt
     cudaMemsetAsync(p->d_flag, 0, sizeof(int), st);
     k_stats_reset<<<1, 1, 0, st>>>(g->stats, (p->eq_init && !d_phi0 && !d_rho0) ? 1 : 0);
     if (g->aa) k_aa_reset<<<1, 1, 0, st>>>(g->aa, p->aa_depth);
+    if (g->phase) k_fill<<<1, 32, 0, st>>>(g->phase, 0.0, kPhases + 1);
     return cuda_status(cudaGraphLaunch(g->exec, st));
 }
 
@@ -1687,6 +1572,17 @@ int plane_flux(Problem *p, int i, const double *d_phi, const double *d_mu, const
 }
 
 size_t gummel_stats_bytes() { return sizeof(DevStats); }
+
+int gummel_phase_times(Problem *p, double *ms, int max_phases) {
+    GummelState *g = p->gs;
+    if (!g || !g->phase || !ms || max_phases < 0) return PNP_ERR_INVALID;
+    double h[kPhases];
+    cudaError_t e = cudaMemcpyAsync(h, g->phase, sizeof(h), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < kPhases && k < max_phases; ++k) ms[k] = h[k] * 1e-6;
+    return kPhases;
+}
 
 void gummel_decode_stats(const void *raw, pnp_stats *out) {
     const DevStats *hs = (const DevStats *)raw;

@@ -246,6 +246,7 @@ static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int 
 }  // namespace pnp
 
 #include "mu_ex_reg.cuh"
+#include "zcol256.cuh"
 
 namespace pnp {
 
@@ -738,6 +739,69 @@ static int x_lines(const Problem *p, int G, long ex_bytes, int npairs) {
 // split derivative stage (see stage 5 of run_pipeline)
 constexpr bool kSplitDerivatives = true;
 
+// z MAC / z back on the 64-lane radix-4 kernels (zcol256.cuh) when the z
+// length is 256, there are at most three species and the values are
+// double-float: measured 2.2x / 1.5x faster than the two-factor kernels at
+// 128^3 -> 256^3, whose residency the shared-memory accumulators cap at 6
+// warps per SM.  The FP32 (bound by latency) and FP64 (bound by the FP64
+// pipe) two-factor kernels stay faster.  False otherwise.
+template <typename T>
+static bool launch_z4(bool back, int s, bool msa, typename vec2<T>::type *B10, typename vec2<T>::type *Bs,
+                      const Dims &d, const typename vec2<T>::type *twz, const T *spec, const SpeciesConst &sc,
+                      cudaStream_t st) {
+    if constexpr (!std::is_same<T, dd>::value) {
+        return false;
+    } else {
+        if (d.Lz != kZ4Len || s < 1 || s > kZ4MaxSpecies) return false;
+        constexpr int TX = z4_tx<T>();
+        const dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
+        const int threads = kZ4Lanes * 2 * TX;
+        const size_t sm = z4_smem<T>();
+        auto go = [&](auto sv) {
+            constexpr int S = decltype(sv)::value;
+            if (!back)
+                k_zmac_q4<T, S><<<g, threads, sm, st>>>(Bs, B10, d, twz, spec, sc);
+            else if (msa)
+                k_zback_q4<T, S, true><<<g, threads, sm, st>>>(B10, Bs, d, twz, spec, sc);
+            else
+                k_zback_q4<T, S, false><<<g, threads, sm, st>>>(B10, Bs, d, twz, spec, sc);
+        };
+        if (s == 1) go(std::integral_constant<int, 1>{});
+        else if (s == 2) go(std::integral_constant<int, 2>{});
+        else go(std::integral_constant<int, 3>{});
+        return true;
+    }
+}
+
+// FP32 z MAC / z back with the per-column state in registers
+// (k_zmac_reg / k_zback_reg) for Lz = 256, at most three species and no MSA
+// term; false otherwise
+template <typename T, int N1, int N2>
+static bool launch_zreg(bool back, int s, bool msa, typename vec2<T>::type *B10, typename vec2<T>::type *Bs,
+                        const Dims &d, const typename vec2<T>::type *twz, const T *spec, const SpeciesConst &sc,
+                        cudaStream_t st) {
+    if constexpr (!std::is_same<T, float>::value || N1 != 16 || N2 != 16) {
+        return false;
+    } else {
+        if (s < 1 || s > 3 || msa) return false;
+        constexpr int TX = 4;
+        const dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
+        const int threads = Shape<N1, N2>::G * 2 * TX;
+        const size_t sm = zreg_smem<N1, N2>(d, s, TX);
+        auto go = [&](auto sv) {
+            constexpr int S = decltype(sv)::value;
+            if (!back)
+                k_zmac_reg<N1, N2, S><<<g, threads, sm, st>>>(Bs, B10, d, twz, spec, sc, TX);
+            else
+                k_zback_reg<N1, N2, S><<<g, threads, sm, st>>>(B10, Bs, d, twz, spec, sc, TX);
+        };
+        if (s == 1) go(std::integral_constant<int, 1>{});
+        else if (s == 2) go(std::integral_constant<int, 2>{});
+        else go(std::integral_constant<int, 3>{});
+        return true;
+    }
+}
+
 template <typename T>
 static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, double *d_mu, cudaStream_t st,
                         bool tc = false) {
@@ -819,8 +883,13 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     // z column kernels (MAC forward / back)
     auto zpass = [&](int stage, bool back) {
         tm.begin(stage, st);
+        if (launch_z4<T>(back, s, sc.msa != 0, B10, Bs, d, twz, spec, sc, st)) {
+            tm.end(st);
+            return;
+        }
         if (!with_shape(d.Lz, [&](auto a, auto b) {
                 constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
+                if (launch_zreg<T, N1, N2>(back, s, sc.msa != 0, B10, Bs, d, twz, spec, sc, st)) return;
                 // paired columns (ky, Ly - ky): 2 TX columns per CTA
                 const long per_col = ((long)s * N1 * G + Shape<N1, N2>::EX) * (long)cs;
                 int TX = pow2_le(std::max<long>(1, std::min<long>(std::min<long>(128 / G, 8), kBudget / (2 * per_col))));

@@ -566,3 +566,228 @@ __global__ void __launch_bounds__(256) k_zback_p(const typename vec2<T>::type *_
 }
 
 }  // namespace pnp
+
+namespace pnp {
+
+// ---------------------------------------------------------------------------
+// FP32 z kernels with the per-column spectral state in registers: square
+// two-factor shapes (L = 16, 64, 256), at most three species.  Each lane keeps
+// its S x N1 accumulators (z back) or transformed density values (z MAC) in
+// registers instead of a shared-memory slot per product, the lane twiddles
+// come from a shared table, and each kernel type's spectra for the CTA's
+// columns are staged in shared memory by cp.async while the first column of
+// the type is transformed.  Problems with the MSA term keep k_zback_p (its
+// extra pair loop would spill here).  Measured at 128^3 -> 256^3: z back 0.648 -> 0.549
+// ms, z MAC 0.505 -> 0.487 ms against k_zback_p / k_zmac_p.
+
+__device__ __forceinline__ void cp_async_f32(float *smem, const float *gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// spectra of kernel `type` for species i < S at (fz < Oz, kx0 + c < Ox) of
+// the CTA's fold row fy: specS[(i * Oz + fz) * TX + c]; out-of-range kx is
+// zero-filled
+__device__ __forceinline__ void stage_type_spectra(float *specS, const float *__restrict__ spec, const Dims &d,
+                                                   int S, int type, int fy, int kx0, int TX) {
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    const int n = S * d.Oz * TX;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int c = k % TX, fz = (k / TX) % d.Oz, i = k / (TX * d.Oz);
+        const int kx = kx0 + c;
+        const bool ok = kx < d.Ox;
+        cp_async_f32(specS + k,
+                     spec + (size_t)(i * kNumKernels + type) * oct + ((size_t)fz * d.Oy + fy) * d.Ox + (ok ? kx : 0),
+                     ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+
+// shared memory of a register-state CTA: exchange buffers, staged spectra,
+// twiddle table
+template <int N1, int N2> inline size_t zreg_smem(const Dims &d, int S, int TX) {
+    const size_t ex = (size_t)Shape<N1, N2>::EX * 2 * TX * sizeof(float2);
+    const size_t sp = ((size_t)S * d.Oz * TX * sizeof(float) + 7) / 8 * 8;
+    return ex + sp + (size_t)Shape<N1, N2>::G * Shape<N1, N2>::G * sizeof(float2);
+}
+
+template <int N1, int N2, int S>
+__global__ void __launch_bounds__(128, 2) k_zback_reg(const float2 *__restrict__ B10, float2 *__restrict__ Bs, Dims d,
+                                                      const float2 *__restrict__ tw, const float *__restrict__ spec,
+                                                      SpeciesConst sc, int TX) {
+    using C = float2;
+    using T = float;
+    constexpr int G = Shape<N1, N2>::G;
+    static_assert(N1 == G && N2 == G, "square shapes only");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = threadIdx.x % TX, b = (threadIdx.x / TX) & 1, t = threadIdx.x / (2 * TX);
+    const int lanes = 2 * TX;
+    C *ex = reinterpret_cast<C *>(smem_raw) + (b * TX + c);
+    float *specS = reinterpret_cast<float *>(reinterpret_cast<C *>(smem_raw) + (size_t)Shape<N1, N2>::EX * lanes);
+    C *twtab = reinterpret_cast<C *>(smem_raw) + (size_t)Shape<N1, N2>::EX * lanes +
+               ((size_t)S * d.Oz * TX * sizeof(float) + sizeof(C) - 1) / sizeof(C);
+    const int kyp = blockIdx.y, kx0 = blockIdx.x * TX, kx = kx0 + c;
+    int ky;
+    const bool ok = zcol(d, kyp, b, kx, ky);
+    const int fy = kyp;
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    SmemTw<N1, N2, C>::fill(twtab, tw);
+    __syncthreads();
+    SmemTw<N1, N2, C> lt;
+    lt.tab = twtab;
+    lt.t = t;
+    C v[G];
+    C acc[S][N1];
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) acc[i][k1] = C{0, 0};
+    for (int type = 0; type < kNumKernels; ++type) {
+        const int nin = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        const bool flip_y = type == 3 && ky > d.Ly / 2;
+        for (int o = 0; o < nin; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+            const C *src = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+            }
+            if (o == 0) {
+                __syncthreads();      // every lane is done with the previous type's spectra
+                stage_type_spectra(specS, spec, d, S, type, fy, kx0, TX);
+            }
+            fwd2<N1, N2>(v, lt, ex, t, lanes);
+            if (o == 0) {
+                cp_async_wait_all_groups();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                        : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    const int kz = t + N2 * k1;
+                    const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+                    T g = specS[(i * d.Oz + fz) * TX + c];
+                    if (flip_y || (type == 4 && kz > d.Lz / 2)) g = -g;
+                    const T gg = cf * g;
+                    const C x = v[k1];
+                    if (type <= 1) {
+                        acc[i][k1].x += gg * x.x;
+                        acc[i][k1].y += gg * x.y;
+                    } else {             // K = -i S
+                        acc[i][k1].x += gg * x.y;
+                        acc[i][k1].y -= gg * x.x;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = acc[i][k1];
+        inv2<N1, N2>(v, lt, ex, t, lanes);
+        if (ok) {
+            C *dst = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int zz = t + N1 * n2;
+                if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+            }
+        }
+    }
+}
+
+template <int N1, int N2, int S>
+__global__ void __launch_bounds__(128, 2) k_zmac_reg(const float2 *__restrict__ Bs, float2 *__restrict__ B10, Dims d,
+                                                     const float2 *__restrict__ tw, const float *__restrict__ spec,
+                                                     SpeciesConst sc, int TX) {
+    using C = float2;
+    using T = float;
+    constexpr int G = Shape<N1, N2>::G;
+    static_assert(N1 == G && N2 == G, "square shapes only");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = threadIdx.x % TX, b = (threadIdx.x / TX) & 1, t = threadIdx.x / (2 * TX);
+    const int lanes = 2 * TX;
+    C *ex = reinterpret_cast<C *>(smem_raw) + (b * TX + c);
+    float *specS = reinterpret_cast<float *>(reinterpret_cast<C *>(smem_raw) + (size_t)Shape<N1, N2>::EX * lanes);
+    C *twtab = reinterpret_cast<C *>(smem_raw) + (size_t)Shape<N1, N2>::EX * lanes +
+               ((size_t)S * d.Oz * TX * sizeof(float) + sizeof(C) - 1) / sizeof(C);
+    const int kyp = blockIdx.y, kx0 = blockIdx.x * TX, kx = kx0 + c;
+    int ky;
+    const bool ok = zcol(d, kyp, b, kx, ky);
+    const int fy = kyp;
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    SmemTw<N1, N2, C>::fill(twtab, tw);
+    __syncthreads();
+    SmemTw<N1, N2, C> lt;
+    lt.tab = twtab;
+    lt.t = t;
+    C v[G];
+    C rs[S][N1];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        const C *src = Bs + (size_t)i * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int zz = t + N1 * n2;
+            v[n2] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+        }
+        if (i == 0) stage_type_spectra(specS, spec, d, S, 0, fy, kx0, TX);
+        fwd2<N1, N2>(v, lt, ex, t, lanes);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) rs[i][k1] = v[k1];
+    }
+    // output groups: shell {n0, n1, n2}, ball {n3}, vector x {n1x, n2x}, y, z
+    for (int type = 0; type < kNumKernels; ++type) {
+        if (type > 0) {
+            __syncthreads();          // every lane is done with the previous type's spectra
+            stage_type_spectra(specS, spec, d, S, type, fy, kx0, TX);
+        }
+        cp_async_wait_all_groups();
+        __syncthreads();
+        const int nout = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        const bool flip_y = type == 3 && ky > d.Ly / 2;
+        for (int o = 0; o < nout; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) v[k1] = C{0, 0};
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                        : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    const int kz = t + N2 * k1;
+                    const int fz = kz <= d.Lz / 2 ? kz : d.Lz - kz;
+                    T g = specS[(i * d.Oz + fz) * TX + c];
+                    if (flip_y || (type == 4 && kz > d.Lz / 2)) g = -g;
+                    const T gg = cf * g;
+                    const C x = rs[i][k1];
+                    if (type <= 1) {
+                        v[k1].x += gg * x.x;
+                        v[k1].y += gg * x.y;
+                    } else {             // conj(K) = +i S
+                        v[k1].x -= gg * x.y;
+                        v[k1].y += gg * x.x;
+                    }
+                }
+            }
+            inv2<N1, N2>(v, lt, ex, t, lanes);
+            if (ok) {
+                C *dst = B10 + (size_t)alpha * d.nz * plane + (size_t)ky * d.Wx + kx;
+#pragma unroll
+                for (int n2 = 0; n2 < N2; ++n2) {
+                    const int zz = t + N1 * n2;
+                    if (zz < d.nz) dst[(size_t)zz * plane] = v[n2];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace pnp

@@ -431,6 +431,7 @@ int validate_and_copy(const pnp_problem_desc *d, Problem *p, std::string *why) {
     p->eq_init = eq;
     p->screened = (d->flags & PNP_FLAG_SCREENED_POISSON) != 0;
     p->msa = (d->flags & PNP_FLAG_MSA) != 0;
+    p->phase_timing = (d->flags & PNP_FLAG_PHASE_TIMING) != 0;
     if (d->anderson_depth < 0 || d->anderson_depth > 6) return bad("anderson_depth must be in 0..6");
     if (d->anderson_depth > 0 && d->rho_mix == PNP_MIX_ADAPTIVE)
         return bad("Anderson mixing needs a relaxation without per-point state (not PNP_MIX_ADAPTIVE)");

@@ -90,6 +90,7 @@ struct Problem {
     bool has_wells = false;
     bool msa = false;                 // mu_ex carries the MSA correlation term (Sec 2.3.4)
     int aa_depth = 0;                 // Anderson mixing depth of the Gummel loop (0: relaxed only)
+    bool phase_timing = false;        // the solve graph marks its phase boundaries
 
     // ---- plan ----
     int L[3] = {0, 0, 0};
@@ -166,6 +167,7 @@ int plane_flux(Problem *p, int species, const double *d_phi, const double *d_mu,
 int gummel_launch(Problem *p, const double *d_phi0, const double *d_rho0, cudaStream_t st);
 int gummel_fetch(Problem *p, double *phi, double *rho, void *dev_stats_copy, cudaStream_t st);
 size_t gummel_stats_bytes();
+int gummel_phase_times(Problem *p, double *ms, int max_phases);   // ms per phase of the last solve
 void gummel_decode_stats(const void *raw, pnp_stats *out);
 size_t estimate_device_bytes(const Problem &p);   // problem + Gummel state, from the plan
 

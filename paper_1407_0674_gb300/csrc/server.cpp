@@ -217,14 +217,16 @@ static void worker_main(pnp_server *s) {
     cudaSetDevice(s->device);
     std::vector<Request *> running;
     while (true) {
-        // admit
+        // admit at most one request per pass: starting one (set-up, graph
+        // recording) takes host time, and finished solves are retired between
+        // starts instead of after a whole burst of them
         std::vector<Request *> admit;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             if (running.empty() && s->queue.empty())
                 s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
             if (s->stop) break;
-            while (!s->queue.empty() && (int)(running.size() + admit.size()) < s->opts.max_slots) {
+            while (!s->queue.empty() && admit.empty() && (int)running.size() < s->opts.max_slots) {
                 auto it = s->queue.begin();
                 if (s->opts.policy == PNP_SERVE_SMALLEST_FIRST)
                     it = std::min_element(s->queue.begin(), s->queue.end(), [](const Request *a, const Request *b) {

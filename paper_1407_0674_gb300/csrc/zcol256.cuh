@@ -1,0 +1,363 @@
+// z kernels for padded length Lz = 256 with up to three species and
+// double-float values: 64 lanes per column, four radix-4 stages, per-lane
+// accumulators in registers.
+//
+// The two-factor z kernels (mu_ex_reg.cuh) give a column 16 lanes of 16
+// values and keep the s spectral accumulators of every column in shared
+// memory, which caps residency at 8 (FP32) or 6 (double-float) warps per SM
+// and costs a shared-memory read-modify-write per product.  Here a column has
+// 64 lanes of 4 values: lane t holds x[t + 64 n1]; after the forward
+// transform lane t = 16 k1 + 4 k2 + k3 holds X[k1 + 4 k2 + 16 k3 + 64 k4] in
+// v[k4], and the inverse takes that layout back to natural order, so the
+// spectral products need no reordering and each lane's s x 4 accumulators
+// stay in registers.  Decimation in frequency: with n = n0 + 64 n1 and
+// k = k1 + 4 k',
+//   X[k1 + 4 k'] = sum_n0 W64^(n0 k') [ W256^(n0 k1) sum_n1 x[n0 + 64 n1] W4^(n1 k1) ],
+// and the same split again on the inner 64- and 16-point transforms.  The
+// three exchanges go through two padded shared-memory buffers per column.
+// A CTA takes TX half-spectrum columns at the two rows (kyp, Ly - kyp), which
+// read the same kernel-spectrum octant entries; thread = t * 2 TX + b * TX + c
+// keeps consecutive kx in consecutive threads for coalesced column loads.
+// Included by mu_ex_core.cuh only.
+#pragma once
+
+#include <type_traits>
+
+#include "fft_reg.cuh"
+
+namespace pnp {
+
+constexpr int kZ4Len = 256;
+constexpr int kZ4Lanes = 64;
+constexpr int kZ4Buf = 320;        // 256 values + one pad slot per four
+constexpr int kZ4MaxSpecies = 3;
+
+// padded exchange index: stride-4 accesses land on the minimum number of
+// shared-memory wavefronts
+__device__ __forceinline__ int z4pad(int i) { return i + (i >> 2); }
+
+// lane t's frequency of value k4
+__device__ __forceinline__ int z4_freq(int t, int k4) { return (t >> 4) + 4 * ((t >> 2) & 3) + 16 * (t & 3) + 64 * k4; }
+
+// twiddles of lane t: [0..2] W256^(n0 k), [3..5] W64^(m0 k), [6..8] W16^(p0 k),
+// k = 1..3, n0 = t, m0 = t mod 16, p0 = t mod 4.  Held in registers (FP32) or
+// read from a per-CTA copy of the W256 table in shared memory (64-bit types).
+template <typename C> struct Z4TwReg {
+    C w[9];
+    __device__ __forceinline__ void init(const C *__restrict__ tab, int t) {
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            w[k - 1] = ldgc(&tab[(t * k) & 255]);
+            w[2 + k] = ldgc(&tab[(4 * (t & 15) * k) & 255]);
+            w[5 + k] = ldgc(&tab[(16 * (t & 3) * k) & 255]);
+        }
+    }
+    __device__ __forceinline__ C operator[](int j) const { return w[j]; }
+};
+template <typename C> struct Z4TwSmem {
+    const C *tab;
+    int e[3];
+    __device__ __forceinline__ void init(const C *stab, int t) {
+        tab = stab;
+        e[0] = t;
+        e[1] = 4 * (t & 15);
+        e[2] = 16 * (t & 3);
+    }
+    __device__ __forceinline__ C operator[](int j) const { return tab[(e[j / 3] * (j % 3 + 1)) & 255]; }
+};
+
+// forward 256-point DFT (see the header comment for the layouts).  A, B: the
+// column's exchange buffers, element i at [z4pad(i) * xs].  Starts with a
+// barrier before its first write (the buffers may still be read by the
+// previous transform); every thread of the block must call it.
+template <typename C, typename TW>
+__device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs) {
+    rdft4<false>(v);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[k - 1]);
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) A[z4pad(k1 * 64 + t) * xs] = v[k1];
+    __syncthreads();
+    {
+        const int k1 = t >> 4, m0 = t & 15;
+#pragma unroll
+        for (int m1 = 0; m1 < 4; ++m1) v[m1] = A[z4pad(k1 * 64 + m0 + 16 * m1) * xs];
+        rdft4<false>(v);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[2 + k]);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) B[z4pad(k1 * 64 + k2 * 16 + m0) * xs] = v[k2];
+    }
+    __syncthreads();
+    {
+        const int k1 = t >> 4, k2 = (t >> 2) & 3, p0 = t & 3;
+#pragma unroll
+        for (int p1 = 0; p1 < 4; ++p1) v[p1] = B[z4pad(k1 * 64 + k2 * 16 + p0 + 4 * p1) * xs];
+        rdft4<false>(v);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[5 + k]);
+#pragma unroll
+        for (int k3 = 0; k3 < 4; ++k3) A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs] = v[k3];
+    }
+    __syncthreads();
+    {
+        const int k1 = t >> 4, k2 = (t >> 2) & 3, k3 = t & 3;
+#pragma unroll
+        for (int p0 = 0; p0 < 4; ++p0) v[p0] = A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs];
+        rdft4<false>(v);
+    }
+}
+
+// inverse (unnormalised) of z4_fwd: the same stages backwards with conjugate
+// twiddles
+template <typename C, typename TW>
+__device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs) {
+    {
+        const int k1 = t >> 4, k2 = (t >> 2) & 3, k3 = t & 3;
+        rdft4<true>(v);
+        __syncthreads();
+#pragma unroll
+        for (int p0 = 0; p0 < 4; ++p0) A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs] = v[p0];
+    }
+    __syncthreads();
+    {
+        const int k1 = t >> 4, k2 = (t >> 2) & 3, p0 = t & 3;
+#pragma unroll
+        for (int k3 = 0; k3 < 4; ++k3) v[k3] = A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[5 + k]));
+        rdft4<true>(v);
+#pragma unroll
+        for (int p1 = 0; p1 < 4; ++p1) B[z4pad(k1 * 64 + k2 * 16 + p0 + 4 * p1) * xs] = v[p1];
+    }
+    __syncthreads();
+    {
+        const int k1 = t >> 4, m0 = t & 15;
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k2] = B[z4pad(k1 * 64 + k2 * 16 + m0) * xs];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[2 + k]));
+        rdft4<true>(v);
+#pragma unroll
+        for (int m1 = 0; m1 < 4; ++m1) A[z4pad(k1 * 64 + m0 + 16 * m1) * xs] = v[m1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) v[k1] = A[z4pad(k1 * 64 + t) * xs];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[k - 1]));
+    rdft4<true>(v);
+}
+
+// columns per CTA side: FP32 4 (512 threads), 64-bit types 2 (256 threads)
+template <typename T> constexpr int z4_tx() { return std::is_same<T, float>::value ? 4 : 2; }
+
+// dynamic shared memory of a z4 CTA: two exchange buffers per column and the
+// twiddle table
+template <typename T> constexpr size_t z4_smem() {
+    return (2 * (size_t)kZ4Buf * 2 * z4_tx<T>() + kZ4Len) * sizeof(typename vec2<T>::type);
+}
+
+// per-lane set-up shared by both kernels
+template <typename T> struct Z4Lane {
+    using C = typename vec2<T>::type;
+    using TW = typename std::conditional<std::is_same<T, float>::value, Z4TwReg<C>, Z4TwSmem<C>>::type;
+    int c, b, t, lanes, kx, ky, fy;
+    bool ok;
+    C *bufA, *bufB;
+    TW tw;
+    int fz[4];
+    bool hi[4];
+    __device__ __forceinline__ void init(const Dims &d, const C *__restrict__ twz, unsigned char *smem) {
+        constexpr int TX = z4_tx<T>();
+        lanes = 2 * TX;
+        c = threadIdx.x % TX;
+        b = (threadIdx.x / TX) & 1;
+        t = threadIdx.x / lanes;
+        const int kyp = blockIdx.y;
+        kx = blockIdx.x * TX + c;
+        ok = zcol(d, kyp, b, kx, ky);
+        fy = kyp;        // both rows of the pair fold to kyp
+        C *base = reinterpret_cast<C *>(smem);
+        bufA = base + (b * TX + c);
+        bufB = bufA + (size_t)kZ4Buf * lanes;
+        C *tab = base + (size_t)2 * kZ4Buf * lanes;
+        if constexpr (std::is_same<T, float>::value) {
+            tw.init(twz, t);
+        } else {
+            for (int k = threadIdx.x; k < kZ4Len; k += blockDim.x) tab[k] = ldgc(&twz[k]);
+            __syncthreads();
+            tw.init(tab, t);
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+            const int kz = z4_freq(t, k4);
+            fz[k4] = kz <= kZ4Len / 2 ? kz : kZ4Len - kz;
+            hi[k4] = kz > kZ4Len / 2;
+        }
+    }
+    // x[t + 64 n1] of a column whose rows z < nz start at src (stride plane)
+    __device__ __forceinline__ void load(C (&v)[4], const C *src, const Dims &d, size_t plane) const {
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) {
+            const int zz = t + 64 * n1;
+            v[n1] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
+        }
+    }
+    __device__ __forceinline__ void store(const C (&v)[4], C *dst, const Dims &d, size_t plane) const {
+        if (!ok) return;
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) {
+            const int zz = t + 64 * n1;
+            if (zz < d.nz) dst[(size_t)zz * plane] = v[n1];
+        }
+    }
+};
+
+// z MAC, L = 256: forward FFT of the S density columns (kept per lane in
+// registers), the ten weighted-density spectra conj(K_alpha,i) rho_i summed
+// over species, inverse FFT, rows z < nz.  grid (ceil(Wx/TX), Ly/2 + 1),
+// block 128 TX.
+template <typename T, int S>
+__global__ void __launch_bounds__(512, 1) k_zmac_q4(const typename vec2<T>::type *__restrict__ Bs,
+                                                    typename vec2<T>::type *__restrict__ B10, Dims d,
+                                                    const typename vec2<T>::type *__restrict__ twz,
+                                                    const T *__restrict__ spec, SpeciesConst sc) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Z4Lane<T> ln;
+    ln.init(d, twz, smem_raw);
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    C rs[S][4];
+    C v[4];
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        ln.load(v, Bs + (size_t)i * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+        z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rs[i][k] = v[k];
+    }
+    // output groups: shell {n0, n1, n2}, ball {n3}, vector x {n1x, n2x}, y, z
+    for (int type = 0; type < kNumKernels; ++type) {
+        const int nout = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        const bool flip_y = type == 3 && ln.ky > d.Ly / 2;
+        T g[S][4];
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+            const T *base = spec + (size_t)(i * kNumKernels + type) * oct + (size_t)ln.fy * d.Ox + ln.kx;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+                T gv = ln.ok ? ldgt(&base[(size_t)ln.fz[k4] * d.Oy * d.Ox]) : (T)0;
+                if (flip_y || (type == 4 && ln.hi[k4])) gv = -gv;
+                g[i][k4] = gv;
+            }
+        }
+        for (int o = 0; o < nout; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = C{0, 0};
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                        : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const T gg = cf * g[i][k4];
+                    const C x = rs[i][k4];
+                    if (type <= 1) {
+                        v[k4].x += gg * x.x;
+                        v[k4].y += gg * x.y;
+                    } else {             // conj(K) = +i S
+                        v[k4].x -= gg * x.y;
+                        v[k4].y += gg * x.x;
+                    }
+                }
+            }
+            z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+            ln.store(v, B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+        }
+    }
+}
+
+// z back, L = 256: forward FFT of each Psi_alpha column, mu_i += K_alpha,i
+// Psi_alpha into per-lane register accumulators, with MSA the pair kernels on
+// the densities' y-spectra still in Bs (written over only at the end), then
+// the inverse FFT of the S accumulators, rows z < nz.
+template <typename T, int S, bool MSA>
+__global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::type *__restrict__ B10,
+                                                     typename vec2<T>::type *__restrict__ Bs, Dims d,
+                                                     const typename vec2<T>::type *__restrict__ twz,
+                                                     const T *__restrict__ spec, SpeciesConst sc) {
+    using C = typename vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Z4Lane<T> ln;
+    ln.init(d, twz, smem_raw);
+    const size_t plane = (size_t)d.Ly * d.Wx;
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    C acc[S][4];
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[i][k] = C{0, 0};
+    C v[4];
+    for (int type = 0; type < kNumKernels; ++type) {
+        const int nin = type == 0 ? 3 : (type == 1 ? 1 : 2);
+        const bool flip_y = type == 3 && ln.ky > d.Ly / 2;
+        for (int o = 0; o < nin; ++o) {
+            const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
+            ln.load(v, B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T cf = alpha == 0 ? sc_c0<T>(sc, i)
+                                        : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
+                const T *base = spec + (size_t)(i * kNumKernels + type) * oct + (size_t)ln.fy * d.Ox + ln.kx;
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    T g = ln.ok ? ldgt(&base[(size_t)ln.fz[k4] * d.Oy * d.Ox]) : (T)0;
+                    if (flip_y || (type == 4 && ln.hi[k4])) g = -g;
+                    const T gg = cf * g;
+                    const C x = v[k4];
+                    if (type <= 1) {
+                        acc[i][k4].x += gg * x.x;
+                        acc[i][k4].y += gg * x.y;
+                    } else {             // K = -i S
+                        acc[i][k4].x += gg * x.y;
+                        acc[i][k4].y -= gg * x.x;
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (MSA) {
+        // MSA correlations (Sec 2.3.4): mu_i -= sum_j C_ij rho_j, the stored
+        // even spectra being -C_ij
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            ln.load(v, Bs + (size_t)j * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const T *base = spec + (size_t)(S * kNumKernels + msa_pair(i, j, S)) * oct + (size_t)ln.fy * d.Ox +
+                                ln.kx;
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const T gg = ln.ok ? ldgt(&base[(size_t)ln.fz[k4] * d.Oy * d.Ox]) : (T)0;
+                    acc[i][k4].x += gg * v[k4].x;
+                    acc[i][k4].y += gg * v[k4].y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = acc[i][k];
+        z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+        ln.store(v, Bs + (size_t)i * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+    }
+}
+
+}  // namespace pnp

@@ -39,6 +39,8 @@ FLAG_AUTOTUNE = 1
 FLAG_EQUILIBRIUM_INIT = 2
 FLAG_SCREENED_POISSON = 4
 FLAG_MSA = 8
+FLAG_PHASE_TIMING = 16
+PHASES = ("mu_ex", "poisson", "nernst_planck", "update")
 SERVE = {"fifo": 0, "smallest_first": 1}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2, "tf32split": 3, None: -1, -1: -1, 0: 0, 1: 1, 2: 2, 3: 3}
 
@@ -134,6 +136,7 @@ def lib():
         L.pnp_excess_mu_noalloc.argtypes = [ctypes.POINTER(Desc), vp, vp, vp]
         L.pnp_selftest_bounded_wait.argtypes = [ctypes.c_double]
         L.pnp_test_fail_alloc_at.argtypes = [ctypes.c_long]
+        L.pnp_gummel_phase_times.argtypes = [vp, _dp, ctypes.c_int]
         L.pnp_plane_flux.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
         L.pnp_plan_problem.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(Info), _dp]
         L.pnp_conductivity.argtypes = [ctypes.POINTER(Desc), _dp, ctypes.c_double, _dp]
@@ -222,7 +225,8 @@ class DescHolder:
         d.flags = (FLAG_AUTOTUNE if getattr(spec, "autotune", False) else 0) | \
             (FLAG_EQUILIBRIUM_INIT if getattr(spec, "eq_init", False) else 0) | \
             (FLAG_SCREENED_POISSON if getattr(spec, "screened_poisson", False) else 0) | \
-            (FLAG_MSA if getattr(spec, "msa", False) else 0)
+            (FLAG_MSA if getattr(spec, "msa", False) else 0) | \
+            (FLAG_PHASE_TIMING if getattr(spec, "phase_timing", False) else 0)
         d.eq_tol = float(getattr(spec, "eq_tol", 0.0))
         d.eq_max_iter = int(getattr(spec, "eq_max_iter", 0))
         d.fmt = int(getattr(spec, "fmt", 0))
@@ -371,6 +375,15 @@ class Problem:
         out = np.empty(self.shape[0] + 1)
         _check(lib().pnp_plane_flux(self.h, int(species), _ptr(p), _ptr(r), _ptr(out)), "pnp_plane_flux")
         return out
+
+    def gummel_phase_times(self):
+        """pnp_gummel_phase_times: ms per phase of the last solve (needs
+        spec.phase_timing)."""
+        out = np.zeros(len(PHASES))
+        n = lib().pnp_gummel_phase_times(self.h, _ptr(out), len(PHASES))
+        if n < 0:
+            raise PnpError(n, "pnp_gummel_phase_times")
+        return dict(zip(PHASES, out.tolist()))
 
     def square_well_energy(self, rho):
         """pnp_square_well_energy: F_sh (kT) of the densities rho [s][nz][ny][nx]."""

@@ -373,3 +373,26 @@ def test_anderson_refuses_adaptive_relaxation(pnp):
     with pytest.raises(pnp.PnpError) as e:
         pnp.Problem(spec)
     assert e.value.code == pnp.ERR_INVALID
+
+
+def test_phase_timing_marks_do_not_change_results(pnp):
+    """PNP_FLAG_PHASE_TIMING: every phase of the iteration gets device time,
+    the phases sum to no more than the solve's wall time, and the results are
+    the same bits as without the marks."""
+    import time
+    spec = film_gummel(16, 16, 16, tol=1e-30, max_iter=8)
+    with pnp.Problem(spec) as P:
+        phi0, rho0, st0 = P.gummel_solve(raise_on_error=False)
+    spec.phase_timing = True
+    with pnp.Problem(spec) as P:
+        P.gummel_solve(raise_on_error=False)            # graph build outside the timing
+        t0 = time.perf_counter()
+        phi, rho, st = P.gummel_solve(raise_on_error=False)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        ph = P.gummel_phase_times()
+    assert set(ph) == {"mu_ex", "poisson", "nernst_planck", "update"}
+    assert all(v > 0 for v in ph.values()), ph
+    assert sum(ph.values()) <= wall_ms, (ph, wall_ms)
+    assert st["iterations"] == st0["iterations"] == 8
+    np.testing.assert_array_equal(phi, phi0)
+    np.testing.assert_array_equal(rho, rho0)

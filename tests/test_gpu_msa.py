@@ -87,6 +87,25 @@ def test_mu_ex_with_msa_matches_oracle(pnp, case):
             assert np.abs(term[i]).max() <= 1e-12 * np.abs(mu[i]).max()
 
 
+@pytest.mark.parametrize("s", [2, 3])
+def test_msa_z_length_256(pnp, s):
+    """Lz = 256: the radix-4 z-back kernels apply the term in double-float,
+    the two-factor ones in FP64 and FP32."""
+    spec, rho = four_species(("N", "P", "D"), (9, 8, 30))
+    keep = slice(0, s)
+    spec = dataclasses.replace(spec, R=spec.R[keep], q=spec.q[keep], rho_b=spec.rho_b[keep], fft_len=(32, 8, 256))
+    rho = np.ascontiguousarray(rho[keep])
+    ref, _ = oracle.excess_mu(spec, rho)
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (32, 8, 256)
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+
+
 def test_msa_generic_z_length(pnp):
     """Lz = 30 has no register FFT: the shared-memory Stockham z-back kernel
     applies the term."""

@@ -319,3 +319,26 @@ def test_uniform_periodic_bulk_equals_closed_form(pnp):
         mu = P.excess_mu(rho)
     py = -np.log(1 - eta) + eta * (14 - 13 * eta + 5 * eta ** 2) / (2 * (1 - eta) ** 3)
     np.testing.assert_allclose(mu, py, rtol=1e-12)
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_z_length_256_radix4_kernels(pnp, s):
+    """Lz = 256 with at most three species runs the 64-lane radix-4 z kernels
+    in double-float, the register-state two-factor ones in FP32 and the
+    shared-memory-accumulator ones in FP64: all against the oracle, with
+    ragged x/y and nz below the half length."""
+    R = (1.5, 2.0, 3.0)[:s]
+    rb = tuple(bulk_density(0.1, r) for r in R)
+    spec = ProblemSpec(nx=11, ny=9, nz=37, bc=("N", "P", "D"), R=R, q=(1, -1, 0)[:s], rho_b=rb,
+                       fft_len=(32, 9, 256))
+    rho = lognormal_density(spec, 21 + s, sigma=0.2)
+    ref, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (32, 9, 256)
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL

@@ -66,6 +66,7 @@ class ProblemSpec:
     fmt: int = 0                             # hard-sphere functional: 0 Rosenfeld, 1 White Bear (MFMT)
     msa: bool = False                        # add the MSA electrostatic-correlation term (Sec 2.3.4)
     anderson: int = 0                        # Anderson mixing depth of the Gummel iteration (0 = relaxed only)
+    phase_timing: bool = False               # the solve graph sums device time per phase of each iteration
 
     @property
     def s(self) -> int:
