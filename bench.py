@@ -649,6 +649,9 @@ def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", lo
     errs = [max(float(np.abs(done[k][1][i] - seq_res[k][0][i]).max() / np.abs(seq_res[k][0][i]).max())
                 for i in range(specs[k].s)) for k in both]
     lat = [v[3] for v in done.values()]
+    # time from submission to the start of the solve (admission and problem
+    # creation) = latency - the solve's own seconds
+    adm = [v[3] - v[2]["seconds"] for v in done.values()]
     grids = sorted({(s.nx, s.ny, s.nz) for s in specs})
     return {
         "workload": f"{len(specs)} independent Gummel solves of the batch recipe (seed 4): grids "
@@ -661,6 +664,8 @@ def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", lo
         "sequential_solver": "the recipe's relaxation (per-point adaptive, 0.05), plain FP64 mu_ex",
         "served": {"solves": len(specs), "solves_per_s": len(specs) / wall, "wall_s": wall,
                    "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+                   "admission_mean_s": float(np.mean(adm)), "admission_max_s": float(np.max(adm)),
+                   "solve_mean_s": float(np.mean([v[2]["seconds"] for v in done.values()])),
                    "converged": sum(1 for v in done.values() if v[0] == 0),
                    "status": [done[k][0] for k in range(len(specs))],
                    "iterations": [done[k][2]["iterations"] for k in range(len(specs))]},

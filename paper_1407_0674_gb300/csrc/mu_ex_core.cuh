@@ -761,10 +761,13 @@ static bool launch_z4(bool back, int s, bool msa, typename vec2<T>::type *B10, t
             constexpr int S = decltype(sv)::value;
             if (!back)
                 k_zmac_q4<T, S><<<g, threads, sm, st>>>(Bs, B10, d, twz, spec, sc);
-            else if (msa)
-                k_zback_q4<T, S, true><<<g, threads, sm, st>>>(B10, Bs, d, twz, spec, sc);
-            else
-                k_zback_q4<T, S, false><<<g, threads, sm, st>>>(B10, Bs, d, twz, spec, sc);
+            else if (msa) {
+                ensure_smem<k_zback_q4<T, S, true>>();
+                k_zback_q4<T, S, true><<<g, threads, z4_smem_back<T>(), st>>>(B10, Bs, d, twz, spec, sc);
+            } else {
+                ensure_smem<k_zback_q4<T, S, false>>();
+                k_zback_q4<T, S, false><<<g, threads, z4_smem_back<T>(), st>>>(B10, Bs, d, twz, spec, sc);
+            }
         };
         if (s == 1) go(std::integral_constant<int, 1>{});
         else if (s == 2) go(std::integral_constant<int, 2>{});

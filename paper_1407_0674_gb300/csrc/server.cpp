@@ -1,12 +1,13 @@
 // Serving loop: a queue of independent Gummel solves running concurrently on
 // one GPU (pnp_server_* in include/pnp.h).
 //
-// A worker thread owns the device work.  It admits queued requests (in arrival
-// order, or smallest first with PNP_SERVE_SMALLEST_FIRST) while a slot is free and the request's device footprint (estimated
-// from its plan before anything is allocated) fits the memory budget, builds
-// the problem, and launches its whole solve -- one CUDA graph whose loops end
-// on the device -- on the problem's own stream, followed by copies of the
-// result into pinned host memory and an event.  Solves therefore overlap on
+// A worker thread admits queued requests (in arrival order, or smallest first
+// with PNP_SERVE_SMALLEST_FIRST) while a slot is free and the request's device footprint (estimated
+// from its plan before anything is allocated) fits the memory budget; a
+// preparer thread per admitted request builds the problem and launches its
+// whole solve -- one CUDA graph whose loops end on the device -- on the
+// problem's own stream, followed by copies of the result into pinned host
+// memory and an event.  Solves therefore overlap on
 // the GPU; requests that arrive while others run are admitted as soon as a
 // slot and memory free up.  Completion is detected with cudaEventQuery (the
 // worker never blocks on one solve); finished results wait in host memory
@@ -98,7 +99,9 @@ struct pnp_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     std::deque<pnp::Request *> queue;
-    std::vector<pnp::Request *> active;
+    std::vector<pnp::Request *> running;   // launched, not yet retired (worker and preparers, under mu)
+    int preparing = 0;                     // admitted requests whose problem is being built
+    std::condition_variable prepared;      // signalled when a preparer ends
     std::map<uint64_t, pnp::Request *> all;
     size_t bytes_in_use = 0;
     long long submitted = 0, completed = 0, failed = 0, rejected = 0;
@@ -213,20 +216,34 @@ static void finish(pnp_server *s, Request *r, int status) {
     else s->failed++;
 }
 
+// Build an admitted request's problem and launch its solve on a thread of its
+// own: problem creation (validation, spectra, set-up kernels, graph
+// recording) is host-heavy and waits for its own set-up work on a busy GPU,
+// so several run side by side while the worker keeps retiring solves.
+static void prepare(pnp_server *s, Request *r) {
+    cudaSetDevice(s->device);
+    r->t_start = std::chrono::steady_clock::now();
+    const int rc = start(s, r);
+    if (rc) finish(s, r, rc);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!rc) s->running.push_back(r);
+    s->preparing--;
+    s->prepared.notify_all();
+}
+
 static void worker_main(pnp_server *s) {
     cudaSetDevice(s->device);
-    std::vector<Request *> running;
     while (true) {
-        // admit at most one request per pass: starting one (set-up, graph
-        // recording) takes host time, and finished solves are retired between
-        // starts instead of after a whole burst of them
-        std::vector<Request *> admit;
+        // admit while a slot is free and the budget allows; each admitted
+        // request is prepared on its own thread
+        std::vector<Request *> done;
+        bool idle = false;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (running.empty() && s->queue.empty())
+            if (s->running.empty() && s->queue.empty() && s->preparing == 0)
                 s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
             if (s->stop) break;
-            while (!s->queue.empty() && admit.empty() && (int)running.size() < s->opts.max_slots) {
+            while (!s->queue.empty() && (int)s->running.size() + s->preparing < s->opts.max_slots) {
                 auto it = s->queue.begin();
                 if (s->opts.policy == PNP_SERVE_SMALLEST_FIRST)
                     it = std::min_element(s->queue.begin(), s->queue.end(), [](const Request *a, const Request *b) {
@@ -237,33 +254,36 @@ static void worker_main(pnp_server *s) {
                 if (s->bytes_in_use + r->bytes > s->opts.hbm_budget_bytes) break;
                 s->queue.erase(it);
                 s->bytes_in_use += r->bytes;
-                admit.push_back(r);
+                s->preparing++;
+                std::thread(prepare, s, r).detach();
             }
-        }
-        for (Request *r : admit) {
-            r->t_start = std::chrono::steady_clock::now();
-            int rc = start(s, r);
-            if (rc) finish(s, r, rc);
-            else running.push_back(r);
-        }
-        // retire finished solves without blocking on any one of them
-        bool any = false;
-        for (size_t k = 0; k < running.size();) {
-            Request *r = running[k];
-            cudaError_t q = cudaEventQuery(r->done_ev);
-            if (q == cudaErrorNotReady) {
-                ++k;
-                continue;
+            // retire finished solves without blocking on any one of them
+            for (size_t k = 0; k < s->running.size();) {
+                Request *r = s->running[k];
+                if (cudaEventQuery(r->done_ev) == cudaErrorNotReady) {
+                    ++k;
+                    continue;
+                }
+                done.push_back(r);
+                s->running[k] = s->running.back();
+                s->running.pop_back();
             }
-            any = true;
+            idle = done.empty();
+        }
+        for (Request *r : done) {
+            const cudaError_t q = cudaEventQuery(r->done_ev);
             finish(s, r, q == cudaSuccess ? PNP_PENDING : PNP_ERR_CUDA);
-            running[k] = running.back();
-            running.pop_back();
         }
-        if (!any && admit.empty() && !running.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
+        if (idle) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
-    // drain: wait for what is on the device, then drop it
-    for (Request *r : running) {
+    // drain: wait for the preparers, then for what is on the device, and drop it
+    std::vector<Request *> left;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->prepared.wait(lk, [&] { return s->preparing == 0; });
+        left.swap(s->running);
+    }
+    for (Request *r : left) {
         if (r->done_ev) cudaEventSynchronize(r->done_ev);
         finish(s, r, PNP_ERR_CUDA);
     }
@@ -373,7 +393,7 @@ int pnp_server_get_stats(pnp_server *s, pnp_server_stats *out) {
     out->failed = s->failed;
     out->rejected = s->rejected;
     out->queued = (int)s->queue.size();
-    out->active = (int)(s->submitted - s->completed - s->failed - (long long)s->queue.size());
+    out->active = (int)s->running.size() + s->preparing;
     out->bytes_in_use = s->bytes_in_use;
     return PNP_OK;
 }

@@ -154,9 +154,20 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
 template <typename T> constexpr int z4_tx() { return std::is_same<T, float>::value ? 4 : 2; }
 
 // dynamic shared memory of a z4 CTA: two exchange buffers per column and the
-// twiddle table
+// twiddle table; the z back adds two prefetch stages of four values per lane
 template <typename T> constexpr size_t z4_smem() {
     return (2 * (size_t)kZ4Buf * 2 * z4_tx<T>() + kZ4Len) * sizeof(typename vec2<T>::type);
+}
+template <typename T> constexpr size_t z4_stage_elems() { return (size_t)2 * 4 * kZ4Lanes * 2 * z4_tx<T>(); }
+template <typename T> constexpr size_t z4_smem_back() {
+    return z4_smem<T>() + z4_stage_elems<T>() * sizeof(typename vec2<T>::type);
+}
+
+// 16-byte asynchronous copy global -> shared (zero-fill when !valid; src must
+// still be a valid address)
+__device__ __forceinline__ void z4_cp16(void *smem, const void *gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0));
 }
 
 // per-lane set-up shared by both kernels
@@ -204,6 +215,22 @@ template <typename T> struct Z4Lane {
             const int zz = t + 64 * n1;
             v[n1] = (ok && zz < d.nz) ? src[(size_t)zz * plane] : C{0, 0};
         }
+    }
+    // asynchronous copy of this lane's four values of a column into its own
+    // slots of a prefetch stage (read back by the same lane: no barrier)
+    __device__ __forceinline__ void prefetch(C *stage, const C *src, const Dims &d, size_t plane) const {
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) {
+            const int zz = t + 64 * n1;
+            const bool in = ok && zz < d.nz;
+            z4_cp16(stage + ((size_t)n1 * kZ4Lanes + t) * lanes + (b * z4_tx<T>() + c), in ? src + (size_t)zz * plane : src,
+                    in);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    __device__ __forceinline__ void take(C (&v)[4], const C *stage) const {
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) v[n1] = stage[((size_t)n1 * kZ4Lanes + t) * lanes + (b * z4_tx<T>() + c)];
     }
     __device__ __forceinline__ void store(const C (&v)[4], C *dst, const Dims &d, size_t plane) const {
         if (!ok) return;
@@ -302,12 +329,27 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[i][k] = C{0, 0};
     C v[4];
+    // the ten Psi columns in the order (type, o) below; each lane prefetches
+    // its values of the next column into its own slots of the other stage
+    C *stage = reinterpret_cast<C *>(smem_raw) + z4_smem<T>() / sizeof(C);
+    const size_t stage_stride = (size_t)4 * kZ4Lanes * ln.lanes;
+    auto column = [&](int alpha) { return B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx; };
+    ln.prefetch(stage, column(0), d, plane);
+    int seq = 0;
     for (int type = 0; type < kNumKernels; ++type) {
         const int nin = type == 0 ? 3 : (type == 1 ? 1 : 2);
         const bool flip_y = type == 3 && ln.ky > d.Ly / 2;
-        for (int o = 0; o < nin; ++o) {
+        for (int o = 0; o < nin; ++o, ++seq) {
             const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
-            ln.load(v, B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
+            if (seq + 1 < kNumWeighted) {
+                const int t1 = o + 1 < nin ? type : type + 1, o1 = o + 1 < nin ? o + 1 : 0;
+                const int a1 = t1 == 0 ? o1 : (t1 == 1 ? 3 : (o1 == 0 ? 4 + t1 - 2 : 7 + t1 - 2));
+                ln.prefetch(stage + ((seq + 1) & 1) * stage_stride, column(a1), d, plane);
+                asm volatile("cp.async.wait_group 1;\n" ::);
+            } else {
+                asm volatile("cp.async.wait_group 0;\n" ::);
+            }
+            ln.take(v, stage + (seq & 1) * stage_stride);
             z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
 #pragma unroll
             for (int i = 0; i < S; ++i) {
