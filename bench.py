@@ -64,11 +64,14 @@ def parse():
                     help="mu_ex precision of the batched / served solves (the sequential baseline is plain FP64)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="autotune the batched / served problems' plans (timing candidates on a loaded GPU)")
-    ap.add_argument("--solve-aa", type=int, default=3,
+    ap.add_argument("--solve-aa", type=int, default=0,
                     help="Anderson depth of the batched / served solves (0: the recipe's relaxation; > 0 with the "
                          "step-limited geometric relaxation); the sequential FP64 baseline keeps the recipe's")
+    ap.add_argument("--film-aa", type=int, default=3,
+                    help="film workload: Anderson depth of the solve reported beside the plain one (0: none)")
     ap.add_argument("--policy", default="smallest_first", choices=["fifo", "smallest_first"],
                     help="admission policy of the batched / served solves")
+    ap.add_argument("--slots", type=int, default=4, help="concurrently resident batched / served solves")
     ap.add_argument("--variants", default="df64,fp32,tf32split,fp64", help="precisions to time, headline first")
     ap.add_argument("--solves", type=int, default=16,
                     help="mu_ex workload: solves of the batch recipe served concurrently, against the same solves "
@@ -534,7 +537,7 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and args.solves > 0:
         from workloads import batch_specs
         line["solves"] = batch_record(batch_specs(args.solves), args.solve_prec, args.autotune, args.solves,
-                                      aa=args.solve_aa, policy=args.policy)
+                                      aa=args.solve_aa, policy=args.policy, slots=args.slots)
     barrier(world)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -605,7 +608,7 @@ def served_variant(spec, autotune, aa):
     return s
 
 
-def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", log=sys.stderr):
+def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", slots=64, log=sys.stderr):
     """Independent Gummel solves of the batch recipe served concurrently
     (mu_ex in `solve_prec`, FP64 Gummel update and linear solves, Anderson
     depth `aa`, admission `policy`) against the first `seq_count` of the same
@@ -624,7 +627,7 @@ def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", lo
             seq_res[k] = (rho, st)
         print(f"sequential fp64 {k} ({s.nx}x{s.ny}x{s.nz}): status {st['status']} it {st['iterations']} "
               f"{seq[-1]:.1f} s", file=log, flush=True)
-    srv = pnp.Server(max_slots=64, policy=policy)
+    srv = pnp.Server(max_slots=slots, policy=policy)
     t0 = time.perf_counter()
     tickets = []
     for s in served:
@@ -660,7 +663,7 @@ def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", lo
                       "concurrently (one CUDA graph per solve) vs one at a time in plain FP64",
         "mu_ex_precision": solve_prec,
         "served_solver": (f"Anderson depth {aa} on the step-limited geometric relaxation (0.05)" if aa > 0 else
-                          "the recipe's relaxation") + f", policy {policy}",
+                          "the recipe's relaxation") + f", policy {policy}, {slots} slots",
         "sequential_solver": "the recipe's relaxation (per-point adaptive, 0.05), plain FP64 mu_ex",
         "served": {"solves": len(specs), "solves_per_s": len(specs) / wall, "wall_s": wall,
                    "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
@@ -668,7 +671,8 @@ def batch_record(specs, solve_prec, autotune, seq_count, aa=0, policy="fifo", lo
                    "solve_mean_s": float(np.mean([v[2]["seconds"] for v in done.values()])),
                    "converged": sum(1 for v in done.values() if v[0] == 0),
                    "status": [done[k][0] for k in range(len(specs))],
-                   "iterations": [done[k][2]["iterations"] for k in range(len(specs))]},
+                   "iterations": [done[k][2]["iterations"] for k in range(len(specs))],
+                   "repeated_sweeps": [done[k][2].get("repeated_sweeps", 0) for k in range(len(specs))]},
         "sequential_fp64": {"solves": len(seq), "solves_per_s": len(seq) / sum(seq) if seq else None,
                             "wall_s": sum(seq), "converged": sum(1 for k in seq_res if seq_res[k][1]["status"] == 0),
                             "iterations": [seq_res[k][1]["iterations"] for k in seq_res]},
@@ -710,15 +714,15 @@ def run_solves(args, world, rank, local):
             _, _, stp = P.gummel_solve()
             ph = P.gummel_phase_times()
         line["phases_ms_per_iteration"] = {k: v / max(stp["iterations"], 1) for k, v in ph.items()}
-        if args.solve_aa > 0:
+        if args.film_aa > 0:
             # the same solve with Anderson mixing (same fixed point)
-            sa = dataclasses.replace(spec, anderson=args.solve_aa)
+            sa = dataclasses.replace(spec, anderson=args.film_aa)
             with pnp.Problem(sa) as P:
                 P.gummel_solve()
                 t0 = time.perf_counter()
                 _, rho_a, sta = P.gummel_solve()
                 dta = time.perf_counter() - t0
-            line["anderson"] = {"depth": args.solve_aa, "solves_per_s": world / dta, "ms_per_solve": dta * 1e3,
+            line["anderson"] = {"depth": args.film_aa, "solves_per_s": world / dta, "ms_per_solve": dta * 1e3,
                                 "iterations": sta["iterations"],
                                 "max_rel_err_rho_vs_plain": max(float(np.abs(rho_a[i] - rho[i]).max() /
                                                                       np.abs(rho[i]).max()) for i in range(2))}
@@ -784,7 +788,7 @@ def run_solves(args, world, rank, local):
         return
     if args.workload == "batch":
         rec = batch_record(batch_specs(args.batch), args.solve_prec, args.autotune, args.seq, aa=args.solve_aa,
-                           policy=args.policy)
+                           policy=args.policy, slots=args.slots)
         line = {"metric": "PNP solves/s", "value": world * rec["served"]["solves_per_s"], "unit": "solves/s",
                 "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": rec["served"]["wall_s"] * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -807,7 +811,7 @@ def run_solves(args, world, rank, local):
             seq.append(time.perf_counter() - t0)
         print(f"serve sequential n {s.nx}: status {st['status']} it {st['iterations']} {seq[-1]:.1f} s",
               file=sys.stderr, flush=True)
-    srv = pnp.Server(max_slots=64, policy=args.policy)
+    srv = pnp.Server(max_slots=args.slots, policy=args.policy)
     t0 = time.perf_counter()
     pending = {}
     lat = []

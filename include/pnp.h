@@ -194,6 +194,8 @@ typedef struct {
     double seconds;                /* wall time of the call */
     int init_iterations;           /* iterations of the equilibrium initial guess (0 if not run) */
     double init_residual;          /* its last residual */
+    int repeated_sweeps;           /* anderson_depth > 0: sweeps repeated from a restored or halved state after
+                                      an unphysical one (not counted in iterations) */
 } pnp_stats;
 
 typedef struct {

@@ -19,7 +19,8 @@
  *   White Bear (MFMT) derivatives, series near n3 = 0                     Sec 2.3.1
  *   equilibrium cDFT initial guess (Poisson-Boltzmann Newton steps)       Sec 3.2.1
  *   screened Poisson step, per-point adaptive relaxation (options)        Sec 3.2
- *   Anderson-accelerated Gummel iteration (an extension)                  Sec 3.2
+ *   Anderson-accelerated Gummel iteration with restart and step halving   Sec 3.2
+ *     after an unphysical sweep (an extension)
  *   plane currents through the z faces                                    Sec 2.1, 3.1
  *   MSA electrostatic-correlation term (integral part)                    Sec 2.3.4
  *

@@ -60,6 +60,7 @@ struct DevStats {
     int eq_enable;         // run the equilibrium stage (set before each launch)
     int eq_iters;          // its iterations
     double eq_residual;    // its last residual
+    int redos;             // Anderson: sweeps repeated after an unphysical one
 };
 
 // control block of the Anderson mixing (see the kernels further down)
@@ -767,6 +768,7 @@ __global__ void k_gummel_check(const unsigned long long *dmax, const int *flag, 
     const double res = __longlong_as_double((long long)bits);
     if (aa && aa->redo) {
         // the sweep is repeated from the restored plain iterate: same iteration
+        st->redos += 1;
         cudaGraphSetConditional(h, 1u);
         return;
     }
@@ -822,6 +824,7 @@ __global__ void k_stats_reset(DevStats *st, int eq_enable) {
     st->eq_enable = eq_enable;
     st->eq_iters = 0;
     st->eq_residual = 0;
+    st->redos = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1592,6 +1595,7 @@ void gummel_decode_stats(const void *raw, pnp_stats *out) {
     out->status = hs->status;
     out->init_iterations = hs->eq_iters;
     out->init_residual = hs->eq_residual;
+    out->repeated_sweeps = hs->redos;
 }
 
 int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d_phi, double *d_rho, pnp_stats *stats,
@@ -1613,6 +1617,7 @@ int gummel_run(Problem *p, const double *d_phi0, const double *d_rho0, double *d
         stats->status = local.status;
         stats->init_iterations = local.init_iterations;
         stats->init_residual = local.init_residual;
+        stats->repeated_sweeps = local.repeated_sweeps;
     }
     return local.status;
 }

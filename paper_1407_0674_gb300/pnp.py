@@ -81,7 +81,8 @@ class Desc(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("residual", ctypes.c_double),
                 ("linear_iterations", ctypes.c_longlong), ("seconds", ctypes.c_double),
-                ("init_iterations", ctypes.c_int), ("init_residual", ctypes.c_double)]
+                ("init_iterations", ctypes.c_int), ("init_residual", ctypes.c_double),
+                ("repeated_sweeps", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -409,7 +410,8 @@ class Problem:
         rc = lib().pnp_gummel_solve(self.h, _ptr(p0), _ptr(r0), _ptr(phi), _ptr(rho), ctypes.byref(st))
         stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
                  "linear_iterations": st.linear_iterations, "seconds": st.seconds,
-                 "init_iterations": st.init_iterations, "init_residual": st.init_residual}
+                 "init_iterations": st.init_iterations, "init_residual": st.init_residual,
+                 "repeated_sweeps": st.repeated_sweeps}
         if raise_on_error and rc not in (OK,):
             raise PnpError(rc, "pnp_gummel_solve")
         return phi, rho, stats
@@ -459,7 +461,8 @@ class Server:
         self._shapes.pop(ticket, None)
         stats = {"status": st.status, "iterations": st.iterations, "residual": st.residual,
                  "linear_iterations": st.linear_iterations, "seconds": st.seconds,
-                 "init_iterations": st.init_iterations, "init_residual": st.init_residual}
+                 "init_iterations": st.init_iterations, "init_residual": st.init_residual,
+                 "repeated_sweeps": st.repeated_sweeps}
         return rc, phi, rho, stats
 
     def stats(self):

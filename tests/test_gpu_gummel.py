@@ -337,6 +337,7 @@ def test_anderson_full_size_film_same_state_fewer_iterations(pnp):
     spec = film_gummel(32, 32, 32, tol=1e-11, max_iter=4000)
     with pnp.Problem(spec) as P:
         phi0, rho0, st0 = P.gummel_solve()
+    assert st0["repeated_sweeps"] == 0
     spec.anderson = 3
     with pnp.Problem(spec) as P:
         phi, rho, st = P.gummel_solve()
@@ -362,6 +363,7 @@ def test_anderson_backtracking_matches_oracle(pnp):
     with pnp.Problem(spec) as P:
         phi, rho, st = P.gummel_solve()
     assert st["status"] == 0 and st["iterations"] <= 300
+    assert st["repeated_sweeps"] > 0          # the restart / step halving ran
     assert rel(phi, ref["phi"], 1.0) <= 1e-6
     for i in range(spec.s):
         assert rel(rho[i], ref["rho"][i]) <= 1e-6
