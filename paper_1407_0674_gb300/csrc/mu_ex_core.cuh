@@ -756,12 +756,12 @@ static bool launch_z4(bool back, int s, bool msa, typename vec2<T>::type *B10, t
         constexpr int TX = z4_tx<T>();
         const dim3 g((d.Wx + TX - 1) / TX, d.Ly / 2 + 1);
         const int threads = kZ4Lanes * 2 * TX;
-        const size_t sm = z4_smem<T>();
         auto go = [&](auto sv) {
             constexpr int S = decltype(sv)::value;
-            if (!back)
-                k_zmac_q4<T, S><<<g, threads, sm, st>>>(Bs, B10, d, twz, spec, sc);
-            else if (msa) {
+            if (!back) {
+                ensure_smem<k_zmac_q4<T, S>>();
+                k_zmac_q4<T, S><<<g, threads, z4_smem_mac<T>(), st>>>(Bs, B10, d, twz, spec, sc);
+            } else if (msa) {
                 ensure_smem<k_zback_q4<T, S, true>>();
                 k_zback_q4<T, S, true><<<g, threads, z4_smem_back<T>(), st>>>(B10, Bs, d, twz, spec, sc);
             } else {

@@ -38,10 +38,17 @@ __device__ __forceinline__ C pack_two(const C *__restrict__ x0, const C *__restr
     return C{X.x - Y.y, X.y + Y.x};
 }
 
+// resident 256-thread CTAs the x kernels are compiled for: two for
+// double-float (at most 128 registers: 16 warps per SM instead of 8; the DF64
+// x stages at 256 points take 1.32 -> 1.08 ms), none (the compiler's own
+// choice) otherwise -- a minimum of one lets it raise the FP32 x inverse from
+// 78 to 88 registers, two CTAs per SM instead of three
+template <typename T> constexpr int xlines_min_blocks() { return std::is_same<T, dd>::value ? 2 : 0; }
+
 // ---------------------------------------------------------------------------
 // x forward (R2C, two real lines per complex FFT).  block P*G, grid (ceil(npairs/P), nz, F)
 template <typename T, int N1, int N2, typename InT = double>
-__global__ void __launch_bounds__(256) k_xfwd_r(const InT *__restrict__ in, size_t in_fstride,
+__global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xfwd_r(const InT *__restrict__ in, size_t in_fstride,
                                                  typename vec2<T>::type *__restrict__ A, Dims d,
                                                  const typename vec2<T>::type *__restrict__ tw, int P) {
     using C = typename vec2<T>::type;
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(256) k_xfwd_r(const InT *__restrict__ in, size
 
 // x inverse (C2R) of F fields, write x < nx as FP64, optionally + coef * U
 template <typename T, int N1, int N2>
-__global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__restrict__ A,
+__global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_r(const typename vec2<T>::type *__restrict__ A,
                                                  double *__restrict__ out, size_t out_fstride, Dims d,
                                                  const typename vec2<T>::type *__restrict__ tw,
                                                  const double *__restrict__ U, SpeciesConst sc, int P,
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(256) k_xinv_r(const typename vec2<T>::type *__
 // x inverse (C2R) of F fields into real arrays of type OutT (x < nx), for the
 // split form of the derivative stage
 template <typename T, int N1, int N2, typename OutT>
-__global__ void __launch_bounds__(256) k_xinv_raw_r(const typename vec2<T>::type *__restrict__ A,
+__global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_raw_r(const typename vec2<T>::type *__restrict__ A,
                                                      OutT *__restrict__ out, Dims d,
                                                      const typename vec2<T>::type *__restrict__ tw, int P) {
     using C = typename vec2<T>::type;

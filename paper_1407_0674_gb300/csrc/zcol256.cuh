@@ -155,12 +155,15 @@ template <typename T> constexpr int z4_tx() { return std::is_same<T, float>::val
 
 // dynamic shared memory of a z4 CTA: two exchange buffers per column and the
 // twiddle table; the z back adds two prefetch stages of four values per lane
+// and two kernel-spectrum stages of S x 4 values per lane and column pair
 template <typename T> constexpr size_t z4_smem() {
     return (2 * (size_t)kZ4Buf * 2 * z4_tx<T>() + kZ4Len) * sizeof(typename vec2<T>::type);
 }
 template <typename T> constexpr size_t z4_stage_elems() { return (size_t)2 * 4 * kZ4Lanes * 2 * z4_tx<T>(); }
+template <typename T> constexpr size_t z4_spec_elems() { return (size_t)2 * kZ4MaxSpecies * 4 * kZ4Lanes * z4_tx<T>(); }
+template <typename T> constexpr size_t z4_smem_mac() { return z4_smem<T>() + z4_spec_elems<T>() * sizeof(T); }
 template <typename T> constexpr size_t z4_smem_back() {
-    return z4_smem<T>() + z4_stage_elems<T>() * sizeof(typename vec2<T>::type);
+    return z4_smem<T>() + z4_stage_elems<T>() * sizeof(typename vec2<T>::type) + z4_spec_elems<T>() * sizeof(T);
 }
 
 // 16-byte asynchronous copy global -> shared (zero-fill when !valid; src must
@@ -168,6 +171,15 @@ template <typename T> constexpr size_t z4_smem_back() {
 __device__ __forceinline__ void z4_cp16(void *smem, const void *gmem, bool valid) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 16 : 0));
+}
+
+// asynchronous copy of one 4- or 8-byte value global -> shared (zero-fill
+// when !valid; src must still be a valid address)
+template <typename T> __device__ __forceinline__ void z4_cp_scalar(T *smem, const T *gmem, bool valid) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"((int)sizeof(T)),
+                 "r"(valid ? (int)sizeof(T) : 0));
 }
 
 // per-lane set-up shared by both kernels
@@ -242,6 +254,36 @@ template <typename T> struct Z4Lane {
     }
 };
 
+// Kernel-spectrum stage: K_type,i at lane t's four frequencies for column c
+// at [((i * 4 + k4) * 64 + t) * TX + c] of buffer type & 1.  The pair's two
+// rows read the same entries (either row's column exists iff kx < Wx); row b
+// copies k4 = 2b, 2b + 1, one commit group per type.  A reader waits for the
+// group and passes a barrier before its first read.
+template <typename T, int S> constexpr size_t z4_spec_stride() { return (size_t)S * 4 * kZ4Lanes * z4_tx<T>(); }
+template <typename T, int S>
+__device__ __forceinline__ void z4_fetch_spec(T *gst, const T *__restrict__ spec, const Z4Lane<T> &ln, const Dims &d,
+                                              int type) {
+    constexpr int TX = z4_tx<T>();
+    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
+    const bool ok = ln.kx < d.Wx;
+    T *dst = gst + (type & 1) * z4_spec_stride<T, S>();
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        const T *base = spec + (size_t)(i * kNumKernels + type) * oct + (size_t)ln.fy * d.Ox + ln.kx;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const int k4 = 2 * ln.b + kk;
+            z4_cp_scalar(&dst[((size_t)(i * 4 + k4) * kZ4Lanes + ln.t) * TX + ln.c],
+                         ok ? &base[(size_t)ln.fz[k4] * d.Oy * d.Ox] : spec, ok);
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+}
+template <typename T, int S>
+__device__ __forceinline__ T z4_spec_at(const T *gst, const Z4Lane<T> &ln, int type, int i, int k4) {
+    return gst[(type & 1) * z4_spec_stride<T, S>() + ((size_t)(i * 4 + k4) * kZ4Lanes + ln.t) * z4_tx<T>() + ln.c];
+}
+
 // z MAC, L = 256: forward FFT of the S density columns (kept per lane in
 // registers), the ten weighted-density spectra conj(K_alpha,i) rho_i summed
 // over species, inverse FFT, rows z < nz.  grid (ceil(Wx/TX), Ly/2 + 1),
@@ -256,9 +298,14 @@ __global__ void __launch_bounds__(512, 1) k_zmac_q4(const typename vec2<T>::type
     Z4Lane<T> ln;
     ln.init(d, twz, smem_raw);
     const size_t plane = (size_t)d.Ly * d.Wx;
-    const size_t oct = (size_t)d.Ox * d.Oy * d.Oz;
     C rs[S][4];
     C v[4];
+    // kernel spectra staged one type ahead: type t + 1 is copied at the start
+    // of type t (the inverse transforms of type t - 1 put barriers after every
+    // thread's last read of that buffer) and published by a barrier at the
+    // start of type t + 1
+    T *gst = reinterpret_cast<T *>(smem_raw + z4_smem<T>());
+    z4_fetch_spec<T, S>(gst, spec, ln, d, 0);
 #pragma unroll
     for (int i = 0; i < S; ++i) {
         ln.load(v, Bs + (size_t)i * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
@@ -270,13 +317,19 @@ __global__ void __launch_bounds__(512, 1) k_zmac_q4(const typename vec2<T>::type
     for (int type = 0; type < kNumKernels; ++type) {
         const int nout = type == 0 ? 3 : (type == 1 ? 1 : 2);
         const bool flip_y = type == 3 && ln.ky > d.Ly / 2;
+        if (type + 1 < kNumKernels) {
+            z4_fetch_spec<T, S>(gst, spec, ln, d, type + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
         T g[S][4];
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-            const T *base = spec + (size_t)(i * kNumKernels + type) * oct + (size_t)ln.fy * d.Ox + ln.kx;
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
-                T gv = ln.ok ? ldgt(&base[(size_t)ln.fz[k4] * d.Oy * d.Ox]) : (T)0;
+                T gv = z4_spec_at<T, S>(gst, ln, type, i, k4);
                 if (flip_y || (type == 4 && ln.hi[k4])) gv = -gv;
                 g[i][k4] = gv;
             }
@@ -334,11 +387,22 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
     C *stage = reinterpret_cast<C *>(smem_raw) + z4_smem<T>() / sizeof(C);
     const size_t stage_stride = (size_t)4 * kZ4Lanes * ln.lanes;
     auto column = [&](int alpha) { return B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx; };
+    // kernel spectra staged one type ahead: type t + 1 is copied after the
+    // first forward transform of type t (whose barriers follow every
+    // thread's last read of that buffer, type t - 1), completes with the next
+    // column's wait and is published by the barriers of the next transform
+    T *gst = reinterpret_cast<T *>(stage + 2 * stage_stride);
     ln.prefetch(stage, column(0), d, plane);
+    z4_fetch_spec<T, S>(gst, spec, ln, d, 0);
     int seq = 0;
+    // the column loop stays rolled: unrolled, its ten forward transforms
+    // and products outgrow the instruction cache (ncu: 1.6 no-instruction
+    // stalls per issue; 2.05 -> 1.83 ms at 128^3 -> 256^3 rolled)
+#pragma unroll 1
     for (int type = 0; type < kNumKernels; ++type) {
         const int nin = type == 0 ? 3 : (type == 1 ? 1 : 2);
         const bool flip_y = type == 3 && ln.ky > d.Ly / 2;
+#pragma unroll 1
         for (int o = 0; o < nin; ++o, ++seq) {
             const int alpha = type == 0 ? o : (type == 1 ? 3 : (o == 0 ? 4 + type - 2 : 7 + type - 2));
             if (seq + 1 < kNumWeighted) {
@@ -351,14 +415,14 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
             }
             ln.take(v, stage + (seq & 1) * stage_stride);
             z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+            if (o == 0 && type + 1 < kNumKernels) z4_fetch_spec<T, S>(gst, spec, ln, d, type + 1);
 #pragma unroll
             for (int i = 0; i < S; ++i) {
                 const T cf = alpha == 0 ? sc_c0<T>(sc, i)
                                         : ((alpha == 1 || (alpha >= 4 && alpha < 7)) ? sc_c1<T>(sc, i) : (T)1);
-                const T *base = spec + (size_t)(i * kNumKernels + type) * oct + (size_t)ln.fy * d.Ox + ln.kx;
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
-                    T g = ln.ok ? ldgt(&base[(size_t)ln.fz[k4] * d.Oy * d.Ox]) : (T)0;
+                    T g = z4_spec_at<T, S>(gst, ln, type, i, k4);
                     if (flip_y || (type == 4 && ln.hi[k4])) g = -g;
                     const T gg = cf * g;
                     const C x = v[k4];
