@@ -270,19 +270,20 @@ def stage_flops(name, dims, s):
 PROFILED_TRAFFIC = {
     ("fp64", "z_back"): 1.1299e9,     # k_zback_p_fp64_120_pad256.md
     ("fp32", "z_back"): None,
-    # k_zq4_dd_120_pad256.md: 1037.7 / 1072.3 MB at 120^3, x (algorithmic
+    # k_zq4_dd_120_pad256.md: 1054.9 / 1083.1 MB at 120^3, x (algorithmic
     # bytes at 128^3 / at 120^3) = 1137 / 1082 MB
-    ("df64", "z_mac"): 1.0904e9,
-    ("df64", "z_back"): 1.1250e9,     # 1070.6 MB at 120^3 (the prefetching kernel) x 1137 / 1082
+    ("df64", "z_mac"): 1.1085e9,
+    ("df64", "z_back"): 1.1382e9,
 }
 # FP32-pipe instructions (thread-level FADD + FMUL + FFMA) one launch of a
 # double-float kernel executes, from ncu's per-opcode counts (profiles/): the
 # work its number format costs the FP32 pipes.  A z kernel transforms every
-# one of the Ly x Wx columns over the full length Lz whatever nz is, so the
-# 120^3 capture holds for 128^3 as it is.  None for a kernel changed since.
+# one of the Ly x Wx columns over the full length Lz, with the same pruned
+# butterflies for any nz <= Lz / 2, so the 120^3 capture holds for 128^3 as
+# it is.  None for a kernel changed since.
 PROFILED_FP32_INST = {
-    ("df64", "z_mac"): 4.3043e10,      # k_zq4_dd_120_pad256.md
-    ("df64", "z_back"): 4.3222e10,
+    ("df64", "z_mac"): 4.1615e10,      # k_zq4_dd_120_pad256.md
+    ("df64", "z_back"): 4.1128e10,
 }
 
 DTYPE = {"fp64": "f64",

@@ -36,6 +36,25 @@ constexpr int kZ4MaxSpecies = 3;
 // shared-memory wavefronts
 __device__ __forceinline__ int z4pad(int i) { return i + (i >> 2); }
 
+// Columns of at most 128 rows (the zero-extended half of Lz = 256): a lane's
+// input values n1 = 2, 3 are zero padding and only its output rows t and
+// t + 64 are stored, so the first forward and the last inverse radix-4
+// butterflies shrink.  Both give the values rdft4 gives (adding an exact zero
+// changes nothing).
+template <bool INV, typename C> __device__ __forceinline__ void rdft4_in2(C (&v)[4]) {
+    const C a = v[0], b = v[1], rb = rot<INV>(b);
+    v[0] = cadd(a, b);
+    v[2] = csub(a, b);
+    v[1] = cadd(a, rb);
+    v[3] = csub(a, rb);
+}
+template <bool INV, typename C> __device__ __forceinline__ void rdft4_out2(C (&v)[4]) {
+    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const C t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
+}
+
 // lane t's frequency of value k4
 __device__ __forceinline__ int z4_freq(int t, int k4) { return (t >> 4) + 4 * ((t >> 2) & 3) + 16 * (t & 3) + 64 * k4; }
 
@@ -67,12 +86,16 @@ template <typename C> struct Z4TwSmem {
 };
 
 // forward 256-point DFT (see the header comment for the layouts).  A, B: the
-// column's exchange buffers, element i at [z4pad(i) * xs].  Starts with a
-// barrier before its first write (the buffers may still be read by the
-// previous transform); every thread of the block must call it.
+// column's exchange buffers, element i at [z4pad(i) * xs]; half: inputs
+// x[t + 128], x[t + 192] are zero.  Starts with a barrier before its first
+// write (the buffers may still be read by the previous transform); every
+// thread of the block must call it.
 template <typename C, typename TW>
-__device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs) {
-    rdft4<false>(v);
+__device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs, bool half) {
+    if (half)
+        rdft4_in2<false>(v);
+    else
+        rdft4<false>(v);
 #pragma unroll
     for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[k - 1]);
     __syncthreads();
@@ -110,9 +133,9 @@ __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int 
 }
 
 // inverse (unnormalised) of z4_fwd: the same stages backwards with conjugate
-// twiddles
+// twiddles; half: only rows t and t + 64 (v[0], v[1]) are produced
 template <typename C, typename TW>
-__device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs) {
+__device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs, bool half) {
     {
         const int k1 = t >> 4, k2 = (t >> 2) & 3, k3 = t & 3;
         rdft4<true>(v);
@@ -147,7 +170,10 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
     for (int k1 = 0; k1 < 4; ++k1) v[k1] = A[z4pad(k1 * 64 + t) * xs];
 #pragma unroll
     for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[k - 1]));
-    rdft4<true>(v);
+    if (half)
+        rdft4_out2<true>(v);
+    else
+        rdft4<true>(v);
 }
 
 // columns per CTA side: FP32 4 (512 threads), 64-bit types 2 (256 threads)
@@ -192,8 +218,10 @@ template <typename T> struct Z4Lane {
     TW tw;
     int fz[4];
     bool hi[4];
+    bool half;         // nz <= 128: rows >= 128 are zero padding
     __device__ __forceinline__ void init(const Dims &d, const C *__restrict__ twz, unsigned char *smem) {
         constexpr int TX = z4_tx<T>();
+        half = d.nz <= kZ4Len / 2;
         lanes = 2 * TX;
         c = threadIdx.x % TX;
         b = (threadIdx.x / TX) & 1;
@@ -309,7 +337,7 @@ __global__ void __launch_bounds__(512, 1) k_zmac_q4(const typename vec2<T>::type
 #pragma unroll
     for (int i = 0; i < S; ++i) {
         ln.load(v, Bs + (size_t)i * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
-        z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+        z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes, ln.half);
 #pragma unroll
         for (int k = 0; k < 4; ++k) rs[i][k] = v[k];
     }
@@ -355,7 +383,7 @@ __global__ void __launch_bounds__(512, 1) k_zmac_q4(const typename vec2<T>::type
                     }
                 }
             }
-            z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+            z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes, ln.half);
             ln.store(v, B10 + (size_t)alpha * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
         }
     }
@@ -414,7 +442,7 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
                 asm volatile("cp.async.wait_group 0;\n" ::);
             }
             ln.take(v, stage + (seq & 1) * stage_stride);
-            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes, ln.half);
             if (o == 0 && type + 1 < kNumKernels) z4_fetch_spec<T, S>(gst, spec, ln, d, type + 1);
 #pragma unroll
             for (int i = 0; i < S; ++i) {
@@ -443,7 +471,7 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             ln.load(v, Bs + (size_t)j * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
-            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+            z4_fwd(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes, ln.half);
 #pragma unroll
             for (int i = 0; i < S; ++i) {
                 const T *base = spec + (size_t)(S * kNumKernels + msa_pair(i, j, S)) * oct + (size_t)ln.fy * d.Ox +
@@ -461,7 +489,7 @@ __global__ void __launch_bounds__(512, 1) k_zback_q4(const typename vec2<T>::typ
     for (int i = 0; i < S; ++i) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = acc[i][k];
-        z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes);
+        z4_inv(v, ln.tw, ln.bufA, ln.bufB, ln.t, ln.lanes, ln.half);
         ln.store(v, Bs + (size_t)i * d.nz * plane + (size_t)ln.ky * d.Wx + ln.kx, d, plane);
     }
 }

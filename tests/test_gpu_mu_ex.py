@@ -342,3 +342,23 @@ def test_z_length_256_radix4_kernels(pnp, s):
     assert normwise(mu, ref) <= FP64_TOL
     assert normwise(mudd, ref) <= FP64_TOL
     assert normwise(mu32, ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("nz,bc", [(150, "D"), (256, "P")])
+def test_z_length_256_full_columns(pnp, nz, bc):
+    """Lz = 256 with columns longer than half the padded length (a
+    zero-extended axis of 150 rows, a periodic one of 256): the radix-4 z
+    kernels take their full first forward and last inverse butterflies
+    instead of the ones pruned for zero padding."""
+    R = (1.5, 2.0, 3.0)
+    rb = tuple(bulk_density(0.1, r) for r in R)
+    spec = ProblemSpec(nx=11, ny=9, nz=nz, bc=("N", "P", bc), R=R, q=(1, -1, 0), rho_b=rb, fft_len=(32, 9, 256))
+    rho = lognormal_density(spec, 40, sigma=0.2)
+    ref, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == (32, 9, 256)
+        mudd = P.excess_mu(rho, precision="df64")
+        mu = P.excess_mu(rho, precision="fp64")
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu, ref) <= FP64_TOL
