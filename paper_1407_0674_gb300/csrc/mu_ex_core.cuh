@@ -243,6 +243,56 @@ static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int 
     if (bad) atomicOr(flag, kFlagPacking);
 }
 
+// The same derivatives for double-float fields: the functions singular at
+// packing, 1/(1 - n3) and ln(1 - n3) (and the White Bear phi3), in FP64;
+// every product with the other weighted densities in double-float on the
+// FP32 pipes, whose error (about 2^-47 of each term) stays far inside the
+// FFT's.  Internal linkage: one copy per translation unit.
+static __global__ void k_dphi_fields_dd(dd *__restrict__ f, size_t N, int *__restrict__ flag, int fmt) {
+    const dd k8pi(1.0 / (8.0 * M_PI)), k12pi(1.0 / (12.0 * M_PI)), k4pi(1.0 / (4.0 * M_PI)), three(3);
+    bool bad = false;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+        dd n[kNumWeighted], psi[kNumWeighted];
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) n[a] = f[a * N + p];
+        const double n3 = (double)n[3];
+        const double gd = 1.0 / (1.0 - n3);
+        const dd g(gd), g2 = g * g;
+        // coefficient functions of n2^2 (psi2, vector psi) and n2^3 (psi3)
+        dd c2, c3, cv;
+        if (fmt == PNP_FMT_WHITE_BEAR) {
+            double fw = 0.0, dfw = 0.0;
+            if (n3 < 1.0) wb_phi3(n3, fw, dfw);
+            c2 = dd(fw * (1.0 / (12.0 * M_PI)));
+            c3 = dd(dfw * (1.0 / (36.0 * M_PI)));
+            cv = dd(fw * (1.0 / (6.0 * M_PI)));
+        } else {
+            c2 = g2 * k8pi;
+            c3 = g2 * g * k12pi;
+            cv = g2 * k4pi;
+        }
+        const dd n0 = n[0], n1 = n[1], n2 = n[2];
+        const dd v1v2 = n[4] * n[7] + n[5] * n[8] + n[6] * n[9];
+        const dd v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
+        psi[0] = dd(-log1p(-n3));
+        psi[1] = n2 * g;
+        psi[2] = n1 * g + (n2 * n2 - v2v2) * c2;
+        psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - three * n2 * v2v2) * c3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            psi[4 + c] = -(n[7 + c] * g);
+            psi[7 + c] = -(n[4 + c] * g) - n2 * n[7 + c] * cv;
+        }
+        bool ok = n3 < 1.0;
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a].hi) && isfinite(psi[a].lo);
+        if (!ok) bad = true;
+#pragma unroll
+        for (int a = 0; a < kNumWeighted; ++a) f[a * N + p] = psi[a];
+    }
+    if (bad) atomicOr(flag, kFlagPacking);
+}
+
 }  // namespace pnp
 
 #include "mu_ex_reg.cuh"
@@ -927,10 +977,12 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
     ypass(3, true, B10, A, kNumWeighted);
 
     // 5: x inverse -> dPhi/dn -> forward.  Split form (real n fields through
-    // the idle y-spectra buffer, a pointwise FP64 kernel at full occupancy) or
-    // one fused kernel; both use the register FFT where the length allows.
+    // the idle y-spectra buffer, a pointwise kernel at full occupancy) or one
+    // fused kernel; both use the register FFT where the length allows.  The
+    // real fields keep the FFT's number format (double-float as FP32 pairs:
+    // no FP64 conversions in the x kernels).
     tm.begin(4, st);
-    using V = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+    using V = typename std::conditional<std::is_same<T, double>::value, double, T>::type;
     V *nf = reinterpret_cast<V *>(B10);     // [10][nz][ny][nx], B10 is free here
     if (!with_shape(d.Lx, [&](auto a, auto b) {
             constexpr int N1 = decltype(a)::value, N2 = decltype(b)::value, G = Shape<N1, N2>::G;
@@ -942,6 +994,9 @@ static int run_pipeline(Problem *p, DeviceBuffers *db, const double *d_rho, doub
                 k_xinv_raw_r<T, N1, N2, V><<<g, P * G, sm, st>>>(A, nf, d, twx, P);
                 if constexpr (std::is_same<V, float>::value)
                     k_dphi_fields_mixed<<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(
+                        nf, N, p->d_flag, p->fmt);
+                else if constexpr (std::is_same<V, dd>::value)
+                    k_dphi_fields_dd<<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(
                         nf, N, p->d_flag, p->fmt);
                 else
                     k_dphi_fields<V><<<std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, st>>>(nf, N, p->d_flag,

@@ -279,15 +279,17 @@ def test_full_size_sampled(pnp):
     assert np.abs(mudd - mu).max() / np.abs(mu).max() <= FP64_TOL
 
 
-def test_packing_error_reported(pnp):
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32", "tf32split"])
+def test_packing_error_reported(pnp, precision):
+    """Every precision's derivative kernel flags a packing violation."""
     spec, rho = mu_microbench(12)
     rho = rho * 12.0     # total packing 3.6 > 1
     with pnp.Problem(spec) as P:
         with pytest.raises(pnp.PnpError) as e:
-            P.excess_mu(rho)
+            P.excess_mu(rho, precision=precision)
         assert e.value.code == pnp.ERR_PACKING
         # the problem stays usable
-        P.excess_mu(mu_microbench(12)[1])
+        P.excess_mu(mu_microbench(12)[1], precision=precision)
 
 
 def test_invalid_density_rejected(pnp):
