@@ -58,6 +58,29 @@ __device__ __forceinline__ dd operator*(dd a, dd b) {
     return dd_fast_two_sum(p, e);
 }
 
+// Packed (re, im) sums: the IEEE operations of operator+ applied to the real
+// and the imaginary part side by side, two FP32 values per instruction (the
+// packed FP32x2 arithmetic of compute capability 10.x), so the results are
+// bitwise those of the scalar code.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+__device__ __forceinline__ dd2 dd2_add(dd2 a, dd2 b) {
+    const float2 ah = make_float2(a.x.hi, a.y.hi), bh = make_float2(b.x.hi, b.y.hi);
+    const float2 al = make_float2(a.x.lo, a.y.lo), bl = make_float2(b.x.lo, b.y.lo);
+    // two-sum of the high parts
+    const float2 s = f2_add(ah, bh);
+    const float2 bb = f2_sub(s, ah);
+    const float2 e = f2_add(f2_sub(ah, f2_sub(s, bb)), f2_sub(bh, bb));
+    // the low parts, then the fast two-sum
+    const float2 t = f2_add(e, f2_add(al, bl));
+    const float2 r = f2_add(s, t);
+    const float2 l = f2_sub(t, f2_sub(r, s));
+    return dd2{dd(r.x, l.x), dd(r.y, l.y)};
+}
+__device__ __forceinline__ dd2 dd2_sub(dd2 a, dd2 b) { return dd2_add(a, dd2{-b.x, -b.y}); }
+
+
 __device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
 __device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
 __device__ __forceinline__ dd &operator*=(dd &a, dd b) { return a = a * b; }

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_xfused_r(typename vec2<T>::type *__rest
 // y pass over TX half-spectrum columns; block TX*G with lane-major thread
 // index (t * TX + c) so global accesses are contiguous over c.
 template <typename T, bool INV, int N1, int N2>
-__global__ void __launch_bounds__(256) k_ypass_r(const typename vec2<T>::type *__restrict__ in,
+__global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_ypass_r(const typename vec2<T>::type *__restrict__ in,
                                                   typename vec2<T>::type *__restrict__ out, Dims d, int rows_in,
                                                   int n_in, int rows_out, int n_out,
                                                   const typename vec2<T>::type *__restrict__ tw, int TX) {
