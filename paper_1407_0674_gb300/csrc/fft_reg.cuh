@@ -115,14 +115,36 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft6(C *v) {
     }
 }
 
-// 16 = 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1
-template <bool INV, typename C> __device__ __forceinline__ void rdft16(C *v) {
+// radix-4 butterflies for zero padding: inputs 2 and 3 zero, or only
+// outputs 0 and 1 wanted; the values rdft4 gives there (adding an exact zero
+// changes nothing)
+template <bool INV, typename C> __device__ __forceinline__ void rdft4_in2(C *v) {
+    const C a = v[0], b = v[1], rb = rot<INV>(b);
+    v[0] = cadd(a, b);
+    v[2] = csub(a, b);
+    v[1] = cadd(a, rb);
+    v[3] = csub(a, rb);
+}
+template <bool INV, typename C> __device__ __forceinline__ void rdft4_out2(C *v) {
+    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const C t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
+}
+
+// 16 = 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1.  IN8: inputs 8..15 are zero
+// (n2 >= 2); OUT8: only outputs 0..7 are wanted (k1 < 2; the others are left
+// undefined).
+template <bool INV, typename C, bool IN8 = false, bool OUT8 = false> __device__ __forceinline__ void rdft16(C *v) {
     C a[4][4];
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) {
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) a[n1][n2] = v[n1 + 4 * n2];
-        rdft4<INV>(a[n1]);
+        if constexpr (IN8)
+            rdft4_in2<INV>(a[n1]);
+        else
+            rdft4<INV>(a[n1]);
     }
     const double sg = INV ? 1.0 : -1.0;
     // W16^(n1 k2): exponents 1, 2, 3 (n1 = 1), 2, 4, 6 (n1 = 2), 3, 6, 9 (n1 = 3)
@@ -138,9 +160,15 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft16(C *v) {
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
         C b[4] = {a[0][k2], a[1][k2], a[2][k2], a[3][k2]};
-        rdft4<INV>(b);
+        if constexpr (OUT8) {
+            rdft4_out2<INV>(b);
+            v[k2] = b[0];
+            v[k2 + 4] = b[1];
+        } else {
+            rdft4<INV>(b);
 #pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = b[k1];
+            for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = b[k1];
+        }
     }
 }
 
@@ -191,13 +219,25 @@ template <int N1, int N2, typename C> struct SmemTw {
 
 // forward: lane t < N1 gives x[t + N1 n2] in v[n2] (n2 < N2); on return lane
 // t < N2 holds X[t + N2 k1] in v[k1] (k1 < N1).  ex = this line's exchange
-// buffer, element a at ex[a * xs] (xs = number of interleaved lines).
-// Contains two __syncthreads (every thread of the block must call).
+// buffer, element a at ex[a * xs] (xs = number of interleaved lines).  half:
+// x[j] = 0 for j >= L / 2 (a zero-extended line of at most L / 2 points),
+// which prunes the first radix-16 stage (FP32 and FP64; double-float keeps
+// the full stage: the second copy of it costs spills at its 128-register
+// budget, 0.46 -> 0.49 ms for ten fields).  Contains two __syncthreads (every
+// thread of the block must call).
 template <int N1, int N2, typename C, typename TW>
-__device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs) {
+__device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs,
+                                     bool half = false) {
     constexpr int S = N2 + 1;
     if (t < N1) {
-        rdftR<N2, false>(v);
+        if constexpr (N2 == 16 && !std::is_same<C, dd2>::value) {
+            if (half)
+                rdft16<false, C, true, false>(v);
+            else
+                rdft16<false>(v);
+        } else {
+            rdftR<N2, false>(v);
+        }
 #pragma unroll
         for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[k2]);
 #pragma unroll
@@ -213,9 +253,12 @@ __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
 }
 
 // inverse (unnormalised): lane t < N2 gives X[t + N2 k1] in v[k1]; on return
-// lane t < N1 holds x[t + N1 n2] in v[n2].
+// lane t < N1 holds x[t + N1 n2] in v[n2].  half: only x[j], j < L / 2, is
+// wanted (v[n2] for n2 >= N2 / 2 may be left undefined; FP32 and FP64 prune
+// the last radix-16 stage).
 template <int N1, int N2, typename C, typename TW>
-__device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs) {
+__device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs,
+                                     bool half = false) {
     constexpr int S = N2 + 1;
     if (t < N2) {
         rdftR<N1, true>(v);
@@ -228,7 +271,14 @@ __device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
     if (t < N1) {
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) v[k2] = ex[(t * S + k2) * xs];
-        rdftR<N2, true>(v);
+        if constexpr (N2 == 16 && !std::is_same<C, dd2>::value) {
+            if (half)
+                rdft16<true, C, false, true>(v);
+            else
+                rdft16<true>(v);
+        } else {
+            rdftR<N2, true>(v);
+        }
     }
     __syncthreads();
 }

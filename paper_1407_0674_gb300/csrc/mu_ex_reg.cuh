@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xfwd_r(const In
             v[n2] = C{re, im};
         }
     }
-    fwd2<N1, N2>(v, lt, ex, t, 1);
+    fwd2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N2) {
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) ex[t + N2 * k1] = v[k1];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_r(const ty
             v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
                               : C{0, 0};
     }
-    inv2<N1, N2>(v, lt, ex, t, 1);
+    inv2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N1 && y0 < d.ny) {
         double *dst = out + f * out_fstride + (size_t)z * d.ny * d.nx;
         const double coef = U ? sc.sh[f] : 0.0;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_raw_r(cons
             v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
                               : C{0, 0};
     }
-    inv2<N1, N2>(v, lt, ex, t, 1);
+    inv2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N1 && y0 < d.ny) {
         OutT *dst = out + ((size_t)f * d.nz + z) * d.ny * d.nx;
 #pragma unroll
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_ypass_r(const t
                 v[n2] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
             }
         }
-        fwd2<N1, N2>(v, lt, ex, t, TX);
+        fwd2<N1, N2>(v, lt, ex, t, TX, 2 * n_in <= N1 * N2);
         if (t < N2 && ok) {
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_ypass_r(const t
                 v[k1] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
             }
         }
-        inv2<N1, N2>(v, lt, ex, t, TX);
+        inv2<N1, N2>(v, lt, ex, t, TX, 2 * n_out <= N1 * N2);
         if (t < N1 && ok) {
 #pragma unroll
             for (int n2 = 0; n2 < N2; ++n2) {

@@ -63,14 +63,14 @@ template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4(C (&v)[
 // t + 64 are stored, so the first forward and the last inverse radix-4
 // butterflies shrink.  Both give the values rdft4 gives (adding an exact zero
 // changes nothing).
-template <bool INV, typename C> __device__ __forceinline__ void rdft4_in2(C (&v)[4]) {
+template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4_in2(C (&v)[4]) {
     const C a = v[0], b = v[1], rb = rot<INV>(b);
     v[0] = z4add(a, b);
     v[2] = z4sub(a, b);
     v[1] = z4add(a, rb);
     v[3] = z4sub(a, rb);
 }
-template <bool INV, typename C> __device__ __forceinline__ void rdft4_out2(C (&v)[4]) {
+template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4_out2(C (&v)[4]) {
     const C t0 = z4add(v[0], v[2]), t1 = z4sub(v[0], v[2]);
     const C t2 = z4add(v[1], v[3]), t3 = rot<INV>(z4sub(v[1], v[3]));
     v[0] = z4add(t0, t2);
@@ -115,7 +115,7 @@ template <typename C> struct Z4TwSmem {
 template <typename C, typename TW>
 __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs, bool half) {
     if (half)
-        rdft4_in2<false>(v);
+        z4_rdft4_in2<false>(v);
     else
         z4_rdft4<false>(v);
 #pragma unroll
@@ -193,7 +193,7 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
 #pragma unroll
     for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[k - 1]));
     if (half)
-        rdft4_out2<true>(v);
+        z4_rdft4_out2<true>(v);
     else
         z4_rdft4<true>(v);
 }

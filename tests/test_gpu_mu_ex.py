@@ -346,6 +346,33 @@ def test_z_length_256_radix4_kernels(pnp, s):
     assert normwise(mu32, ref) <= FP32_TOL
 
 
+@pytest.mark.parametrize("axis,n", [(0, 100), (0, 150), (1, 100), (1, 150)])
+def test_xy_length_256_half_and_full_lines(pnp, axis, n):
+    """x or y zero-extended to 256 points: lines of at most 128 points take
+    the FP32 and FP64 transforms with the first forward / last inverse
+    radix-16 stage pruned to the zero padding, longer lines the full ones;
+    every precision against the oracle."""
+    R = (1.5, 2.0)
+    rb = tuple(bulk_density(0.1, r) for r in R)
+    shape = [10, 10, 10]
+    shape[axis] = n
+    fft = [24, 24, 24]
+    fft[axis] = 256
+    spec = ProblemSpec(nx=shape[0], ny=shape[1], nz=shape[2], bc=("N", "N", "D"), R=R, q=(1, -1), rho_b=rb,
+                       fft_len=tuple(fft))
+    rho = lognormal_density(spec, 50 + axis, sigma=0.2)
+    ref, bad = oracle.excess_mu(spec, rho)
+    assert bad == 0
+    with pnp.Problem(spec) as P:
+        assert P.info()["fft_len"] == tuple(fft)
+        mu = P.excess_mu(rho, precision="fp64")
+        mudd = P.excess_mu(rho, precision="df64")
+        mu32 = P.excess_mu(rho, precision="fp32")
+    assert normwise(mu, ref) <= FP64_TOL
+    assert normwise(mudd, ref) <= FP64_TOL
+    assert normwise(mu32, ref) <= FP32_TOL
+
+
 @pytest.mark.parametrize("nz,bc", [(150, "D"), (256, "P")])
 def test_z_length_256_full_columns(pnp, nz, bc):
     """Lz = 256 with columns longer than half the padded length (a
