@@ -51,13 +51,26 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft3(C *v) {
     v[2] = csub(m, r);
 }
 
-template <bool INV, typename C> __device__ __forceinline__ void rdft4(C *v) {
-    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    C t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+// complex sums of the radix-4 butterflies: PK selects, for double-float,
+// the packed FP32x2 form (two FP32 additions per instruction, the scalar
+// bits).  Only the 256-point x and y transforms take it: in every kernel it
+// multiplies the compiler's register-allocation time several-fold.
+template <bool PK, typename C> __device__ __forceinline__ C bsum(C a, C b) {
+    if constexpr (PK && std::is_same<C, dd2>::value) return dd2_add(a, b);
+    else return cadd(a, b);
+}
+template <bool PK, typename C> __device__ __forceinline__ C bdif(C a, C b) {
+    if constexpr (PK && std::is_same<C, dd2>::value) return dd2_sub(a, b);
+    else return csub(a, b);
+}
+
+template <bool INV, typename C, bool PK = false> __device__ __forceinline__ void rdft4(C *v) {
+    C t0 = bsum<PK>(v[0], v[2]), t1 = bdif<PK>(v[0], v[2]);
+    C t2 = bsum<PK>(v[1], v[3]), t3 = rot<INV>(bdif<PK>(v[1], v[3]));
+    v[0] = bsum<PK>(t0, t2);
+    v[2] = bdif<PK>(t0, t2);
+    v[1] = bsum<PK>(t1, t3);
+    v[3] = bdif<PK>(t1, t3);
 }
 
 template <bool INV, typename C> __device__ __forceinline__ void rdft5(C *v) {
@@ -118,33 +131,34 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft6(C *v) {
 // radix-4 butterflies for zero padding: inputs 2 and 3 zero, or only
 // outputs 0 and 1 wanted; the values rdft4 gives there (adding an exact zero
 // changes nothing)
-template <bool INV, typename C> __device__ __forceinline__ void rdft4_in2(C *v) {
+template <bool INV, typename C, bool PK = false> __device__ __forceinline__ void rdft4_in2(C *v) {
     const C a = v[0], b = v[1], rb = rot<INV>(b);
-    v[0] = cadd(a, b);
-    v[2] = csub(a, b);
-    v[1] = cadd(a, rb);
-    v[3] = csub(a, rb);
+    v[0] = bsum<PK>(a, b);
+    v[2] = bdif<PK>(a, b);
+    v[1] = bsum<PK>(a, rb);
+    v[3] = bdif<PK>(a, rb);
 }
-template <bool INV, typename C> __device__ __forceinline__ void rdft4_out2(C *v) {
-    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    const C t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
-    v[0] = cadd(t0, t2);
-    v[1] = cadd(t1, t3);
+template <bool INV, typename C, bool PK = false> __device__ __forceinline__ void rdft4_out2(C *v) {
+    const C t0 = bsum<PK>(v[0], v[2]), t1 = bdif<PK>(v[0], v[2]);
+    const C t2 = bsum<PK>(v[1], v[3]), t3 = rot<INV>(bdif<PK>(v[1], v[3]));
+    v[0] = bsum<PK>(t0, t2);
+    v[1] = bsum<PK>(t1, t3);
 }
 
 // 16 = 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1.  IN8: inputs 8..15 are zero
 // (n2 >= 2); OUT8: only outputs 0..7 are wanted (k1 < 2; the others are left
 // undefined).
-template <bool INV, typename C, bool IN8 = false, bool OUT8 = false> __device__ __forceinline__ void rdft16(C *v) {
+template <bool INV, typename C, bool IN8 = false, bool OUT8 = false, bool PK = false>
+__device__ __forceinline__ void rdft16(C *v) {
     C a[4][4];
 #pragma unroll
     for (int n1 = 0; n1 < 4; ++n1) {
 #pragma unroll
         for (int n2 = 0; n2 < 4; ++n2) a[n1][n2] = v[n1 + 4 * n2];
         if constexpr (IN8)
-            rdft4_in2<INV>(a[n1]);
+            rdft4_in2<INV, C, PK>(a[n1]);
         else
-            rdft4<INV>(a[n1]);
+            rdft4<INV, C, PK>(a[n1]);
     }
     const double sg = INV ? 1.0 : -1.0;
     // W16^(n1 k2): exponents 1, 2, 3 (n1 = 1), 2, 4, 6 (n1 = 2), 3, 6, 9 (n1 = 3)
@@ -161,11 +175,11 @@ template <bool INV, typename C, bool IN8 = false, bool OUT8 = false> __device__ 
     for (int k2 = 0; k2 < 4; ++k2) {
         C b[4] = {a[0][k2], a[1][k2], a[2][k2], a[3][k2]};
         if constexpr (OUT8) {
-            rdft4_out2<INV>(b);
+            rdft4_out2<INV, C, PK>(b);
             v[k2] = b[0];
             v[k2 + 4] = b[1];
         } else {
-            rdft4<INV>(b);
+            rdft4<INV, C, PK>(b);
 #pragma unroll
             for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = b[k1];
         }
@@ -225,7 +239,7 @@ template <int N1, int N2, typename C> struct SmemTw {
 // the full stage: the second copy of it costs spills at its 128-register
 // budget, 0.46 -> 0.49 ms for ten fields).  Contains two __syncthreads (every
 // thread of the block must call).
-template <int N1, int N2, typename C, typename TW>
+template <int N1, int N2, bool PK = false, typename C, typename TW>
 __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs,
                                      bool half = false) {
     constexpr int S = N2 + 1;
@@ -235,6 +249,8 @@ __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
                 rdft16<false, C, true, false>(v);
             else
                 rdft16<false>(v);
+        } else if constexpr (N2 == 16) {
+            rdft16<false, C, false, false, PK>(v);
         } else {
             rdftR<N2, false>(v);
         }
@@ -247,7 +263,10 @@ __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
     if (t < N2) {
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) v[n1] = ex[(n1 * S + t) * xs];
-        rdftR<N1, false>(v);
+        if constexpr (N1 == 16)
+            rdft16<false, C, false, false, PK>(v);
+        else
+            rdftR<N1, false>(v);
     }
     __syncthreads();
 }
@@ -256,12 +275,15 @@ __device__ __forceinline__ void fwd2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
 // lane t < N1 holds x[t + N1 n2] in v[n2].  half: only x[j], j < L / 2, is
 // wanted (v[n2] for n2 >= N2 / 2 may be left undefined; FP32 and FP64 prune
 // the last radix-16 stage).
-template <int N1, int N2, typename C, typename TW>
+template <int N1, int N2, bool PK = false, typename C, typename TW>
 __device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *ex, int t, int xs,
                                      bool half = false) {
     constexpr int S = N2 + 1;
     if (t < N2) {
-        rdftR<N1, true>(v);
+        if constexpr (N1 == 16)
+            rdft16<true, C, false, false, PK>(v);
+        else
+            rdftR<N1, true>(v);
 #pragma unroll
         for (int n1 = 1; n1 < N1; ++n1) v[n1] = cmul(v[n1], cconj(tw[n1]));
 #pragma unroll
@@ -276,6 +298,8 @@ __device__ __forceinline__ void inv2(C (&v)[Shape<N1, N2>::G], const TW &tw, C *
                 rdft16<true, C, false, true>(v);
             else
                 rdft16<true>(v);
+        } else if constexpr (N2 == 16) {
+            rdft16<true, C, false, false, PK>(v);
         } else {
             rdftR<N2, true>(v);
         }

@@ -38,9 +38,7 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-// double-float complex sums on packed FP32x2 instructions (same bits)
-template <> __device__ __forceinline__ dd2 cadd<dd2>(dd2 a, dd2 b) { return dd2_add(a, b); }
-template <> __device__ __forceinline__ dd2 csub<dd2>(dd2 a, dd2 b) { return dd2_sub(a, b); }
+
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
 // multiply by -i (forward) or +i (inverse)

@@ -45,6 +45,11 @@ __device__ __forceinline__ C pack_two(const C *__restrict__ x0, const C *__restr
 // 78 to 88 registers, two CTAs per SM instead of three
 template <typename T> constexpr int xlines_min_blocks() { return std::is_same<T, dd>::value ? 2 : 0; }
 
+// packed FP32x2 butterfly sums for the double-float 256-point x and y lines
+template <typename T, int N1, int N2> constexpr bool lines_packed() {
+    return std::is_same<T, dd>::value && N1 == 16 && N2 == 16;
+}
+
 // ---------------------------------------------------------------------------
 // x forward (R2C, two real lines per complex FFT).  block P*G, grid (ceil(npairs/P), nz, F)
 template <typename T, int N1, int N2, typename InT = double>
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xfwd_r(const In
             v[n2] = C{re, im};
         }
     }
-    fwd2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
+    fwd2<N1, N2, lines_packed<T, N1, N2>()>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N2) {
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) ex[t + N2 * k1] = v[k1];
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_r(const ty
             v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
                               : C{0, 0};
     }
-    inv2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
+    inv2<N1, N2, lines_packed<T, N1, N2>()>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N1 && y0 < d.ny) {
         double *dst = out + f * out_fstride + (size_t)z * d.ny * d.nx;
         const double coef = U ? sc.sh[f] : 0.0;
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_xinv_raw_r(cons
             v[k1] = y0 < d.ny ? pack_two(src, y0 + 1 < d.ny ? src + d.Wx : (const C *)nullptr, t + N2 * k1, L)
                               : C{0, 0};
     }
-    inv2<N1, N2>(v, lt, ex, t, 1, 2 * d.nx <= L);
+    inv2<N1, N2, lines_packed<T, N1, N2>()>(v, lt, ex, t, 1, 2 * d.nx <= L);
     if (t < N1 && y0 < d.ny) {
         OutT *dst = out + ((size_t)f * d.nz + z) * d.ny * d.nx;
 #pragma unroll
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_ypass_r(const t
                 v[n2] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
             }
         }
-        fwd2<N1, N2>(v, lt, ex, t, TX, 2 * n_in <= N1 * N2);
+        fwd2<N1, N2, lines_packed<T, N1, N2>()>(v, lt, ex, t, TX, 2 * n_in <= N1 * N2);
         if (t < N2 && ok) {
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(256, xlines_min_blocks<T>()) k_ypass_r(const t
                 v[k1] = (ok && j < n_in) ? src[(size_t)j * d.Wx] : C{0, 0};
             }
         }
-        inv2<N1, N2>(v, lt, ex, t, TX, 2 * n_out <= N1 * N2);
+        inv2<N1, N2, lines_packed<T, N1, N2>()>(v, lt, ex, t, TX, 2 * n_out <= N1 * N2);
         if (t < N1 && ok) {
 #pragma unroll
             for (int n2 = 0; n2 < N2; ++n2) {

@@ -36,27 +36,10 @@ constexpr int kZ4MaxSpecies = 3;
 // shared-memory wavefronts
 __device__ __forceinline__ int z4pad(int i) { return i + (i >> 2); }
 
-// complex sums of the radix-4 butterflies: the packed FP32x2 forms (cadd,
-// csub) or the scalar ones, which leave the register allocator free pairs
-// (measured faster here: 1.57 / 1.77 ms for z MAC / z back against
-// 1.62 / 1.79 ms packed)
-constexpr bool kZ4Packed = false;
-template <typename C> __device__ __forceinline__ C z4add(C a, C b) {
-    if constexpr (kZ4Packed) return cadd(a, b);
-    else return C{a.x + b.x, a.y + b.y};
-}
-template <typename C> __device__ __forceinline__ C z4sub(C a, C b) {
-    if constexpr (kZ4Packed) return csub(a, b);
-    else return C{a.x - b.x, a.y - b.y};
-}
-template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4(C (&v)[4]) {
-    const C t0 = z4add(v[0], v[2]), t1 = z4sub(v[0], v[2]);
-    const C t2 = z4add(v[1], v[3]), t3 = rot<INV>(z4sub(v[1], v[3]));
-    v[0] = z4add(t0, t2);
-    v[2] = z4sub(t0, t2);
-    v[1] = z4add(t1, t3);
-    v[3] = z4sub(t1, t3);
-}
+// The radix-4 butterflies here keep scalar double-float sums: the packed
+// FP32x2 form of the x and y lines (fft_reg.cuh) measured slower in these
+// kernels (z MAC 1.57 -> 1.62 ms, z back 1.77 -> 1.79 ms at 128^3 -> 256^3),
+// whose register budget leaves no room to pair real and imaginary parts.
 
 // Columns of at most 128 rows (the zero-extended half of Lz = 256): a lane's
 // input values n1 = 2, 3 are zero padding and only its output rows t and
@@ -65,16 +48,16 @@ template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4(C (&v)[
 // changes nothing).
 template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4_in2(C (&v)[4]) {
     const C a = v[0], b = v[1], rb = rot<INV>(b);
-    v[0] = z4add(a, b);
-    v[2] = z4sub(a, b);
-    v[1] = z4add(a, rb);
-    v[3] = z4sub(a, rb);
+    v[0] = cadd(a, b);
+    v[2] = csub(a, b);
+    v[1] = cadd(a, rb);
+    v[3] = csub(a, rb);
 }
 template <bool INV, typename C> __device__ __forceinline__ void z4_rdft4_out2(C (&v)[4]) {
-    const C t0 = z4add(v[0], v[2]), t1 = z4sub(v[0], v[2]);
-    const C t2 = z4add(v[1], v[3]), t3 = rot<INV>(z4sub(v[1], v[3]));
-    v[0] = z4add(t0, t2);
-    v[1] = z4add(t1, t3);
+    const C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const C t2 = cadd(v[1], v[3]), t3 = rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[1] = cadd(t1, t3);
 }
 
 // lane t's frequency of value k4
@@ -117,7 +100,7 @@ __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int 
     if (half)
         z4_rdft4_in2<false>(v);
     else
-        z4_rdft4<false>(v);
+        rdft4<false>(v);
 #pragma unroll
     for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[k - 1]);
     __syncthreads();
@@ -128,7 +111,7 @@ __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int 
         const int k1 = t >> 4, m0 = t & 15;
 #pragma unroll
         for (int m1 = 0; m1 < 4; ++m1) v[m1] = A[z4pad(k1 * 64 + m0 + 16 * m1) * xs];
-        z4_rdft4<false>(v);
+        rdft4<false>(v);
 #pragma unroll
         for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[2 + k]);
 #pragma unroll
@@ -139,7 +122,7 @@ __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int 
         const int k1 = t >> 4, k2 = (t >> 2) & 3, p0 = t & 3;
 #pragma unroll
         for (int p1 = 0; p1 < 4; ++p1) v[p1] = B[z4pad(k1 * 64 + k2 * 16 + p0 + 4 * p1) * xs];
-        z4_rdft4<false>(v);
+        rdft4<false>(v);
 #pragma unroll
         for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], tw[5 + k]);
 #pragma unroll
@@ -150,7 +133,7 @@ __device__ __forceinline__ void z4_fwd(C (&v)[4], const TW &tw, C *A, C *B, int 
         const int k1 = t >> 4, k2 = (t >> 2) & 3, k3 = t & 3;
 #pragma unroll
         for (int p0 = 0; p0 < 4; ++p0) v[p0] = A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs];
-        z4_rdft4<false>(v);
+        rdft4<false>(v);
     }
 }
 
@@ -160,7 +143,7 @@ template <typename C, typename TW>
 __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int t, int xs, bool half) {
     {
         const int k1 = t >> 4, k2 = (t >> 2) & 3, k3 = t & 3;
-        z4_rdft4<true>(v);
+        rdft4<true>(v);
         __syncthreads();
 #pragma unroll
         for (int p0 = 0; p0 < 4; ++p0) A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs] = v[p0];
@@ -172,7 +155,7 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
         for (int k3 = 0; k3 < 4; ++k3) v[k3] = A[z4pad(k1 * 64 + k2 * 16 + k3 * 4 + p0) * xs];
 #pragma unroll
         for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[5 + k]));
-        z4_rdft4<true>(v);
+        rdft4<true>(v);
 #pragma unroll
         for (int p1 = 0; p1 < 4; ++p1) B[z4pad(k1 * 64 + k2 * 16 + p0 + 4 * p1) * xs] = v[p1];
     }
@@ -183,7 +166,7 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
         for (int k2 = 0; k2 < 4; ++k2) v[k2] = B[z4pad(k1 * 64 + k2 * 16 + m0) * xs];
 #pragma unroll
         for (int k = 1; k < 4; ++k) v[k] = cmul(v[k], cconj(tw[2 + k]));
-        z4_rdft4<true>(v);
+        rdft4<true>(v);
 #pragma unroll
         for (int m1 = 0; m1 < 4; ++m1) A[z4pad(k1 * 64 + m0 + 16 * m1) * xs] = v[m1];
     }
@@ -195,7 +178,7 @@ __device__ __forceinline__ void z4_inv(C (&v)[4], const TW &tw, C *A, C *B, int 
     if (half)
         z4_rdft4_out2<true>(v);
     else
-        z4_rdft4<true>(v);
+        rdft4<true>(v);
 }
 
 // columns per CTA side: FP32 4 (512 threads), 64-bit types 2 (256 threads)
