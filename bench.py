@@ -287,8 +287,8 @@ PROFILED_FP32_INST = {
 }
 
 DTYPE = {"fp64": "f64",
-         "df64": "df64 (FFT values and FMT derivatives as FP32 pairs, ~48-bit, on the FP32 pipes; "
-                 "ln(1 - n3) by range reduction and an atanh series)",
+         "df64": "df64 (FFT values and FMT derivative products as FP32 pairs, ~48-bit; "
+                 "FP64 singular terms ln(1 - n3), 1/(1 - n3))",
          "fp32": "f32 FFT / f64 singular terms of the FMT derivatives",
          "tf32split": "f32 FFT with the y-axis radix-16 DFT stages as 3xTF32 tensor-core products / "
                       "f64 singular terms of the FMT derivatives"}

@@ -81,57 +81,6 @@ __device__ __forceinline__ dd2 dd2_add(dd2 a, dd2 b) {
 __device__ __forceinline__ dd2 dd2_sub(dd2 a, dd2 b) { return dd2_add(a, dd2{-b.x, -b.y}); }
 
 
-// a / b: the FP32 quotient of the high parts, corrected once by the
-// remainder a - q b taken in double-float (about 2^-47 relative)
-__device__ __forceinline__ dd dd_div(dd a, dd b) {
-    const float q1 = a.hi / b.hi;
-    const dd r = a - b * dd(q1, 0.f);
-    const float q2 = r.hi / b.hi;
-    return dd_fast_two_sum(q1, q2);
-}
-
-// ln(1 - u) for 1 - u > 2^-100, on the FP32 pipes.  With x = 1 - u = 2^e m,
-// m in [1/sqrt2, sqrt2): ln x = e ln2 + 2 atanh(r), r = (m - 1) / (m + 1),
-// |r| <= 0.1716, and atanh(r) = r (1 + r^2/3 + r^4/5 + ... + r^18/19): the
-// first term left out is below 2^-54 of the sum.  For u <= 0.29 (e = 0)
-// r = -u / (2 - u) is formed from u itself, so a small u keeps its relative
-// precision (1 - u would round its low bits away).
-__device__ __forceinline__ dd dd_log1m(dd u) {
-    constexpr dd kLn2(0.6931471805599453094172321);
-    const dd one(1.f, 0.f);
-    dd num, den;
-    int e = 0;
-    if (u.hi <= 0.29f) {
-        num = -u;
-        den = dd(2.f, 0.f) - u;
-    } else {
-        const dd x = one - u;
-        e = ((__float_as_int(x.hi) >> 23) & 0xff) - 126;       // x.hi / 2^e in [1/2, 1)
-        const float sc = __int_as_float((127 - e) << 23);          // 2^-e, exact
-        dd m(x.hi * sc, x.lo * sc);
-        if (m.hi < 0.70710678f) {
-            m = dd(2.f * m.hi, 2.f * m.lo);
-            e -= 1;
-        }
-        num = m - one;
-        den = m + one;
-    }
-    const dd r = dd_div(num, den);
-    const dd z = r * r;
-    dd p(1.0 / 19.0);
-    p = p * z + dd(1.0 / 17.0);
-    p = p * z + dd(1.0 / 15.0);
-    p = p * z + dd(1.0 / 13.0);
-    p = p * z + dd(1.0 / 11.0);
-    p = p * z + dd(1.0 / 9.0);
-    p = p * z + dd(1.0 / 7.0);
-    p = p * z + dd(1.0 / 5.0);
-    p = p * z + dd(1.0 / 3.0);
-    p = p * z + one;
-    const dd at = r * p;
-    return dd(2.f * at.hi, 2.f * at.lo) + dd((float)e, 0.f) * kLn2;
-}
-
 __device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
 __device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
 __device__ __forceinline__ dd &operator*=(dd &a, dd b) { return a = a * b; }

@@ -243,26 +243,24 @@ static __global__ void k_dphi_fields_mixed(float *__restrict__ f, size_t N, int 
     if (bad) atomicOr(flag, kFlagPacking);
 }
 
-// The same derivatives for double-float fields, entirely in double-float on
-// the FP32 pipes: 1/(1 - n3) by a corrected FP32 quotient, ln(1 - n3) by
-// dd_log1m (about 2^-47 relative each, far inside the FFT's error); only the
-// White Bear phi3 stays in FP64.  Internal linkage: one copy per translation
-// unit.
+// The same derivatives for double-float fields: the functions singular at
+// packing, 1/(1 - n3) and ln(1 - n3) (and the White Bear phi3), in FP64;
+// every product with the other weighted densities in double-float on the
+// FP32 pipes, whose error (about 2^-47 of each term) stays far inside the
+// FFT's.  Internal linkage: one copy per translation unit.
 static __global__ void k_dphi_fields_dd(dd *__restrict__ f, size_t N, int *__restrict__ flag, int fmt) {
     const dd k8pi(1.0 / (8.0 * M_PI)), k12pi(1.0 / (12.0 * M_PI)), k4pi(1.0 / (4.0 * M_PI)), three(3);
-    const dd one(1.f, 0.f);
     bool bad = false;
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
         dd n[kNumWeighted], psi[kNumWeighted];
 #pragma unroll
         for (int a = 0; a < kNumWeighted; ++a) n[a] = f[a * N + p];
-        const dd x = one - n[3];
-        const bool inside = x.hi > 0x1p-100f;           // n3 < 1 (dd_log1m's range)
-        const dd g = dd_div(one, x), g2 = g * g;
+        const double n3 = (double)n[3];
+        const double gd = 1.0 / (1.0 - n3);
+        const dd g(gd), g2 = g * g;
         // coefficient functions of n2^2 (psi2, vector psi) and n2^3 (psi3)
         dd c2, c3, cv;
         if (fmt == PNP_FMT_WHITE_BEAR) {
-            const double n3 = (double)n[3];
             double fw = 0.0, dfw = 0.0;
             if (n3 < 1.0) wb_phi3(n3, fw, dfw);
             c2 = dd(fw * (1.0 / (12.0 * M_PI)));
@@ -276,7 +274,7 @@ static __global__ void k_dphi_fields_dd(dd *__restrict__ f, size_t N, int *__res
         const dd n0 = n[0], n1 = n[1], n2 = n[2];
         const dd v1v2 = n[4] * n[7] + n[5] * n[8] + n[6] * n[9];
         const dd v2v2 = n[7] * n[7] + n[8] * n[8] + n[9] * n[9];
-        psi[0] = -dd_log1m(n[3]);
+        psi[0] = dd(-log1p(-n3));
         psi[1] = n2 * g;
         psi[2] = n1 * g + (n2 * n2 - v2v2) * c2;
         psi[3] = n0 * g + (n1 * n2 - v1v2) * g2 + (n2 * n2 * n2 - three * n2 * v2v2) * c3;
@@ -285,7 +283,7 @@ static __global__ void k_dphi_fields_dd(dd *__restrict__ f, size_t N, int *__res
             psi[4 + c] = -(n[7 + c] * g);
             psi[7 + c] = -(n[4 + c] * g) - n2 * n[7 + c] * cv;
         }
-        bool ok = inside;
+        bool ok = n3 < 1.0;
 #pragma unroll
         for (int a = 0; a < kNumWeighted; ++a) ok = ok && isfinite(psi[a].hi) && isfinite(psi[a].lo);
         if (!ok) bad = true;

@@ -281,11 +281,11 @@ def test_full_size_sampled(pnp):
 
 @pytest.mark.parametrize("scale", [1e-6, 1e-2, 1.0, 2.5, 3.0])
 def test_df64_derivatives_across_packing(pnp, scale):
-    """The double-float derivative stage takes ln(1 - n3) and 1/(1 - n3) on
-    the FP32 pipes (a corrected FP32 quotient; range reduction and an atanh
-    series, with r formed from n3 itself below 0.29).  From a nearly empty
-    fluid (mu ~ 1e-6) to one close to packing (mu up to ~1e4) it stays within
-    1e-12 of the FP64 path (about 2e-14 on the bench workload)."""
+    """The double-float derivative stage (ln(1 - n3) and 1/(1 - n3) in FP64,
+    their products with the other weighted densities in double-float): from
+    a nearly empty fluid (mu ~ 1e-6) to one close to packing (mu up to ~1e4)
+    it stays within 1e-12 of the FP64 path (about 2e-14 on the bench
+    workload)."""
     spec, rho = mu_microbench(12)
     rho = rho * scale
     with pnp.Problem(spec) as P:
