@@ -53,8 +53,8 @@ template <bool INV, typename C> __device__ __forceinline__ void rdft3(C *v) {
 
 // complex sums of the radix-4 butterflies: PK selects, for double-float,
 // the packed FP32x2 form (two FP32 additions per instruction, the scalar
-// bits).  Only the 256-point x and y transforms take it: in every kernel it
-// multiplies the compiler's register-allocation time several-fold.
+// bits).  Only the 256-point x and y transforms take it: taken by every
+// double-float kernel it stretched that unit's compile from 2 to 10.5 min.
 template <bool PK, typename C> __device__ __forceinline__ C bsum(C a, C b) {
     if constexpr (PK && std::is_same<C, dd2>::value) return dd2_add(a, b);
     else return cadd(a, b);

@@ -39,7 +39,8 @@ __device__ __forceinline__ int z4pad(int i) { return i + (i >> 2); }
 // The radix-4 butterflies here keep scalar double-float sums: the packed
 // FP32x2 form of the x and y lines (fft_reg.cuh) measured slower in these
 // kernels (z MAC 1.57 -> 1.62 ms, z back 1.77 -> 1.79 ms at 128^3 -> 256^3),
-// whose register budget leaves no room to pair real and imaginary parts.
+// presumably because their 128-register budget leaves little room to keep
+// real and imaginary parts paired.
 
 // Columns of at most 128 rows (the zero-extended half of Lz = 256): a lane's
 // input values n1 = 2, 3 are zero padding and only its output rows t and
